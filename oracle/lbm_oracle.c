@@ -1,0 +1,515 @@
+/*
+ * Plain FP64 CPU oracle of one time step of the extended Shan-Chen lattice
+ * Boltzmann method for metal-foam bubbles (Barzegari, Bayani, Mirbagheri &
+ * Shetabivash, arXiv 1708.01613).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library. The product path (the
+ * CUDA library and its Python binding) never calls it, and this file shares
+ * no source, header, table or helper with the CUDA path.
+ *
+ * Everything is FP64, written as the plain definition: one loop nest per
+ * equation, no blocking, no fusion. Loops over rows run under OpenMP; every
+ * cell is computed independently, so results do not depend on the thread
+ * count.
+ *
+ * Paper passages followed (section / equation numbers of arXiv 1708.01613):
+ *   moments                 Sec. 2.1.1, Eq. 11
+ *   equilibrium             Sec. 2.1.1, Eq. 14
+ *   D2Q9 velocities/weights Sec. 2.1.1, Eqs. 15-16
+ *   BGK collision           Sec. 2.1.1, Eq. 18 (Eq. 12 is the same update
+ *                           with the "- f_i" lost; Eq. 18 is used)
+ *   streaming               Sec. 2.1.1, Eq. 19
+ *   Shan-Chen force         Sec. 2.1.2, Eq. 22
+ *   equation of state       Sec. 2.1.2, Eq. 29 (Eq. 33 drops the square)
+ *   pseudopotential         Sec. 2.1.2, Eq. 30, psi = rho0 (1 - exp(-rho/rho0))
+ *   velocity shift          Sec. 2.1.5, Eqs. 39-40: u = u_total + tau * F
+ *                           (F per unit density here)
+ *   nearest-bubble rule     Sec. 2.1.5 (interaction zones, nearest bubble,
+ *                           Eq. 38 selection of one bubble's potential)
+ *   barrier wall            Sec. 2.1.5, modified Shan-Chen flowchart
+ *                           ("neglect effect from other side of barrier wall")
+ *   rupture criterion       Sec. 2.1.5, Eq. 41 (eta_m = 0 when d2p/dn2 = 0)
+ *   run termination         Sec. 2.1.4 main flowchart and Sec. 5 (the foam
+ *                           run ends when the first cell reaches rupture)
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - direction order 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1)
+ *     6:(-1,1) 7:(-1,-1) 8:(1,-1);
+ *   - periodic box on all sides (the paper's "mirror" boundary, which it
+ *     defines as re-entering at the opposite wall);
+ *   - gas cell: rho < gas_threshold (default ln 2, the critical density of
+ *     Sec. 2.1.2); bubbles are 4-connected gas components on the torus,
+ *     labelled by the smallest row-major index in the component;
+ *   - owner of a liquid cell: the bubble of the nearest gas cell within the
+ *     zone radius R_z, ties broken by the smaller label; none beyond R_z;
+ *   - a blocked edge (x, x+e_i) has owners that differ, both defined, and
+ *     neither end opened; across a blocked edge the force uses psi(x) in
+ *     place of psi(x+e_i);
+ *   - "d2p/dn2 = 0": at a cell with a differing-owner neighbour, n is the
+ *     first such lattice direction; D2 = p(x+n) - 2 p(x) + p(x-n); the cell
+ *     opens (for good) when |D2| <= eps or the sign of D2 differs from the
+ *     sign stored at the previous relabel; eps < 0 disables rupture;
+ *   - the barrier pipeline runs on the pre-collision density at the start of
+ *     every step t with t % K == 0 and the mask is held for K steps;
+ *   - reported velocity u = (j + F/2) / rho; reported pressure p of Eq. 29.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q 9
+
+static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
+                             1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+typedef struct {
+  int32_t nx, ny;
+  int32_t barrier;          /* 0: plain Shan-Chen; 1: film barrier + rupture */
+  int32_t relabel_every;    /* K >= 1 */
+  int32_t zone_radius;      /* R_z */
+  int32_t stop_on_first_rupture;
+  double tau, G, rho0;
+  double gas_threshold;     /* rho below this is gas */
+  double rupture_eps;       /* eps for |D2| <= eps; < 0 disables rupture */
+} orc_params;
+
+typedef struct {
+  double *f;       /* [9][ny][nx] incoming populations at the start of step t */
+  double *f_next;  /* [9][ny][nx] scratch */
+  double *rho, *jx, *jy, *psi, *Fx, *Fy; /* [ny][nx] scratch */
+  int32_t *label;  /* [ny][nx] bubble label or -1 */
+  int32_t *owner;  /* [ny][nx] owning bubble or -1 */
+  int8_t *sgn;     /* [ny][nx] sign of D2 at the last relabel (0: none) */
+  uint8_t *open;   /* [ny][nx] 1 once the cell has ruptured */
+  uint8_t *mask;   /* [ny][nx] bit i-1: edge (x, x+e_i) blocked */
+  int64_t t;               /* steps done */
+  int64_t opened_total;    /* cells opened so far */
+  int32_t opened_last;     /* cells opened at the latest relabel */
+  int32_t halted;          /* 1 after the first rupture if stopping on it */
+} orc_state;
+
+static inline int wrap(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_lattice(int32_t *ex, int32_t *ey, double *w) {
+  for (int i = 0; i < Q; ++i) {
+    ex[i] = EX[i];
+    ey[i] = EY[i];
+    w[i] = WT[i];
+  }
+}
+
+/* Eq. 30 with the scale rho0. */
+double orc_psi(double rho, double rho0) { return rho0 * (1.0 - exp(-rho / rho0)); }
+
+/* Eq. 29 with c_s^2 = 1/3. */
+double orc_pressure(double rho, double G, double rho0) {
+  double s = orc_psi(rho, rho0);
+  return rho / 3.0 + G * s * s / 6.0;
+}
+
+/* Eq. 14 with c_s^2 = 1/3. */
+void orc_equilibrium(double rho, double ux, double uy, double *feq) {
+  double uu = ux * ux + uy * uy;
+  for (int i = 0; i < Q; ++i) {
+    double eu = EX[i] * ux + EY[i] * uy;
+    feq[i] = WT[i] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+  }
+}
+
+/* Eq. 11: rho = sum f_i, j = sum e_i f_i. */
+void orc_moments(const orc_params *p, const double *f, double *rho, double *jx, double *jy) {
+  const int nx = p->nx, ny = p->ny;
+  const size_t N = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      double r = 0.0, a = 0.0, b = 0.0;
+      for (int i = 0; i < Q; ++i) {
+        double fi = f[i * N + c];
+        r += fi;
+        a += EX[i] * fi;
+        b += EY[i] * fi;
+      }
+      rho[c] = r;
+      if (jx) jx[c] = a;
+      if (jy) jy[c] = b;
+    }
+}
+
+/* Eq. 22: F(x) = -G psi(x) sum_{i=1..8} w_i psi~_i e_i, where psi~_i is
+ * psi(x+e_i), or psi(x) if the edge (x, x+e_i) is blocked (mask may be NULL). */
+void orc_force(const orc_params *p, const double *psi, const uint8_t *mask, double *Fx,
+               double *Fy) {
+  const int nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      double sx = 0.0, sy = 0.0;
+      for (int i = 1; i < Q; ++i) {
+        size_t nb = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+        double s = psi[nb];
+        if (mask && ((mask[c] >> (i - 1)) & 1u)) s = psi[c];
+        sx += WT[i] * s * EX[i];
+        sy += WT[i] * s * EY[i];
+      }
+      Fx[c] = -p->G * psi[c] * sx;
+      Fy[c] = -p->G * psi[c] * sy;
+    }
+}
+
+/* Gas cells (rho < threshold) grouped into 4-connected components on the
+ * torus. Cells are visited in row-major order and each unvisited gas cell
+ * starts a breadth-first search that gives its whole component its own index,
+ * which is therefore the smallest index in the component. Liquid: -1. */
+void orc_label(const orc_params *p, const double *rho, int32_t *label) {
+  const int nx = p->nx, ny = p->ny;
+  const size_t N = (size_t)nx * ny;
+  int32_t *queue = (int32_t *)malloc(N * sizeof(int32_t));
+  for (size_t c = 0; c < N; ++c) label[c] = -1;
+  for (size_t c0 = 0; c0 < N; ++c0) {
+    if (!(rho[c0] < p->gas_threshold) || label[c0] >= 0) continue;
+    size_t head = 0, tail = 0;
+    label[c0] = (int32_t)c0;
+    queue[tail++] = (int32_t)c0;
+    while (head < tail) {
+      int32_t c = queue[head++];
+      int x = c % nx, y = c / nx;
+      for (int i = 1; i <= 4; ++i) {
+        size_t nb = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+        if (rho[nb] < p->gas_threshold && label[nb] < 0) {
+          label[nb] = (int32_t)c0;
+          queue[tail++] = (int32_t)nb;
+        }
+      }
+    }
+  }
+  free(queue);
+}
+
+/* Interaction zones (Sec. 2.1.5): a gas cell belongs to its own bubble; a
+ * liquid cell belongs to the bubble of the gas cell g that minimises
+ * (|x-g|^2 on the torus, label(g)) among gas cells with |x-g|^2 <= R_z^2;
+ * none (-1) if there is no such cell. Exhaustive search of the window. */
+void orc_owner(const orc_params *p, const int32_t *label, int32_t *owner) {
+  const int nx = p->nx, ny = p->ny, R = p->zone_radius;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      if (label[c] >= 0) {
+        owner[c] = label[c];
+        continue;
+      }
+      int best_d2 = -1;
+      int32_t best = -1;
+      for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx) {
+          int d2 = dx * dx + dy * dy;
+          if (d2 > R * R) continue;
+          int32_t l = label[(size_t)wrap(y + dy, ny) * nx + wrap(x + dx, nx)];
+          if (l < 0) continue;
+          if (best < 0 || d2 < best_d2 || (d2 == best_d2 && l < best)) {
+            best_d2 = d2;
+            best = l;
+          }
+        }
+      owner[c] = best;
+    }
+}
+
+/* First lattice direction i (1..8) across which the owner changes between two
+ * defined owners, or 0 if x is not on a barrier. */
+static int barrier_direction(const orc_params *p, const int32_t *owner, int x, int y) {
+  const int nx = p->nx, ny = p->ny;
+  int32_t o = owner[(size_t)y * nx + x];
+  if (o < 0) return 0;
+  for (int i = 1; i < Q; ++i) {
+    int32_t on = owner[(size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx)];
+    if (on >= 0 && on != o) return i;
+  }
+  return 0;
+}
+
+/* Rupture test of Eq. 41 under the reading given in the header. */
+void orc_rupture(const orc_params *p, const double *rho, const int32_t *owner, int8_t *sgn,
+                 uint8_t *open, int32_t *n_opened) {
+  const int nx = p->nx, ny = p->ny;
+  int32_t opened = 0;
+#pragma omp parallel for schedule(static) reduction(+ : opened)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      int i = barrier_direction(p, owner, x, y);
+      if (i == 0) {
+        sgn[c] = 0;
+        continue;
+      }
+      size_t cp = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+      size_t cm = (size_t)wrap(y - EY[i], ny) * nx + wrap(x - EX[i], nx);
+      double d2 = orc_pressure(rho[cp], p->G, p->rho0) - 2.0 * orc_pressure(rho[c], p->G, p->rho0) +
+                  orc_pressure(rho[cm], p->G, p->rho0);
+      int s = (d2 > 0.0) - (d2 < 0.0);
+      if (p->rupture_eps >= 0.0 && !open[c]) {
+        if (fabs(d2) <= p->rupture_eps || (sgn[c] != 0 && s != sgn[c])) {
+          open[c] = 1;
+          opened += 1;
+        }
+      }
+      sgn[c] = (int8_t)s;
+    }
+  *n_opened = opened;
+}
+
+/* Blocked-edge mask: bit i-1 of mask(x) is set when owner(x) and owner(x+e_i)
+ * are both defined and differ, and neither cell is open. */
+void orc_mask(const orc_params *p, const int32_t *owner, const uint8_t *open, uint8_t *mask) {
+  const int nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      uint8_t m = 0;
+      for (int i = 1; i < Q; ++i) {
+        size_t nb = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+        if (owner[c] >= 0 && owner[nb] >= 0 && owner[c] != owner[nb] && !open[c] && !open[nb])
+          m |= (uint8_t)(1u << (i - 1));
+      }
+      mask[c] = m;
+    }
+}
+
+/* The barrier pipeline on the populations of the current step. */
+void orc_relabel(const orc_params *p, orc_state *s) {
+  orc_moments(p, s->f, s->rho, NULL, NULL);
+  orc_label(p, s->rho, s->label);
+  orc_owner(p, s->label, s->owner);
+  int32_t opened = 0;
+  orc_rupture(p, s->rho, s->owner, s->sgn, s->open, &opened);
+  orc_mask(p, s->owner, s->open, s->mask);
+  s->opened_last = opened;
+  s->opened_total += opened;
+}
+
+/* f_i = f_i^eq(rho, 0) = w_i rho, open/sign state cleared, t = 0. */
+void orc_init_state(const orc_params *p, orc_state *s, const double *rho_init) {
+  const size_t N = (size_t)p->nx * p->ny;
+  for (int i = 0; i < Q; ++i)
+    for (size_t c = 0; c < N; ++c) s->f[i * N + c] = WT[i] * rho_init[c];
+  memset(s->sgn, 0, N);
+  memset(s->open, 0, N);
+  memset(s->mask, 0, N);
+  for (size_t c = 0; c < N; ++c) s->label[c] = s->owner[c] = -1;
+  s->t = 0;
+  s->opened_total = 0;
+  s->opened_last = 0;
+  s->halted = 0;
+}
+
+/* One time step: barrier pipeline when due, then moments (Eq. 11),
+ * pseudopotential (Eq. 30), force (Eq. 22, masked), velocity shift
+ * (Eqs. 39-40), equilibrium (Eq. 14), BGK collision (Eq. 18) and streaming
+ * (Eq. 19). Returns 1 if the run is halted, else 0. */
+int orc_step(const orc_params *p, orc_state *s) {
+  const int nx = p->nx, ny = p->ny;
+  const size_t N = (size_t)nx * ny;
+  if (s->halted) return 1;
+  int barrier = p->barrier != 0;
+  if (barrier && s->t % p->relabel_every == 0) orc_relabel(p, s);
+  orc_moments(p, s->f, s->rho, s->jx, s->jy);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      s->psi[c] = orc_psi(s->rho[c], p->rho0);
+    }
+  orc_force(p, s->psi, barrier ? s->mask : NULL, s->Fx, s->Fy);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      double r = s->rho[c];
+      double ux = (s->jx[c] + p->tau * s->Fx[c]) / r;
+      double uy = (s->jy[c] + p->tau * s->Fy[c]) / r;
+      double feq[Q];
+      orc_equilibrium(r, ux, uy, feq);
+      for (int i = 0; i < Q; ++i) {
+        double fi = s->f[i * N + c];
+        double fout = fi - (fi - feq[i]) / p->tau;
+        size_t dst = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+        s->f_next[i * N + dst] = fout;
+      }
+    }
+  memcpy(s->f, s->f_next, Q * N * sizeof(double));
+  s->t += 1;
+  if (barrier && p->stop_on_first_rupture && s->opened_total > 0) s->halted = 1;
+  return s->halted;
+}
+
+/* Up to nsteps steps; returns the number of steps done. */
+int64_t orc_run(const orc_params *p, orc_state *s, int64_t nsteps) {
+  int64_t done = 0;
+  while (done < nsteps && !s->halted) {
+    orc_step(p, s);
+    done += 1;
+  }
+  return done;
+}
+
+/* Diagnostics at the start of the current step (the mask last computed is
+ * used for the force): rho, u = (j + F/2)/rho, and p of Eq. 29. Any output
+ * pointer may be NULL. */
+void orc_fields(const orc_params *p, orc_state *s, double *rho, double *ux, double *uy,
+                double *pr) {
+  const int nx = p->nx, ny = p->ny;
+  orc_moments(p, s->f, s->rho, s->jx, s->jy);
+  for (size_t c = 0; c < (size_t)nx * ny; ++c) s->psi[c] = orc_psi(s->rho[c], p->rho0);
+  orc_force(p, s->psi, p->barrier ? s->mask : NULL, s->Fx, s->Fy);
+  for (size_t c = 0; c < (size_t)nx * ny; ++c) {
+    double r = s->rho[c];
+    if (rho) rho[c] = r;
+    if (ux) ux[c] = (s->jx[c] + 0.5 * s->Fx[c]) / r;
+    if (uy) uy[c] = (s->jy[c] + 0.5 * s->Fy[c]) / r;
+    if (pr) pr[c] = orc_pressure(r, p->G, p->rho0);
+  }
+}
+
+/* One step of the update evaluated only at the listed cells: given the
+ * incoming populations f of a whole box and a blocked-edge mask (may be NULL),
+ * writes the incoming populations of the next step at cells[k] into
+ * out[k*9 + i]. Each output is computed from its 5x5 neighbourhood with the
+ * same equations as orc_step. */
+void orc_step_cells(const orc_params *p, const double *f, const uint8_t *mask,
+                    const int64_t *cells, int64_t ncells, double *out) {
+  const int nx = p->nx, ny = p->ny;
+  const size_t N = (size_t)nx * ny;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t k = 0; k < ncells; ++k) {
+    int64_t c = cells[k];
+    int x = (int)(c % nx), y = (int)(c / nx);
+    for (int i = 0; i < Q; ++i) {
+      /* the population i arriving at x left the source cell x - e_i */
+      int sx = wrap(x - EX[i], nx), sy = wrap(y - EY[i], ny);
+      size_t sc = (size_t)sy * nx + sx;
+      double rho_s = 0.0, jx = 0.0, jy = 0.0;
+      for (int q = 0; q < Q; ++q) {
+        rho_s += f[q * N + sc];
+        jx += EX[q] * f[q * N + sc];
+        jy += EY[q] * f[q * N + sc];
+      }
+      double psi_s = orc_psi(rho_s, p->rho0);
+      double sxs = 0.0, sys = 0.0;
+      for (int q = 1; q < Q; ++q) {
+        size_t nb = (size_t)wrap(sy + EY[q], ny) * nx + wrap(sx + EX[q], nx);
+        double rn = 0.0;
+        for (int r = 0; r < Q; ++r) rn += f[r * N + nb];
+        double s = orc_psi(rn, p->rho0);
+        if (mask && ((mask[sc] >> (q - 1)) & 1u)) s = psi_s;
+        sxs += WT[q] * s * EX[q];
+        sys += WT[q] * s * EY[q];
+      }
+      double Fx = -p->G * psi_s * sxs, Fy = -p->G * psi_s * sys;
+      double ux = (jx + p->tau * Fx) / rho_s, uy = (jy + p->tau * Fy) / rho_s;
+      double feq[Q];
+      orc_equilibrium(rho_s, ux, uy, feq);
+      double fi = f[i * N + sc];
+      out[k * Q + i] = fi - (fi - feq[i]) / p->tau;
+    }
+  }
+}
+
+/* Initial density of round bubbles with a tanh interface: each cell takes
+ * the bubble whose surface is nearest, s = min_k (d_k - r_k) with d_k the
+ * torus distance from the cell centre to bubble k's centre, and
+ * rho = (rho_l + rho_g)/2 + (rho_l - rho_g)/2 * tanh(s / (width / 2)).
+ * With no bubbles the box is liquid. bubbles: n triples (cx, cy, r). */
+void orc_init_bubbles(const orc_params *p, const double *bubbles, int32_t n, double rho_l,
+                      double rho_g, double width, double *rho) {
+  const int nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      double best = INFINITY;
+      for (int32_t k = 0; k < n; ++k) {
+        double dx = fabs((double)x - bubbles[3 * k + 0]);
+        double dy = fabs((double)y - bubbles[3 * k + 1]);
+        dx = fmin(dx, nx - dx);
+        dy = fmin(dy, ny - dy);
+        double s = sqrt(dx * dx + dy * dy) - bubbles[3 * k + 2];
+        if (s < best) best = s;
+      }
+      double v = (n > 0) ? tanh(best / (0.5 * width)) : 1.0;
+      rho[(size_t)y * nx + x] = 0.5 * (rho_l + rho_g) + 0.5 * (rho_l - rho_g) * v;
+    }
+}
+
+/* Bubble statistics from a label array: number of bubbles, gas fraction,
+ * areas (cells) and equivalent diameters 2 sqrt(A/pi) of each bubble in
+ * order of their labels, and a histogram of the diameters on nbins
+ * logarithmic bins between dmin and dmax (values outside are clamped into the
+ * end bins). areas/diam may be NULL; they need room for the bubble count.
+ * Returns the number of bubbles. */
+int32_t orc_stats(const orc_params *p, const int32_t *label, double *gas_fraction,
+                  double *mean_diameter, double *areas, double *diam, double *hist,
+                  int32_t nbins, double dmin, double dmax) {
+  const size_t N = (size_t)p->nx * p->ny;
+  int64_t *count = (int64_t *)calloc(N, sizeof(int64_t));
+  int64_t gas = 0;
+  for (size_t c = 0; c < N; ++c)
+    if (label[c] >= 0) {
+      count[label[c]] += 1;
+      gas += 1;
+    }
+  int32_t nb = 0;
+  double sum_d = 0.0;
+  if (hist)
+    for (int b = 0; b < nbins; ++b) hist[b] = 0.0;
+  for (size_t c = 0; c < N; ++c) {
+    if (count[c] == 0) continue;
+    double a = (double)count[c];
+    double d = 2.0 * sqrt(a / M_PI);
+    if (areas) areas[nb] = a;
+    if (diam) diam[nb] = d;
+    sum_d += d;
+    if (hist && nbins > 0) {
+      double u = (log(d) - log(dmin)) / (log(dmax) - log(dmin));
+      int b = (int)floor(u * nbins);
+      if (b < 0) b = 0;
+      if (b >= nbins) b = nbins - 1;
+      hist[b] += 1.0;
+    }
+    nb += 1;
+  }
+  *gas_fraction = (double)gas / (double)N;
+  *mean_diameter = nb > 0 ? sum_d / nb : 0.0;
+  free(count);
+  return nb;
+}

@@ -1,0 +1,510 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/paper_constants.json), closed forms, conservation
+laws, textbook limits (shear-wave decay, Laplace's law, the Shan-Chen
+coexistence construction) and brute-force enumeration on tiny boxes.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize
+from scipy.sparse import coo_matrix
+from scipy.sparse.csgraph import connected_components
+
+import inputs
+import oracle as O
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+
+
+# ----------------------------------------------------------------- lattice
+def test_d2q9_weights_and_isotropy():
+    ex, ey, w = O.lattice()
+    g = GOLDEN["d2q9_weights"]["value"]
+    assert w[0] == pytest.approx(g[0], abs=1e-16)
+    assert np.allclose(w[1:5], g[1], atol=1e-16) and np.allclose(w[5:], g[2], atol=1e-16)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    cs2 = GOLDEN["cs2"]["value"]
+    for a in (ex, ey):
+        assert abs(np.sum(w * a)) < 1e-16
+        assert np.sum(w * a * a) == pytest.approx(cs2, abs=1e-15)
+    assert abs(np.sum(w * ex * ey)) < 1e-16
+    # fourth-order isotropy: sum w ex^4 = 3 cs2^2, sum w ex^2 ey^2 = cs2^2
+    assert np.sum(w * ex**4) == pytest.approx(3 * cs2**2, abs=1e-15)
+    assert np.sum(w * ex**2 * ey**2) == pytest.approx(cs2**2, abs=1e-15)
+    # opposite directions are paired as the header states
+    for i in range(9):
+        assert ex[OPP[i]] == -ex[i] and ey[OPP[i]] == -ey[i]
+
+
+def test_equilibrium_moments():
+    """Eq. 14: zeroth, first and second moments of f^eq are rho, rho u, rho cs2 I + rho u u."""
+    ex, ey, _ = O.lattice()
+    for rho, ux, uy in [(1.0, 0.0, 0.0), (2.3, 0.05, -0.02), (0.1, -0.1, 0.07)]:
+        f = O.equilibrium(rho, ux, uy)
+        assert f.sum() == pytest.approx(rho, rel=1e-14)
+        assert np.sum(f * ex) == pytest.approx(rho * ux, abs=1e-15)
+        assert np.sum(f * ey) == pytest.approx(rho * uy, abs=1e-15)
+        assert np.sum(f * ex * ex) == pytest.approx(rho / 3 + rho * ux * ux, rel=1e-13)
+        assert np.sum(f * ey * ey) == pytest.approx(rho / 3 + rho * uy * uy, rel=1e-13)
+        assert np.sum(f * ex * ey) == pytest.approx(rho * ux * uy, abs=1e-15)
+
+
+def test_pseudopotential_and_eos_limits():
+    g = GOLDEN["psi_limits"]
+    h = 1e-7
+    assert O.psi(h) / h == pytest.approx(g["small_rho_slope"], rel=1e-6)
+    assert O.psi(60.0) == pytest.approx(g["large_rho_value"], abs=1e-15)
+    # Eq. 29 at G = 0 is the ideal lattice gas p = rho cs2
+    assert O.pressure(1.7, G=0.0) == pytest.approx(1.7 / 3, rel=1e-15)
+
+
+def test_critical_point():
+    """Eqs. 31-32: p' = p'' = 0 at rho = ln 2 with G = -4 (printed after Eq. 34)."""
+    Gc = GOLDEN["G_critical"]["value"]
+    rc = GOLDEN["rho_critical"]["value"]
+    assert O.RHO_CRITICAL == pytest.approx(rc, abs=1e-16)
+    h = 1e-4
+    p = lambda r: O.pressure(r, Gc)
+    d1 = (p(rc + h) - p(rc - h)) / (2 * h)
+    d2 = (p(rc + h) - 2 * p(rc) + p(rc - h)) / h**2
+    assert abs(d1) < 1e-8 and abs(d2) < 1e-6
+    # just above the critical G the EOS is monotone; just below it is not
+    rr = np.linspace(0.05, 4.0, 2000)
+    assert np.all(np.diff([O.pressure(r, -3.9) for r in rr]) > 0)
+    assert np.any(np.diff([O.pressure(r, -4.2) for r in rr]) < 0)
+
+
+def test_spinodal_limits_closed_form():
+    """p'(rho) = 0 where exp(-rho) = (1 +- sqrt(1 + 4/G))/2 for psi = 1 - exp(-rho)."""
+    G = -5.5
+    lo = -math.log((1 + math.sqrt(1 + 4 / G)) / 2)
+    hi = -math.log((1 - math.sqrt(1 + 4 / G)) / 2)
+    h = 1e-6
+    for r in (lo, hi):
+        d1 = (O.pressure(r + h, G) - O.pressure(r - h, G)) / (2 * h)
+        assert abs(d1) < 1e-8
+    assert (O.pressure(1.0 + h, G) - O.pressure(1.0 - h, G)) < 0  # unstable inside
+    assert lo == pytest.approx(0.2730, abs=1e-4) and hi == pytest.approx(1.4317, abs=1e-4)
+
+
+# ----------------------------------------------------------------- force
+def test_force_stencil_closed_form_1d_and_2d():
+    """Eq. 22 on psi = sin(kx) sin(ly): the neighbour sum is
+    sin k cos kx sin ly (2 + cos l) / 9 exactly; its small-k limit has the
+    Taylor coefficients 1/3 and 1/18 of Eq. 23."""
+    nx, ny = 64, 48
+    P = O.make_params(nx, ny, G=-5.5)
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    k = 2 * np.pi * 3 / nx
+    for l in (0.0, 2 * np.pi * 2 / ny):
+        psi = np.sin(k * x) * (np.sin(l * y) if l else np.ones_like(y, dtype=float))
+        psi = np.ascontiguousarray(np.broadcast_to(psi, (ny, nx)))
+        Fx, Fy = O.force(P, psi)
+        sl = np.sin(l * y) if l else 1.0
+        expect = -P.G * psi * np.sin(k) * np.cos(k * x) * sl * (2 + np.cos(l)) / 9
+        assert np.max(np.abs(Fx - expect)) < 1e-14
+    # Taylor coefficients: (1/3) sin k = k/3 - k^3/18 + O(k^5)
+    c1, c3 = GOLDEN["taylor_coefficients"]["value"]
+    for kk in (0.05, 0.1):
+        assert math.sin(kk) / 3 == pytest.approx(c1 * kk - c3 * kk**3, abs=kk**5 / 300)
+
+
+def test_force_mask_substitutes_own_psi():
+    """A blocked edge replaces psi(x+e_i) by psi(x): with every edge blocked the
+    force vanishes; blocking only the +x edge of one cell changes only that
+    cell's force, by -G psi(x) w_1 (psi(x) - psi(x+e_1))."""
+    nx, ny = 8, 6
+    P = O.make_params(nx, ny, G=-5.0)
+    rng = np.random.default_rng(1)
+    psi = rng.uniform(0.1, 0.9, (ny, nx))
+    m = np.full((ny, nx), 0xFF, np.uint8)
+    Fx, Fy = O.force(P, psi, m)
+    assert np.max(np.abs(Fx)) < 1e-15 and np.max(np.abs(Fy)) < 1e-15
+    m = np.zeros((ny, nx), np.uint8)
+    m[2, 3] = 1 << 0  # direction 1 is bit 0
+    F0x, F0y = O.force(P, psi)
+    F1x, F1y = O.force(P, psi, m)
+    d = F1x - F0x
+    assert d[2, 3] == pytest.approx(-P.G * psi[2, 3] * (1 / 9) * (psi[2, 3] - psi[2, 4]), rel=1e-12)
+    d[2, 3] = 0
+    assert np.max(np.abs(d)) == 0 and np.max(np.abs(F1y - F0y)) == 0
+
+
+# ----------------------------------------------------------------- dynamics
+def test_rest_state_is_stationary():
+    P = O.make_params(24, 16, G=-5.5)
+    s = O.OracleSim(P)
+    s.init_density(np.full((16, 24), 0.7))
+    f0 = s.f.copy()
+    s.step(50)
+    assert np.max(np.abs(s.f - f0)) < 1e-15
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_shear_wave_decay_matches_viscosity(tau):
+    """G = 0: a shear wave u_y = U sin kx decays as exp(-nu k^2 t) with
+    nu = cs2 (tau - 1/2) (Eq. 17)."""
+    nx, ny = 64, 4
+    P = O.make_params(nx, ny, G=0.0, tau=tau)
+    s = O.OracleSim(P)
+    k = 2 * np.pi / nx
+    U = 1e-3
+    f = np.zeros((9, ny, nx))
+    for xx in range(nx):
+        f[:, :, xx] = O.equilibrium(1.0, 0.0, U * math.sin(k * xx))[:, None]
+    s.load_populations(f)
+
+    def amp():
+        uy = s.fields()["uy"][0]
+        return 2.0 / nx * np.sum(uy * np.sin(k * np.arange(nx)))
+
+    s.step(100)
+    a0 = amp()
+    s.step(1000)
+    a1 = amp()
+    nu = -math.log(a1 / a0) / (k * k * 1000)
+    assert nu == pytest.approx((tau - 0.5) / 3, rel=0.01)
+
+
+def test_mass_and_momentum_conservation_spinodal():
+    """Collision keeps sum f, streaming permutes: mass is conserved to
+    rounding. The pairwise force sums to zero on a periodic box, so the
+    momentum sum(j + F/2) is conserved too (barrier off)."""
+    rho = inputs.noise_density(128, 128, seed=1)
+    P = O.make_params(128, 128, G=-5.5)
+    s = O.OracleSim(P)
+    s.init_density(rho)
+    m0 = s.mass()
+    p0 = s.momentum()
+    s.step(2000)
+    assert abs(s.mass() - m0) / m0 < 1e-12
+    p1 = s.momentum()
+    assert abs(p1[0] - p0[0]) < 1e-12 * m0 and abs(p1[1] - p0[1]) < 1e-12 * m0
+
+
+def test_spinodal_separates_only_below_critical_G():
+    """rho = 0.7 lies inside the spinodal for G = -5.5 (phase separation),
+    and the EOS is monotone for G = -3.5 (noise decays)."""
+    rho = inputs.noise_density(128, 128, seed=2)
+    for G, separates in ((-5.5, True), (-3.5, False)):
+        s = O.OracleSim(O.make_params(128, 128, G=G))
+        s.init_density(rho)
+        s.step(2000)
+        r = s.fields()["rho"]
+        if separates:
+            assert r.min() < 0.2 and r.max() > 2.0
+        else:
+            assert np.max(np.abs(r - 0.7)) < 0.007
+
+
+def _coexistence(G, eps):
+    """Solve p(rg) = p(rl) and int (p - p0) psi'/psi^(1+eps) drho = 0
+    (Shan-Chen mechanical stability; eps = -1 is the classical equal-area
+    rule in the specific volume when psi = rho)."""
+    psi = lambda r: 1 - math.exp(-r)
+    dpsi = lambda r: math.exp(-r)
+    p = lambda r: r / 3 + G * psi(r) ** 2 / 6
+
+    def eqs(v):
+        rg, rl = v
+        p0 = p(rg)
+        if eps is None:  # classical Maxwell: int (p - p0) / r^2 dr = 0
+            I = integrate.quad(lambda r: (p(r) - p0) / r**2, rg, rl, limit=200)[0]
+        else:
+            I = integrate.quad(lambda r: (p(r) - p0) * dpsi(r) / psi(r) ** (1 + eps), rg, rl,
+                               limit=200)[0]
+        return [p(rl) - p0, I]
+
+    return optimize.fsolve(eqs, [0.1, 2.3], xtol=1e-13)
+
+
+def test_flat_interface_coexistence():
+    """A flat liquid slab relaxes to the densities of the eps = 1 Shan-Chen
+    construction within 1 %, and not to the classical Maxwell rule; the
+    input recipe's initial densities equal the relaxed slab's."""
+    nx, ny = 128, 4
+    P = O.make_params(nx, ny, G=-5.5)
+    s = O.OracleSim(P)
+    x = np.arange(nx)
+    prof = 1.2 - 1.1 * np.tanh((np.abs(x - nx / 2) - nx / 4) / 2.0)
+    s.init_density(np.ascontiguousarray(np.broadcast_to(prof, (ny, nx))))
+    for _ in range(40):
+        s.step(2000)
+        if np.max(np.abs(s.fields()["ux"])) < 1e-10:
+            break
+    r = s.fields()["rho"][0]
+    rl, rg = r[nx // 2], r[0]
+    sg1, sl1 = _coexistence(-5.5, 1)
+    sgM, slM = _coexistence(-5.5, None)
+    assert rg == pytest.approx(sg1, rel=0.01) and rl == pytest.approx(sl1, rel=0.01)
+    assert abs(rg - sgM) / sgM > 0.02  # the classical rule is distinguishable
+    assert inputs.RHO_GAS_G55 == pytest.approx(rg, rel=1e-4)
+    assert inputs.RHO_LIQ_G55 == pytest.approx(rl, rel=1e-4)
+
+
+def test_laplace_law_droplets():
+    """Static droplets: p_in - p_out is linear in 1/R with a near-zero
+    intercept (Laplace). Droplets are used because small gas bubbles in a
+    closed box at coexistence density dissolve."""
+    rl, rg = inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55
+    pts = []
+    for R, L in ((10, 96), (14, 96), (18, 128), (24, 128)):
+        P = O.make_params(L, L, G=-5.5)
+        s = O.OracleSim(P)
+        s.init_density(O.init_bubbles(P, [[L / 2, L / 2, R]], rg, rl, 4.0))  # liquid inside
+        s.step(4000)
+        fl = s.fields()
+        A = np.sum((fl["rho"] - rg) / (rl - rg))
+        yy, xx = np.mgrid[0:L, 0:L]
+        d = np.hypot(xx - L / 2, yy - L / 2)
+        p_in = fl["p"][d < R - 5].mean()
+        p_out = fl["p"][d > R + 10].mean()
+        pts.append((1 / math.sqrt(A / math.pi), p_in - p_out))
+    xs, dp = np.array(pts).T
+    slope, icpt = np.polyfit(xs, dp, 1)
+    fit = slope * xs + icpt
+    r2 = 1 - np.sum((dp - fit) ** 2) / np.sum((dp - dp.mean()) ** 2)
+    assert slope > 0 and r2 >= 0.999
+    assert abs(icpt) <= 0.05 * dp[0]
+
+
+# ----------------------------------------------------------------- barrier pipeline
+def _torus_components(gas):
+    ny, nx = gas.shape
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    rows, cols = [], []
+    for dy, dx in ((0, 1), (1, 0)):
+        nb = np.roll(np.roll(idx, -dy, 0), -dx, 1)
+        both = gas & np.roll(np.roll(gas, -dy, 0), -dx, 1)
+        rows += list(idx[both])
+        cols += list(nb[both])
+    g = coo_matrix((np.ones(len(rows)), (rows, cols)), shape=(nx * ny, nx * ny))
+    _, comp = connected_components(g, directed=False)
+    out = np.full(nx * ny, -1, np.int64)
+    flat = gas.ravel()
+    for c in np.unique(comp[flat]):
+        members = np.where((comp == c) & flat)[0]
+        out[members] = members.min()
+    return out.reshape(ny, nx)
+
+
+@pytest.mark.parametrize("shape,seed", [((8, 8), 3), ((12, 16), 4), ((12, 16), 5)])
+def test_labels_owner_mask_brute_force(shape, seed):
+    ny, nx = shape
+    rng = np.random.default_rng(seed)
+    gas = rng.random((ny, nx)) < 0.3
+    rho = np.where(gas, 0.1, 2.3)
+    R = 2
+    P = O.make_params(nx, ny, barrier=True, zone_radius=R)
+    lab = O.label(P, rho)
+    assert np.array_equal(lab, _torus_components(gas))
+    own = O.owner(P, lab)
+    gy, gx = np.nonzero(gas)
+    for y in range(ny):
+        for x in range(nx):
+            if gas[y, x]:
+                assert own[y, x] == lab[y, x]
+                continue
+            dx = np.abs(gx - x)
+            dy = np.abs(gy - y)
+            d2 = np.minimum(dx, nx - dx) ** 2 + np.minimum(dy, ny - dy) ** 2
+            ok = d2 <= R * R
+            if not ok.any():
+                assert own[y, x] == -1
+                continue
+            cand = sorted(zip(d2[ok], lab[gy[ok], gx[ok]]))
+            assert own[y, x] == cand[0][1]
+    op = (rng.random((ny, nx)) < 0.2).astype(np.uint8)
+    m = O.mask(P, own, op)
+    ex, ey, _ = O.lattice()
+    for y in range(ny):
+        for x in range(nx):
+            for i in range(1, 9):
+                yy, xx = (y + ey[i]) % ny, (x + ex[i]) % nx
+                want = (own[y, x] >= 0 and own[yy, xx] >= 0 and own[y, x] != own[yy, xx]
+                        and not op[y, x] and not op[yy, xx])
+                assert bool((m[y, x] >> (i - 1)) & 1) == want
+                assert bool((m[y, x] >> (i - 1)) & 1) == bool((m[yy, xx] >> (OPP[i] - 1)) & 1)
+
+
+def test_rupture_rule_on_hand_cases():
+    """Two zones meet between columns 3 and 4 (column 0 has no owner). On the
+    liquid branch p is increasing in rho (rho > 1.43 for G = -5.5), so with a
+    density dip in column 3, D2 > 0 at column 3 (normal +x) and D2 < 0 at
+    column 4 (normal -x, the first direction whose owner differs); a bump
+    flips both signs. The first evaluation stores the sign, a flip opens the
+    cell, eps >= |D2| opens it, eps < 0 never opens, and cells off the owner
+    change keep sign 0."""
+    nx, ny = 8, 4
+    own = np.zeros((ny, nx), np.int32)
+    own[:, 4:] = 1
+    own[:, 0] = -1
+    base = np.full((ny, nx), 2.3)
+    dip = base.copy()
+    dip[:, 3] = 2.2
+    bump = base.copy()
+    bump[:, 3] = 2.4
+    P = O.make_params(nx, ny, barrier=True, rupture_eps=1e-9)
+    sgn = np.zeros((ny, nx), np.int8)
+    op = np.zeros((ny, nx), np.uint8)
+    assert O.rupture(P, dip, own, sgn, op) == 0
+    assert np.all(sgn[:, 3] == 1) and np.all(sgn[:, 4] == -1) and np.all(op == 0)
+    assert np.all(sgn[:, [0, 1, 2, 5, 6, 7]] == 0)
+    assert O.rupture(P, bump, own, sgn, op) == 8 and np.all(op[:, 3:5] == 1)
+    assert np.all(sgn[:, 3] == -1) and np.all(sgn[:, 4] == 1)
+    # sticky: opened cells are not counted again
+    assert O.rupture(P, dip, own, sgn, op) == 0 and np.all(op[:, 3:5] == 1)
+    # |D2| <= eps opens every barrier cell and nothing else
+    P2 = O.make_params(nx, ny, barrier=True, rupture_eps=1e9)
+    s2 = np.zeros((ny, nx), np.int8)
+    o2 = np.zeros((ny, nx), np.uint8)
+    assert O.rupture(P2, dip, own, s2, o2) == 8
+    assert np.all(o2[:, 3:5] == 1) and np.all(o2[:, [0, 1, 2, 5, 6, 7]] == 0)
+    # a uniform liquid has D2 = 0 exactly at the barrier: it opens for eps >= 0
+    s4 = np.zeros((ny, nx), np.int8)
+    o4 = np.zeros((ny, nx), np.uint8)
+    assert O.rupture(P, base, own, s4, o4) == 8
+    # eps < 0 never opens, signs are still stored
+    P3 = O.make_params(nx, ny, barrier=True, rupture_eps=-1.0)
+    s3 = np.zeros((ny, nx), np.int8)
+    o3 = np.zeros((ny, nx), np.uint8)
+    O.rupture(P3, dip, own, s3, o3)
+    assert O.rupture(P3, bump, own, s3, o3) == 0 and np.all(o3 == 0) and np.all(s3[:, 3] == -1)
+
+
+TWO = dict(nx=160, ny=80, R=20)
+
+
+def _two_bubbles(gap, **kw):
+    nx, ny, R = TWO["nx"], TWO["ny"], TWO["R"]
+    b = [[nx / 2 - R - gap / 2, ny / 2, R], [nx / 2 + R + gap / 2, ny / 2, R]]
+    P = O.make_params(nx, ny, G=-5.5, **kw)
+    s = O.OracleSim(P)
+    s.init_density(O.init_bubbles(P, b, inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, 4.0))
+    return P, s
+
+
+def test_two_bubbles_plain_merge_and_zone_reduction():
+    """(i) plain Shan-Chen merges two R=20 bubbles at edge gap 3 within 1000
+    steps; (ii) with R_z = 3 the zones of bubbles 6 apart never meet, the mask
+    stays empty and the barrier run is bitwise the plain run."""
+    P, s = _two_bubbles(3.0)
+    assert O.stats(P, s.labels_now())["n_bubbles"] == 2
+    s.step(1000)
+    assert O.stats(P, s.labels_now())["n_bubbles"] == 1
+    _, a = _two_bubbles(6.0)
+    _, b = _two_bubbles(6.0, barrier=True, zone_radius=3)
+    a.step(300)
+    b.step(300)
+    assert np.array_equal(a.f, b.f) and not b.mask.any()
+    assert O.stats(a.params, a.labels_now())["n_bubbles"] == 2
+
+
+def test_two_bubbles_first_rupture_hand_check():
+    """Barrier on: the film between bubbles 3 apart carries a blocked-edge
+    line; at the first step where a cell opens, that cell sits on the owner
+    change, and D2 recomputed from the density at the start of that step
+    meets the criterion. With stop_on_first_rupture the run halts right after
+    that step; mass is conserved throughout."""
+    P, s = _two_bubbles(3.0, barrier=True)
+    m0 = s.mass()
+    ex, ey, _ = O.lattice()
+    G = P.G
+    p = lambda r: r / 3 + G * (1 - np.exp(-r)) ** 2 / 6
+    sgn_prev = s.sgn.copy()
+    for t in range(400):
+        f_before = s.f.copy()
+        sgn_prev = s.sgn.copy()
+        open_prev = s.open.copy()
+        s.step(1)
+        if s.mask.any():
+            m = s.mask
+            for i in range(1, 9):
+                assert np.array_equal((m >> (i - 1)) & 1, (np.roll(np.roll(m, -ey[i], 0), -ex[i], 1) >> (OPP[i] - 1)) & 1)
+        new = np.argwhere((s.open == 1) & (open_prev == 0))
+        if len(new):
+            rho = f_before.sum(0)
+            for y, x in new[:5]:
+                own = s.owner
+                o = own[y, x]
+                dirs = [i for i in range(1, 9)
+                        if own[(y + ey[i]) % P.ny, (x + ex[i]) % P.nx] >= 0
+                        and own[(y + ey[i]) % P.ny, (x + ex[i]) % P.nx] != o]
+                assert o >= 0 and dirs
+                i = dirs[0]
+                d2 = (p(rho[(y + ey[i]) % P.ny, (x + ex[i]) % P.nx]) - 2 * p(rho[y, x])
+                      + p(rho[(y - ey[i]) % P.ny, (x - ex[i]) % P.nx]))
+                sgn = int(np.sign(d2))
+                assert abs(d2) <= P.rupture_eps or (sgn_prev[y, x] != 0 and sgn != sgn_prev[y, x])
+            break
+    else:
+        pytest.fail("no cell opened within 400 steps")
+    t_open = s.t
+    assert abs(s.mass() - m0) / m0 < 1e-12
+    # the same run with the stop flag halts right after the rupture step
+    P2, s2 = _two_bubbles(3.0, barrier=True, stop_on_first_rupture=True)
+    done = s2.step(1000)
+    assert done == t_open and s2.halted
+
+
+def test_step_cells_matches_full_step():
+    rho = inputs.noise_density(32, 24, seed=7)
+    P = O.make_params(32, 24, G=-5.5)
+    s = O.OracleSim(P)
+    s.init_density(rho)
+    s.step(300)  # some structure
+    f0 = s.f.copy()
+    rng = np.random.default_rng(0)
+    m = (rng.random((24, 32)) < 0.1).astype(np.uint8) * 0  # plain: no mask
+    cells = rng.choice(32 * 24, 50, replace=False)
+    out = O.step_cells(P, f0, cells, m)
+    s.step(1)
+    full = s.f.reshape(9, -1)[:, cells].T
+    assert np.max(np.abs(out - full)) < 1e-15
+
+
+def test_init_bubbles_profile():
+    P = O.make_params(64, 64)
+    r = O.init_bubbles(P, [[32.0, 32.0, 10.0]], 2.3, 0.1, 4.0)
+    assert r[32, 32] == pytest.approx(1.2 - 1.1 * math.tanh(5.0), abs=1e-14)
+    assert r[32, 42] == pytest.approx(1.2, abs=1e-14)  # on the surface
+    assert r[0, 0] == pytest.approx(1.2 + 1.1 * math.tanh((math.hypot(32, 32) - 10) / 2), abs=1e-14)
+    # periodic: a bubble at the corner appears on all four corners
+    r2 = O.init_bubbles(P, [[0.0, 0.0, 5.0]], 2.3, 0.1, 4.0)
+    assert r2[0, 63] == pytest.approx(r2[0, 1], abs=1e-14) and r2[63, 0] == pytest.approx(r2[1, 0], abs=1e-14)
+
+
+def test_stats_hand_case():
+    P = O.make_params(8, 8)
+    lab = np.full((8, 8), -1, np.int32)
+    lab[0, 0:2] = 0          # area 2
+    lab[3:6, 3:6] = 27       # area 9
+    st = O.stats(P, lab, nbins=4, dmin=1.0, dmax=16.0)
+    assert st["n_bubbles"] == 2 and st["gas_fraction"] == pytest.approx(11 / 64)
+    d = [2 * math.sqrt(2 / math.pi), 2 * math.sqrt(9 / math.pi)]
+    assert np.allclose(st["diameters"], d) and st["mean_diameter"] == pytest.approx(sum(d) / 2)
+    # log bins [1,2),[2,4),[4,8),[8,16): 1.596 -> bin 0, 3.385 -> bin 1
+    assert list(st["hist"]) == [1, 1, 0, 0]
+
+
+def test_inputs_are_seeded_and_independent_of_order():
+    a = inputs.noise_density(16, 8, seed=1)
+    b = inputs.noise_density(16, 8, seed=1)
+    c = inputs.noise_density(16, 8, seed=2)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    assert np.all(np.abs(a / 0.7 - 1) <= 0.01)
+    u = inputs.splitmix64_uniform(123, np.arange(5))
+    assert np.array_equal(u[3:], inputs.splitmix64_uniform(123, np.arange(3, 5)))
+    bub = inputs.poisson_disk_bubbles(512, 512, 40, 8, 64, 2.0, seed=21)
+    for i in range(len(bub)):
+        for j in range(i):
+            dx = abs(bub[i, 0] - bub[j, 0]); dx = min(dx, 512 - dx)
+            dy = abs(bub[i, 1] - bub[j, 1]); dy = min(dy, 512 - dy)
+            assert math.hypot(dx, dy) - bub[i, 2] - bub[j, 2] >= 2.0
