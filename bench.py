@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the extended Shan-Chen LB time step on GB300.
+
+Default workload (one GPU): an 8192 x 8192 periodic D2Q9 box with 400
+Poisson-disk gas bubbles (radii 8-64, log-uniform, edge gap >= 2), G = -5.5,
+tau = 1, psi = 1 - exp(-rho), film barrier on (R_z = 4, relabel every
+K = 10 steps). A "step" is one full time step of the method: the barrier
+pipeline when due, then the fused pull-stream/force/collide kernel.
+
+Prints one JSON line. `value` is whole-job MLUPS (FP32 storage) with the
+state resident in HBM; the FP16-deviation-storage run and the every-step
+barrier variant are reported beside it. `roofline` relates the fused step
+kernel's algorithmic bytes (9 population reads + 9 writes + 1 mask byte per
+cell) to the measured HBM copy bandwidth. `cpu_baseline` is the FP64 oracle
+timed on the host cores on a bounded sample. `e2e` runs whole jobs through
+the public C ABI from pinned host memory (density in, density out).
+
+Multi-GPU: the path is run as independent replicas (one box per rank, no
+collective in the data path); `value` sums all ranks' cell updates over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM roofline fraction (FP32 vs FP16-store) at 8192^2; served p50/p99"
+WORKLOADS = {
+    "c3": dict(n=8192, bubbles=400, rmin=8.0, rmax=64.0, seed=21,
+               desc="8192^2 periodic D2Q9, 400 Poisson-disk bubbles r 8-64 log-uniform (gap>=2), "
+                    "G=-5.5, tau=1, psi=1-exp(-rho), film barrier on (R_z=4)"),
+    "small": dict(n=2048, bubbles=25, rmin=8.0, rmax=64.0, seed=21,
+                  desc="2048^2 periodic D2Q9, 25 Poisson-disk bubbles r 8-64 (profiling case)"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3")
+    ap.add_argument("--relabel-every", type=int, default=10)
+    ap.add_argument("--storage", choices=["f32", "f16", "both"], default="both")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-k1", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(storage: str):
+    """DRAM bytes per launch of the fused step from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = open(os.path.join(ROOT, "paper_1708_01613_gb300", "csrc", "step.cu"), "rb").read()
+    if d.get("step_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    v = d.get(storage, {}).get("bytes_per_launch_full")
+    return float(v) if v else None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float, device=None) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1708_01613_gb300 import Simulation, make_config
+    from paper_1708_01613_gb300 import lbm as L
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    N = n * n
+    bub = inputs.poisson_disk_bubbles(n, n, wl["bubbles"], wl["rmin"], wl["rmax"], 2.0,
+                                      seed=wl["seed"] + 1000 * rank)
+    RL, RG = inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55
+    peak, peak_kind = measured_peaks()
+    K = args.relabel_every
+
+    def timed(storage: str, relabel_every: int, steps: int, warmup: int, sample_clocks: bool):
+        sim = Simulation(make_config(n, n, storage=storage, barrier=True, relabel_every=relabel_every,
+                                     rho_ref=RL), device=dev)
+        sim.init_bubbles(bub, RL, RG, 4.0)
+        sim.step(warmup)
+        sim.sync()
+        stream = sim.stream
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        launches0 = sim.kernel_launches
+        t_first = sim.steps_done
+        t_all0.record(stream)
+        for k in range(steps):
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        clocks = sampler.stop() if sampler else None
+        launches = sim.kernel_launches - launches0
+        sim.sync()  # raises on a device-side numeric fault
+        total_ms = t_all0.elapsed_time(t_all1)
+        per = [a.elapsed_time(b) for a, b in ev]
+        plain = [d for k, d in enumerate(per) if (t_first + k) % relabel_every != 0]
+        relab = [d for k, d in enumerate(per) if (t_first + k) % relabel_every == 0]
+        st = sim.stats()
+        del sim
+        torch.cuda.empty_cache()
+        return dict(total_ms=total_ms, per=per, plain=plain, relab=relab, launches=launches,
+                    clocks=clocks, stats=st)
+
+    def roofline(storage, r):
+        eb = 4 if storage == "f32" else 2
+        bytes_cell = 2 * 9 * eb + 1
+        kern_ms = statistics.mean(r["plain"]) if r["plain"] else r["total_ms"] / args.steps
+        achieved = bytes_cell * N / (kern_ms * 1e-3) / 1e9
+        traffic = kernel_traffic(storage)
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else peak_kind,
+                "algorithmic_bytes_per_cell": bytes_cell, "kernel": "k_step_strip",
+                "kernel_ms_avg": round(kern_ms, 5),
+                "kernel_mlups": round(N / (kern_ms * 1e-3) / 1e6, 1),
+                "roofline_mlups": round(peak * 1e9 / bytes_cell / 1e6, 1)}
+
+    results = {}
+    storages = ["f32", "f16"] if args.storage == "both" else [args.storage]
+    for s in storages:
+        results[s] = timed(s, K, args.steps, args.warmup, sample_clocks=(s == storages[0]))
+    primary = storages[0]
+    r0 = results[primary]
+    tmax = max_over_ranks(world, r0["total_ms"], dev)
+    value = world * N * args.steps / (tmax * 1e-3) / 1e6
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tmax / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if primary == "f32" else "f16-storage/f32-math", "data": "synthetic",
+        "config": {"workload": wl["desc"], "cells": N, "storage": primary, "relabel_every": K,
+                   "zone_radius": 4, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "no flush: the resident state (>= 2.4 GB) is far larger than L2",
+                   "per_rank_seed_offset": 1000},
+        "roofline": roofline(primary, r0),
+        "gpu_launches": int(r0["launches"]),
+        "clocks": r0["clocks"],
+        "relabel_ms_avg": round(statistics.mean(r0["relab"]) - statistics.mean(r0["plain"]), 4)
+        if r0["relab"] and r0["plain"] else None,
+        "bubbles_after": {"n": r0["stats"]["n_bubbles"], "gas_fraction": r0["stats"]["gas_fraction"]},
+    }
+    for s in storages[1:]:
+        r = results[s]
+        t = max_over_ranks(world, r["total_ms"], dev)
+        out[s] = {"value": round(world * N * args.steps / (t * 1e-3) / 1e6, 1),
+                  "ms_per_step": round(t / args.steps, 5), "roofline": roofline(s, r),
+                  "gpu_launches": int(r["launches"])}
+    if not args.no_k1:
+        ksteps = max(5, min(args.steps, 20))
+        r = timed(primary, 1, ksteps, min(args.warmup, 3), sample_clocks=False)
+        t = max_over_ranks(world, r["total_ms"], dev)
+        out["barrier_every_step"] = {"value": round(world * N * ksteps / (t * 1e-3) / 1e6, 1),
+                                     "ms_per_step": round(t / ksteps, 5), "steps": ksteps,
+                                     "relabel_every": 1}
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, dev, n, bub, RL, RG, world)
+    return out
+
+
+def run_e2e(args, dev, n, bub, RL, RG, world):
+    """Whole jobs through the C ABI from pinned host memory: density in
+    (FP64), `job_steps` steps, density out (FP32), synchronised."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1708_01613_gb300 import lbm as L
+
+    N = n * n
+    job_steps = 100
+    lib = L.load_library()
+    cfg = L.make_config(n, n, storage="f32", barrier=True, relabel_every=args.relabel_every, rho_ref=RL)
+    nbytes = L.lbm_workspace_bytes(cfg)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = C.c_void_p()
+    L._check(lib.lbm_create(C.byref(cfg), C.c_void_p((ws.data_ptr() + 255) // 256 * 256), nbytes,
+                            C.c_void_p(stream.cuda_stream), C.byref(h)))
+    rho_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    out_host = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    # the initial density of the job (made once on the host, outside the timing)
+    sim_tmp = L.Simulation(cfg, device=dev)
+    sim_tmp.init_bubbles(bub, RL, RG, 4.0)
+    r = sim_tmp.read("rho")["rho"].astype(np.float64).ravel()
+    rho_host.copy_(torch.from_numpy(r))
+    del sim_tmp
+    torch.cuda.empty_cache()
+
+    def job():
+        L._check(lib.lbm_init_density(h, C.c_void_p(rho_host.data_ptr()), 0), h)
+        L._check(lib.lbm_step(h, job_steps), h)
+        L._check(lib.lbm_read_fields(h, L.FIELD_RHO, C.c_void_p(out_host.data_ptr()), 4 * N, 0), h)
+
+    job()
+    iters = 3
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        job()
+    t1 = time.perf_counter()
+    barrier(world)
+    lib.lbm_destroy(h)
+    dt = max_over_ranks(world, t1 - t0, dev)
+    return {"value": round(world * N * job_steps * iters / dt / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 4 * N,
+            "job": f"init_density(host FP64) + {job_steps} steps + read_fields(RHO, host)",
+            "steps_per_job": job_steps, "jobs": iters}
+
+
+# ----------------------------------------------------------------- oracle (CPU)
+def cpu_sample(steps: int, warmup: int, budget_s: float | None):
+    """The FP64 oracle on a 512^2 box with the benchmark's bubble density
+    (bubbles per area of the 8192^2 workload, about 1.6 per 512^2: 2 here),
+    barrier on, K = 10."""
+    import inputs
+    import oracle as O
+
+    n = 512
+    bub = inputs.poisson_disk_bubbles(n, n, 2, 8.0, 64.0, 2.0, seed=21)
+    P = O.make_params(n, n, barrier=True, relabel_every=10)
+    s = O.OracleSim(P)
+    s.init_density(O.init_bubbles(P, bub, inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, 4.0))
+    s.step(warmup)
+    if budget_s is not None:
+        t0 = time.perf_counter()
+        s.step(2)
+        per = (time.perf_counter() - t0) / 2
+        steps = max(2, int(budget_s / per))
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt / 1e6, steps, dt, O.max_threads()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        mlups, steps, dt, cores = cpu_sample(args.steps, args.warmup, None)
+        out = {"metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / steps * 1e3, 3),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "impl": "reference",
+               "config": {"workload": WORKLOADS[args.workload]["desc"],
+                          "sample": "512^2 box at the workload's bubble density, barrier on, K=10"},
+               "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{steps} steps of a 512^2 box (FP64 oracle, OpenMP)"},
+               "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+    out = run_gpu(args, world, rank, local)
+    if rank == 0 and not args.no_cpu:
+        mlups, steps, dt, cores = cpu_sample(0, 2, budget_s=12.0)
+        out["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                               "sample": f"{steps} steps of a 512^2 box at the workload's bubble density, "
+                                         f"barrier on, K=10 ({dt:.1f} s, FP64 oracle, OpenMP)"}
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

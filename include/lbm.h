@@ -1,0 +1,185 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) library for the time step of the
+ * extended Shan-Chen lattice Boltzmann method for metal-foam bubbles
+ * (Barzegari, Bayani, Mirbagheri & Shetabivash, arXiv 1708.01613).
+ *
+ * One handle advances one periodic D2Q9 box on one GPU. Per step it runs:
+ * pull streaming (Sec. 2.1.1, Eq. 19), moments (Eq. 11), pseudopotential
+ * psi = rho0 (1 - exp(-rho/rho0)) (Sec. 2.1.2, Eq. 30), the neighbour-sum
+ * Shan-Chen force (Eq. 22) with the film-barrier mask, the velocity-shift
+ * equilibrium u_eq = (j + tau F)/rho (Sec. 2.1.5, Eqs. 39-40; Eq. 14) and
+ * BGK collision (Eq. 18). Every K steps it runs the film-barrier pipeline of
+ * Sec. 2.1.5: gas labelling, nearest-bubble interaction zones, the
+ * d2p/dn2 = 0 rupture test (Eq. 41) and the blocked-edge mask.
+ *
+ * Conventions
+ *  - Box: nx by ny cells, periodic on all sides, row-major, x fastest.
+ *  - Directions: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1)
+ *    7:(-1,-1) 8:(1,-1); weights 4/9, 1/9 (1-4), 1/36 (5-8) (Eqs. 15-16).
+ *  - Memory: the caller owns ALL device memory. lbm_create takes one
+ *    caller-allocated device workspace of lbm_workspace_bytes() bytes
+ *    (aligned to 256 bytes) and never allocates device memory itself. The
+ *    handle owns only host state and must not outlive the workspace.
+ *  - Streams: every call enqueues its work on the stream given to
+ *    lbm_create (NULL = legacy default stream). lbm_step is asynchronous.
+ *    lbm_read_fields, lbm_mass, lbm_bubble_stats, lbm_sync and a step with
+ *    stop_on_first_rupture synchronise that stream.
+ *  - Errors: every int-returning call returns an lbm_status; the library
+ *    never aborts and never prints. lbm_last_error gives a message for the
+ *    last failing call on that handle. A handle is not thread-safe.
+ *  - Numeric faults (NaN/Inf or rho <= 0 met by the step kernel) are
+ *    recorded on the device and reported as LBM_ENUMERIC by the next
+ *    synchronising call.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,   /* bad config or argument */
+  LBM_ENOMEM = 2,   /* workspace too small */
+  LBM_ECUDA = 3,    /* a CUDA runtime call failed */
+  LBM_ENUMERIC = 4, /* NaN/Inf or rho <= 0 seen on the device */
+  LBM_ETIMEOUT = 5, /* a bounded device loop gave up */
+  LBM_ENOTSUP = 6   /* unsupported request */
+} lbm_status;
+
+/* Population storage. F32: f_i as float. F16_DEV / BF16_DEV: the deviation
+ * g_i = f_i - w_i rho_ref as IEEE half / bfloat16 (round to nearest even);
+ * all arithmetic is FP32 in every mode. */
+typedef enum { LBM_F32 = 0, LBM_F16_DEV = 1, LBM_BF16_DEV = 2 } lbm_storage;
+
+/* Field selectors for lbm_read_fields / lbm_fields_bytes. Selected fields are
+ * written back to back in increasing bit order, each as a full [ny][nx]
+ * array (POPS: [9][ny][nx]). */
+enum {
+  LBM_FIELD_RHO = 1u << 0,   /* float32: rho = sum f_i (Eq. 11) */
+  LBM_FIELD_UX = 1u << 1,    /* float32: (j_x + F_x / 2) / rho */
+  LBM_FIELD_UY = 1u << 2,    /* float32: (j_y + F_y / 2) / rho */
+  LBM_FIELD_P = 1u << 3,     /* float32: p = rho/3 + G psi^2 / 6 (Eq. 29) */
+  LBM_FIELD_LABEL = 1u << 4, /* int32: bubble label (min row-major index) or -1 */
+  LBM_FIELD_OWNER = 1u << 5, /* int32: interaction-zone owner or -1 (barrier on) */
+  LBM_FIELD_MASK = 1u << 6,  /* uint8: bit i-1 set = edge (x, x+e_i) blocked */
+  LBM_FIELD_OPEN = 1u << 7,  /* uint8: 1 = cell has ruptured (barrier on) */
+  LBM_FIELD_POPS = 1u << 8   /* float32 [9][ny][nx]: incoming f_i of the next step */
+};
+
+typedef struct {
+  int32_t nx, ny;                /* box size, each >= 4 */
+  int32_t storage;               /* lbm_storage */
+  int32_t barrier;               /* 0: plain Shan-Chen; 1: film barrier + rupture */
+  int32_t relabel_every;         /* K >= 1: barrier pipeline every K steps */
+  int32_t zone_radius;           /* R_z >= 0; with the barrier on, nx, ny > 2 R_z + 1 */
+  int32_t stop_on_first_rupture; /* 1: lbm_step stops after the step whose
+                                    relabel first opened a cell (Sec. 2.1.4
+                                    flowchart; Sec. 5 "best foaming time") */
+  int32_t reserved;              /* must be 0 */
+  double tau;                    /* BGK relaxation time > 0.5 */
+  double G;                      /* Shan-Chen coupling (Eq. 22) */
+  double rho0;                   /* psi scale, psi = rho0 (1 - exp(-rho/rho0)) */
+  double rho_ref;                /* reference density of 16-bit deviations */
+  double gas_threshold;          /* gas iff rho < this (default ln 2) */
+  double rupture_eps;            /* open when |D2| <= eps; eps < 0: never */
+} lbm_config;
+
+typedef struct {
+  double cx, cy, r; /* centre (cell units, cell x at coordinate x) and radius */
+} lbm_bubble;
+
+typedef struct {
+  int64_t step;            /* steps done */
+  int32_t n_bubbles;       /* gas components of the current density */
+  int32_t reserved;
+  int64_t n_open;          /* cells opened so far (barrier on) */
+  double gas_fraction;     /* gas cells / all cells */
+  double mean_eq_diameter; /* mean of 2 sqrt(A / pi) over bubbles */
+  double mass;             /* FP64 sum of rho */
+} lbm_stats;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Defaults: 256x256, F32, tau 1, G -5.5, rho0 1, rho_ref 1, barrier off,
+ * K 1, R_z 4, gas threshold ln 2, eps 1e-6. */
+void lbm_config_default(lbm_config* cfg);
+
+/* Device bytes lbm_create needs for cfg (0 if cfg is invalid). */
+size_t lbm_workspace_bytes(const lbm_config* cfg);
+
+/* Validates cfg and binds the caller's device workspace (>= the size above,
+ * 256-byte aligned) and CUDA stream (a cudaStream_t, may be NULL). The
+ * current CUDA device must be the workspace's. On success *out is a new
+ * handle; the populations are undefined until an init call. */
+int lbm_create(const lbm_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
+               lbm_handle** out);
+
+/* f_i = f_i^eq(rho, 0) = w_i rho from nx*ny FP64 densities (row-major),
+ * read from host memory (src_is_device = 0) or device memory (1). Resets the
+ * step counter, the rupture state and the error flags. */
+int lbm_init_density(lbm_handle* h, const double* rho, int src_is_device);
+
+/* Same as lbm_init_density with rho made on the device from n bubbles
+ * (host array): each cell takes the bubble whose surface is nearest,
+ * s = min_k (|x - c_k|_torus - r_k), and
+ * rho = (rho_l + rho_g)/2 + (rho_l - rho_g)/2 tanh(s / (width / 2)),
+ * computed in FP64. n = 0 gives a uniform liquid. */
+int lbm_init_bubbles(lbm_handle* h, const lbm_bubble* b, int32_t n, double rho_l, double rho_g,
+                     double width);
+
+/* Loads incoming populations f[9][ny][nx] (float32, host or device) as the
+ * state of the next step (bitwise resume for F32 storage). */
+int lbm_load_populations(lbm_handle* h, const float* f, int src_is_device);
+
+/* Enqueues nsteps time steps (each: barrier pipeline when t % K == 0, then
+ * the fused step). With stop_on_first_rupture it synchronises after each
+ * relabel and stops after the step whose relabel opened the first cell;
+ * lbm_steps_done tells how many steps ran. */
+int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Kernels this handle has launched since lbm_create (host-side count). */
+int64_t lbm_kernel_launches(const lbm_handle* h);
+
+/* Steps done since the last init/load. */
+int64_t lbm_steps_done(const lbm_handle* h);
+
+/* 1 once a stop_on_first_rupture run has stopped, else 0. */
+int lbm_halted(const lbm_handle* h);
+
+/* Bytes lbm_read_fields writes for the selection `fields`. */
+size_t lbm_fields_bytes(const lbm_handle* h, uint32_t fields);
+
+/* Writes the selected fields of the current state to dst (host or device,
+ * dst_bytes >= lbm_fields_bytes). LABEL is recomputed from the current
+ * density; OWNER/MASK/OPEN are those of the last relabel. Synchronises. */
+int lbm_read_fields(lbm_handle* h, uint32_t fields, void* dst, size_t dst_bytes,
+                    int dst_is_device);
+
+/* FP64 sum of rho over the box, reduced in a fixed order. Synchronises. */
+int lbm_mass(lbm_handle* h, double* out);
+
+/* Bubble statistics of the current density (labels recomputed) and, if
+ * hist != NULL, a histogram of equivalent diameters on nbins logarithmic
+ * bins over [dmin, dmax) (outliers clamped to the end bins). Synchronises. */
+int lbm_bubble_stats(lbm_handle* h, lbm_stats* out, double* hist, int32_t nbins, double dmin,
+                     double dmax);
+
+/* Synchronises the stream and reports device-side faults. */
+int lbm_sync(lbm_handle* h);
+
+/* Message of the last failing call on h ("" if none). */
+const char* lbm_last_error(const lbm_handle* h);
+
+/* Frees the host handle (not the workspace). NULL is allowed. */
+void lbm_destroy(lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

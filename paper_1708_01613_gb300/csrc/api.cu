@@ -1,0 +1,512 @@
+// C ABI of liblbm (declared in include/lbm.h): configuration checks,
+// workspace layout, and the host driver of the time loop of the extended
+// Shan-Chen method (arXiv 1708.01613, Sec. 2.1.4 main flowchart: barrier
+// pipeline when due, then collide+stream with the modified force).
+//
+// The library never allocates device memory: every device buffer is a slice
+// of the caller's workspace. The population buffer that is idle between
+// steps doubles as staging space for host transfers and as scratch for the
+// statistics.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t pops[2], rho, label, owner, mask, open, sgn, flags, partials, scalars, total;
+  int nparts;
+};
+
+bool valid_config(const lbm_config* c, char* why, size_t n) {
+  if (!c) return snprintf(why, n, "config is NULL"), false;
+  if (c->nx < 4 || c->ny < 4) return snprintf(why, n, "nx, ny must be >= 4"), false;
+  if ((long long)c->nx * c->ny > 0x7fffffffLL)
+    return snprintf(why, n, "nx * ny must fit in int32"), false;
+  if (c->storage < LBM_F32 || c->storage > LBM_BF16_DEV) return snprintf(why, n, "bad storage"), false;
+  if (c->barrier != 0 && c->barrier != 1) return snprintf(why, n, "barrier must be 0 or 1"), false;
+  if (c->relabel_every < 1) return snprintf(why, n, "relabel_every must be >= 1"), false;
+  if (c->zone_radius < 0) return snprintf(why, n, "zone_radius must be >= 0"), false;
+  if (c->barrier && (2 * c->zone_radius + 1 >= c->nx || 2 * c->zone_radius + 1 >= c->ny))
+    return snprintf(why, n, "with the barrier on, 2 zone_radius + 1 < nx, ny"), false;
+  if (c->stop_on_first_rupture != 0 && c->stop_on_first_rupture != 1)
+    return snprintf(why, n, "stop_on_first_rupture must be 0 or 1"), false;
+  if (c->reserved != 0) return snprintf(why, n, "reserved must be 0"), false;
+  if (!(c->tau > 0.5) || !isfinite(c->tau)) return snprintf(why, n, "tau must be > 0.5"), false;
+  if (!isfinite(c->G)) return snprintf(why, n, "G must be finite"), false;
+  if (!(c->rho0 > 0.0) || !isfinite(c->rho0)) return snprintf(why, n, "rho0 must be > 0"), false;
+  if (!isfinite(c->rho_ref) || !isfinite(c->gas_threshold) || !isfinite(c->rupture_eps))
+    return snprintf(why, n, "rho_ref, gas_threshold, rupture_eps must be finite"), false;
+  return true;
+}
+
+Layout layout_for(const lbm_config& c) {
+  Layout L{};
+  const size_t N = (size_t)c.nx * c.ny;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t eb = (size_t)storage_bytes(c.storage);
+  L.pops[0] = take(Q * N * eb);
+  L.pops[1] = take(Q * N * eb);
+  L.rho = take(4 * N);
+  L.label = take(4 * N);
+  if (c.barrier) {
+    L.owner = take(4 * N);
+    L.mask = take(N);
+    L.open = take(N);
+    L.sgn = take(N);
+  }
+  L.flags = take(sizeof(int) * FLAG_COUNT);
+  L.nparts = mass_partials_needed();
+  L.partials = take(sizeof(double) * L.nparts);
+  L.scalars = take(sizeof(double) * 16);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct lbm_handle {
+  lbm_config cfg;
+  Layout L;
+  char* ws;
+  cudaStream_t stream;
+  int device;
+  int cur;
+  int64_t t;
+  int64_t launches;
+  int halted;
+  float wref[Q];
+  char err[320];
+
+  void* pops(int k) { return ws + L.pops[k]; }
+  float* rho() { return reinterpret_cast<float*>(ws + L.rho); }
+  int32_t* label() { return reinterpret_cast<int32_t*>(ws + L.label); }
+  int32_t* owner() { return cfg.barrier ? reinterpret_cast<int32_t*>(ws + L.owner) : nullptr; }
+  uint8_t* mask() { return cfg.barrier ? reinterpret_cast<uint8_t*>(ws + L.mask) : nullptr; }
+  uint8_t* open() { return cfg.barrier ? reinterpret_cast<uint8_t*>(ws + L.open) : nullptr; }
+  int8_t* sgn() { return cfg.barrier ? reinterpret_cast<int8_t*>(ws + L.sgn) : nullptr; }
+  int* flags() { return reinterpret_cast<int*>(ws + L.flags); }
+  double* partials() { return reinterpret_cast<double*>(ws + L.partials); }
+  double* scalars() { return reinterpret_cast<double*>(ws + L.scalars); }
+  size_t N() const { return (size_t)cfg.nx * cfg.ny; }
+  size_t pops_bytes() const { return Q * N() * storage_bytes(cfg.storage); }
+};
+
+namespace {
+
+int fail(lbm_handle* h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CUDA_TRY(h, expr)                                                               \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail((h), LBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));             \
+  } while (0)
+
+FieldParams field_params(lbm_handle* h) {
+  FieldParams fp{};
+  fp.pops = h->pops(h->cur);
+  fp.storage = h->cfg.storage;
+  fp.nx = h->cfg.nx;
+  fp.ny = h->cfg.ny;
+  fp.N = (long long)h->N();
+  fp.G = (float)h->cfg.G;
+  fp.rho0 = (float)h->cfg.rho0;
+  fp.inv_rho0 = (float)(1.0 / h->cfg.rho0);
+  fp.tau = (float)h->cfg.tau;
+  for (int i = 0; i < Q; ++i) fp.wref[i] = h->wref[i];
+  return fp;
+}
+
+int select_device(lbm_handle* h) {
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  return LBM_OK;
+}
+
+int check_flags(lbm_handle* h) {
+  int f[3] = {0, 0, 0};
+  CUDA_TRY(h, cudaMemcpyAsync(f, h->flags(), sizeof(f), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (f[FLAG_NUMERIC]) return fail(h, LBM_ENUMERIC, "NaN/Inf or rho <= 0 met by the step kernel");
+  if (f[FLAG_TIMEOUT]) return fail(h, LBM_ETIMEOUT, "a bounded labelling loop gave up");
+  return LBM_OK;
+}
+
+int reset_state(lbm_handle* h) {
+  CUDA_TRY(h, cudaMemsetAsync(h->flags(), 0, sizeof(int) * FLAG_COUNT, h->stream));
+  if (h->cfg.barrier) {
+    CUDA_TRY(h, cudaMemsetAsync(h->mask(), 0, h->N(), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->open(), 0, h->N(), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->sgn(), 0, h->N(), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->owner(), 0xff, 4 * h->N(), h->stream));
+  }
+  h->t = 0;
+  h->halted = 0;
+  return LBM_OK;
+}
+
+// Barrier pipeline on the current populations (Sec. 2.1.5).
+int relabel(lbm_handle* h) {
+  const FieldParams fp = field_params(h);
+  const lbm_config& c = h->cfg;
+  CUDA_TRY(h, launch_density(fp, h->rho(), h->stream));
+  CUDA_TRY(h, launch_labels(fp, h->rho(), (float)c.gas_threshold, h->label(), h->flags(), h->stream));
+  CUDA_TRY(h, launch_owner(c.nx, c.ny, c.zone_radius, h->label(), h->owner(), h->stream));
+  CUDA_TRY(h, launch_rupture(c.nx, c.ny, (float)c.G, (float)c.rho0, (float)c.rupture_eps, h->rho(),
+                             h->owner(), h->sgn(), h->open(), h->flags(), h->stream));
+  CUDA_TRY(h, launch_mask(c.nx, c.ny, h->owner(), h->open(), h->mask(), h->stream));
+  h->launches += 7;
+  return LBM_OK;
+}
+
+int read_opened(lbm_handle* h, int* out) {
+  CUDA_TRY(h, cudaMemcpyAsync(out, h->flags() + FLAG_OPENED, sizeof(int), cudaMemcpyDeviceToHost,
+                              h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+size_t field_bytes(const lbm_handle* h, uint32_t bit) {
+  const size_t N = h->N();
+  switch (bit) {
+    case LBM_FIELD_RHO:
+    case LBM_FIELD_UX:
+    case LBM_FIELD_UY:
+    case LBM_FIELD_P:
+    case LBM_FIELD_LABEL:
+    case LBM_FIELD_OWNER: return 4 * N;
+    case LBM_FIELD_MASK:
+    case LBM_FIELD_OPEN: return N;
+    case LBM_FIELD_POPS: return 4 * Q * N;
+    default: return 0;
+  }
+}
+
+constexpr uint32_t kAllFields = (LBM_FIELD_POPS << 1) - 1;
+
+}  // namespace
+
+extern "C" {
+
+void lbm_config_default(lbm_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->nx = 256;
+  cfg->ny = 256;
+  cfg->storage = LBM_F32;
+  cfg->barrier = 0;
+  cfg->relabel_every = 1;
+  cfg->zone_radius = 4;
+  cfg->stop_on_first_rupture = 0;
+  cfg->tau = 1.0;
+  cfg->G = -5.5;
+  cfg->rho0 = 1.0;
+  cfg->rho_ref = 1.0;
+  cfg->gas_threshold = log(2.0);
+  cfg->rupture_eps = 1e-6;
+}
+
+size_t lbm_workspace_bytes(const lbm_config* cfg) {
+  char why[128];
+  if (!valid_config(cfg, why, sizeof(why))) return 0;
+  return layout_for(*cfg).total;
+}
+
+int lbm_create(const lbm_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
+               lbm_handle** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  char why[256];
+  if (!valid_config(cfg, why, sizeof(why))) return LBM_EINVAL;
+  const Layout L = layout_for(*cfg);
+  if (!d_workspace || ((uintptr_t)d_workspace % kAlign) != 0) return LBM_EINVAL;
+  if (bytes < L.total) return LBM_ENOMEM;
+  lbm_handle* h = new (std::nothrow) lbm_handle();
+  if (!h) return LBM_ENOMEM;
+  h->cfg = *cfg;
+  h->L = L;
+  h->ws = static_cast<char*>(d_workspace);
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->cur = 0;
+  h->err[0] = 0;
+  for (int i = 0; i < Q; ++i) h->wref[i] = cfg->storage == LBM_F32 ? 0.0f : (float)(wq(i) * cfg->rho_ref);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return LBM_ECUDA;
+  }
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, d_workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    delete h;
+    return LBM_EINVAL;
+  }
+  if (reset_state(h) != LBM_OK) {
+    delete h;
+    return LBM_ECUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_init_density(lbm_handle* h, const double* rho, int src_is_device) {
+  if (!h) return LBM_EINVAL;
+  if (!rho) return fail(h, LBM_EINVAL, "rho is NULL");
+  int rc = select_device(h);
+  if (rc) return rc;
+  const double* src = rho;
+  if (!src_is_device) {
+    void* stage = h->pops(1 - h->cur);
+    CUDA_TRY(h, cudaMemcpyAsync(stage, rho, 8 * h->N(), cudaMemcpyHostToDevice, h->stream));
+    src = static_cast<const double*>(stage);
+  }
+  CUDA_TRY(h, launch_init_from_rho(h->cfg.storage, h->pops(h->cur), src, h->cfg.nx, h->cfg.ny, h->wref,
+                                   h->stream));
+  return reset_state(h);
+}
+
+int lbm_init_bubbles(lbm_handle* h, const lbm_bubble* b, int32_t n, double rho_l, double rho_g,
+                     double width) {
+  if (!h) return LBM_EINVAL;
+  if (n < 0 || (n > 0 && !b)) return fail(h, LBM_EINVAL, "bad bubble list");
+  if (!(width > 0.0) || !isfinite(rho_l) || !isfinite(rho_g))
+    return fail(h, LBM_EINVAL, "width must be > 0 and densities finite");
+  for (int k = 0; k < n; ++k)
+    if (!isfinite(b[k].cx) || !isfinite(b[k].cy) || !isfinite(b[k].r))
+      return fail(h, LBM_EINVAL, "bubble %d is not finite", k);
+  const size_t bub_bytes = align_up(sizeof(lbm_bubble) * (size_t)n);
+  if (bub_bytes + 8 * h->N() > h->pops_bytes())
+    return fail(h, LBM_EINVAL, "too many bubbles for the staging area (%d)", n);
+  int rc = select_device(h);
+  if (rc) return rc;
+  char* stage = static_cast<char*>(h->pops(1 - h->cur));
+  lbm_bubble* d_b = reinterpret_cast<lbm_bubble*>(stage);
+  double* d_rho = reinterpret_cast<double*>(stage + bub_bytes);
+  if (n > 0)
+    CUDA_TRY(h, cudaMemcpyAsync(d_b, b, sizeof(lbm_bubble) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, launch_bubbles_rho(d_b, n, rho_l, rho_g, width, h->cfg.nx, h->cfg.ny, d_rho, h->stream));
+  CUDA_TRY(h, launch_init_from_rho(h->cfg.storage, h->pops(h->cur), d_rho, h->cfg.nx, h->cfg.ny, h->wref,
+                                   h->stream));
+  // the bubble list is read from pageable memory by an async copy: keep it valid
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return reset_state(h);
+}
+
+int lbm_load_populations(lbm_handle* h, const float* f, int src_is_device) {
+  if (!h) return LBM_EINVAL;
+  if (!f) return fail(h, LBM_EINVAL, "populations pointer is NULL");
+  int rc = select_device(h);
+  if (rc) return rc;
+  const size_t N = h->N();
+  for (int i = 0; i < Q; ++i) {
+    const float* plane = f + (size_t)i * N;
+    if (!src_is_device) {
+      float* stage = static_cast<float*>(h->pops(1 - h->cur));
+      CUDA_TRY(h, cudaMemcpyAsync(stage, plane, 4 * N, cudaMemcpyHostToDevice, h->stream));
+      plane = stage;
+    }
+    CUDA_TRY(h, launch_load_plane(h->cfg.storage, h->pops(h->cur), plane, i, h->cfg.nx, h->cfg.ny,
+                                  h->wref, h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->halted = 0;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+  if (!h) return LBM_EINVAL;
+  if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
+  int rc = select_device(h);
+  if (rc) return rc;
+  const lbm_config& c = h->cfg;
+  StepParams p{};
+  p.mask = nullptr;
+  p.flags = h->flags();
+  p.nx = c.nx;
+  p.ny = c.ny;
+  p.N = (long long)h->N();
+  p.tau = (float)c.tau;
+  p.inv_tau = (float)(1.0 / c.tau);
+  p.G = (float)c.G;
+  p.rho0 = (float)c.rho0;
+  p.inv_rho0 = (float)(1.0 / c.rho0);
+  for (int i = 0; i < Q; ++i) p.wref[i] = h->wref[i];
+  for (int64_t s = 0; s < nsteps && !h->halted; ++s) {
+    bool stop_after = false;
+    if (c.barrier && h->t % c.relabel_every == 0) {
+      int before = 0;
+      if (c.stop_on_first_rupture && (rc = read_opened(h, &before))) return rc;
+      if ((rc = relabel(h))) return rc;
+      if (c.stop_on_first_rupture) {
+        int after = 0;
+        if ((rc = read_opened(h, &after))) return rc;
+        stop_after = after > before;
+      }
+    }
+    p.src = h->pops(h->cur);
+    p.dst = h->pops(1 - h->cur);
+    p.mask = c.barrier ? h->mask() : nullptr;
+    CUDA_TRY(h, launch_step(c.storage, p, h->stream));
+    h->launches += 1;
+    h->cur ^= 1;
+    h->t += 1;
+    if (stop_after) h->halted = 1;
+  }
+  return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->t : -1; }
+
+int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : -1; }
+
+int lbm_halted(const lbm_handle* h) { return h ? h->halted : 0; }
+
+size_t lbm_fields_bytes(const lbm_handle* h, uint32_t fields) {
+  if (!h || (fields & ~kAllFields)) return 0;
+  size_t total = 0;
+  for (uint32_t bit = 1; bit <= LBM_FIELD_POPS; bit <<= 1)
+    if (fields & bit) total += field_bytes(h, bit);
+  return total;
+}
+
+int lbm_read_fields(lbm_handle* h, uint32_t fields, void* dst, size_t dst_bytes, int dst_is_device) {
+  if (!h) return LBM_EINVAL;
+  if (!dst || fields == 0 || (fields & ~kAllFields)) return fail(h, LBM_EINVAL, "bad field selection");
+  if (dst_bytes < lbm_fields_bytes(h, fields)) return fail(h, LBM_EINVAL, "dst too small");
+  int rc = select_device(h);
+  if (rc) return rc;
+  const FieldParams fp = field_params(h);
+  const size_t N = h->N();
+  char* out = static_cast<char*>(dst);
+  float* stage = static_cast<float*>(h->pops(1 - h->cur));
+  const cudaMemcpyKind d2x = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(h, launch_density(fp, h->rho(), h->stream));
+  for (uint32_t bit = 1; bit <= LBM_FIELD_POPS; bit <<= 1) {
+    if (!(fields & bit)) continue;
+    const size_t nb = field_bytes(h, bit);
+    switch (bit) {
+      case LBM_FIELD_RHO:
+      case LBM_FIELD_UX:
+      case LBM_FIELD_UY:
+      case LBM_FIELD_P: {
+        float* target = dst_is_device ? reinterpret_cast<float*>(out) : stage;
+        CUDA_TRY(h, launch_fields(fp, h->rho(), h->mask(), bit, target, h->stream));
+        if (!dst_is_device) CUDA_TRY(h, cudaMemcpyAsync(out, stage, nb, d2x, h->stream));
+        break;
+      }
+      case LBM_FIELD_LABEL:
+        CUDA_TRY(h, launch_labels(fp, h->rho(), (float)h->cfg.gas_threshold, h->label(), h->flags(),
+                                  h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(out, h->label(), nb, d2x, h->stream));
+        break;
+      case LBM_FIELD_OWNER:
+      case LBM_FIELD_MASK:
+      case LBM_FIELD_OPEN: {
+        const void* srcp = bit == LBM_FIELD_OWNER ? (const void*)h->owner()
+                           : bit == LBM_FIELD_MASK ? (const void*)h->mask()
+                                                   : (const void*)h->open();
+        if (srcp) {
+          CUDA_TRY(h, cudaMemcpyAsync(out, srcp, nb, d2x, h->stream));
+        } else {
+          const int fill = bit == LBM_FIELD_OWNER ? 0xff : 0;
+          if (dst_is_device)
+            CUDA_TRY(h, cudaMemsetAsync(out, fill, nb, h->stream));
+          else
+            memset(out, fill, nb);
+        }
+        break;
+      }
+      case LBM_FIELD_POPS:
+        for (int i = 0; i < Q; ++i) {
+          float* target = dst_is_device ? reinterpret_cast<float*>(out + 4 * N * i) : stage;
+          CUDA_TRY(h, launch_pops_out(fp, i, target, h->stream));
+          if (!dst_is_device)
+            CUDA_TRY(h, cudaMemcpyAsync(out + 4 * N * i, stage, 4 * N, d2x, h->stream));
+        }
+        break;
+    }
+    out += nb;
+  }
+  return check_flags(h);
+}
+
+int lbm_mass(lbm_handle* h, double* out) {
+  if (!h) return LBM_EINVAL;
+  if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+  int rc = select_device(h);
+  if (rc) return rc;
+  CUDA_TRY(h, launch_mass(field_params(h), h->partials(), h->L.nparts, h->scalars(), h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(out, h->scalars(), sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return check_flags(h);
+}
+
+int lbm_bubble_stats(lbm_handle* h, lbm_stats* out, double* hist, int32_t nbins, double dmin, double dmax) {
+  if (!h) return LBM_EINVAL;
+  if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+  if (hist && (nbins < 1 || nbins > kMaxHistBins || !(dmin > 0.0) || !(dmax > dmin)))
+    return fail(h, LBM_EINVAL, "histogram needs 1 <= nbins <= %d and 0 < dmin < dmax", kMaxHistBins);
+  int rc = select_device(h);
+  if (rc) return rc;
+  const FieldParams fp = field_params(h);
+  int32_t* area = static_cast<int32_t*>(h->pops(1 - h->cur));
+  CUDA_TRY(h, launch_density(fp, h->rho(), h->stream));
+  CUDA_TRY(h, launch_labels(fp, h->rho(), (float)h->cfg.gas_threshold, h->label(), h->flags(), h->stream));
+  CUDA_TRY(h, launch_stats(h->cfg.nx, h->cfg.ny, h->label(), area, h->partials(), h->L.nparts, h->scalars(),
+                           h->flags() + FLAG_HIST, hist ? nbins : 0, hist ? dmin : 1.0, hist ? dmax : 2.0,
+                           h->stream));
+  double sc[3];
+  int hc[kMaxHistBins];
+  int opened = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(sc, h->scalars(), sizeof(sc), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(hc, h->flags() + FLAG_HIST, sizeof(hc), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(&opened, h->flags() + FLAG_OPENED, sizeof(int), cudaMemcpyDeviceToHost,
+                              h->stream));
+  if ((rc = check_flags(h))) return rc;
+  double mass = 0.0;
+  if ((rc = lbm_mass(h, &mass))) return rc;
+  memset(out, 0, sizeof(*out));
+  out->step = h->t;
+  out->n_bubbles = (int32_t)llround(sc[0]);
+  out->n_open = opened;
+  out->gas_fraction = sc[1] / (double)h->N();
+  out->mean_eq_diameter = sc[0] > 0 ? sc[2] / sc[0] : 0.0;
+  out->mass = mass;
+  if (hist)
+    for (int b = 0; b < nbins; ++b) hist[b] = hc[b];
+  return LBM_OK;
+}
+
+int lbm_sync(lbm_handle* h) {
+  if (!h) return LBM_EINVAL;
+  int rc = select_device(h);
+  if (rc) return rc;
+  return check_flags(h);
+}
+
+const char* lbm_last_error(const lbm_handle* h) { return h ? h->err : "handle is NULL"; }
+
+void lbm_destroy(lbm_handle* h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,555 @@
+// Film-barrier pipeline of the extended Shan-Chen model (arXiv 1708.01613,
+// Sec. 2.1.5) and the auxiliary kernels: density, gas labelling, interaction
+// zones, rupture test (Eq. 41), blocked-edge mask, diagnostics fields,
+// initialisation, FP64 mass and bubble statistics.
+//
+// Readings used (the paper is silent on them):
+//  - gas cell: rho < threshold (default ln 2, the critical density of
+//    Sec. 2.1.2); bubbles are 4-connected gas components on the torus,
+//    labelled by the smallest row-major index in the component;
+//  - owner of a liquid cell: the bubble of the nearest gas cell within R_z,
+//    ties broken by the smaller label (the nearest-bubble rule of Sec. 2.1.5,
+//    which is where the largest |xi_k| of Eq. 38 sits);
+//  - rupture: at a cell with a differing-owner neighbour, n = the first such
+//    lattice direction, D2 = p(x+n) - 2 p(x) + p(x-n) with p of Eq. 29; the
+//    cell opens for good when |D2| <= eps or sign(D2) differs from the sign
+//    stored at the previous relabel;
+//  - blocked edge: owners differ, both defined, neither end open.
+#include <math.h>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnionIters = 1 << 20;  // bound of the union/find retry loops
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+inline unsigned blocks_for(long long n, int threads = kThreads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 64) b = 152LL * 64;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+template <int S>
+__device__ __forceinline__ float pulled(const void* pops, const FieldParams& fp, int i, int x, int y) {
+  using T = typename Store<S>::T;
+  const T* p = static_cast<const T*>(pops);
+  const int xs = wrapi(x - cx(i), fp.nx), ys = wrapi(y - cy(i), fp.ny);
+  return Store<S>::load(p, (size_t)i * fp.N + (size_t)ys * fp.nx + xs, fp.wref[i]);
+}
+
+template <int S>
+__global__ void k_density(const FieldParams fp, float* __restrict__ rho) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < fp.N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % fp.nx), y = (int)(c / fp.nx);
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = pulled<S>(fp.pops, fp, i, x, y);
+    rho[c] = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  }
+}
+
+// --- union-find labelling (min-root hooking: the root is the min index) ---
+__global__ void k_label_init(const float* __restrict__ rho, long long N, float th, int32_t* L) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x)
+    L[c] = rho[c] < th ? (int32_t)c : -1;
+}
+
+__device__ int find_root(const int32_t* L, int a, int* fail) {
+  for (int it = 0; it < kUnionIters; ++it) {
+    const int p = L[a];
+    if (p == a) return a;
+    a = p;
+  }
+  *fail = 1;
+  return a;
+}
+
+__device__ void unite(int32_t* L, int a, int b, int* fail) {
+  for (int it = 0; it < kUnionIters; ++it) {
+    a = find_root(L, a, fail);
+    b = find_root(L, b, fail);
+    if (a == b) return;
+    if (a < b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    // hook the larger root a under b; if a stopped being a root meanwhile,
+    // continue with the value it points to (links only ever decrease)
+    const int old = atomicMin(&L[a], b);
+    if (old == a) return;
+    a = old;
+  }
+  *fail = 1;
+}
+
+__global__ void k_label_union(int nx, int ny, int32_t* L, int* flags) {
+  const long long N = (long long)nx * ny;
+  int fail = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    if (L[c] < 0) continue;
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    const int right = y * nx + (x + 1 == nx ? 0 : x + 1);
+    const int down = (y + 1 == ny ? 0 : y + 1) * nx + x;
+    if (L[right] >= 0) unite(L, (int)c, right, &fail);
+    if (L[down] >= 0) unite(L, (int)c, down, &fail);
+  }
+  if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
+}
+
+__global__ void k_label_flatten(long long N, int32_t* L, int* flags) {
+  int fail = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    if (L[c] >= 0) L[c] = find_root(L, (int)c, &fail);
+  }
+  if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
+}
+
+// --- interaction zones: nearest gas cell within R, ties to the smaller label ---
+__global__ void k_owner(int nx, int ny, int R, const int32_t* __restrict__ L, int32_t* __restrict__ own) {
+  const long long N = (long long)nx * ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int lc = L[c];
+    if (lc >= 0) {
+      own[c] = lc;
+      continue;
+    }
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    int best = -1, bd = 0x7fffffff;
+    for (int dy = -R; dy <= R; ++dy) {
+      const long long row = (long long)wrapi(y + dy, ny) * nx;
+      for (int dx = -R; dx <= R; ++dx) {
+        const int d2 = dx * dx + dy * dy;
+        if (d2 > R * R || d2 > bd) continue;
+        const int l = __ldg(L + row + wrapi(x + dx, nx));
+        if (l < 0) continue;
+        if (d2 < bd || l < best) {
+          bd = d2;
+          best = l;
+        }
+      }
+    }
+    own[c] = best;
+  }
+}
+
+__device__ __forceinline__ float pressure_of(float rho, float G, float rho0) {
+  const float s = rho0 * (1.0f - expf(-rho / rho0));
+  return rho * (1.0f / 3.0f) + G * s * s * (1.0f / 6.0f);
+}
+
+__global__ void k_rupture(int nx, int ny, float G, float rho0, float eps,
+                          const float* __restrict__ rho, const int32_t* __restrict__ own,
+                          int8_t* __restrict__ sgn, uint8_t* __restrict__ open, int* flags) {
+  const long long N = (long long)nx * ny;
+  int opened = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int o = own[c];
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    int dir = 0;
+    if (o >= 0) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int on = own[(long long)wrapi(y + cy(i), ny) * nx + wrapi(x + cx(i), nx)];
+        if (dir == 0 && on >= 0 && on != o) dir = i;
+      }
+    }
+    if (dir == 0) {
+      sgn[c] = 0;
+      continue;
+    }
+    int ex = 0, ey = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (i == dir) {
+        ex = cx(i);
+        ey = cy(i);
+      }
+    const float pp = pressure_of(rho[(long long)wrapi(y + ey, ny) * nx + wrapi(x + ex, nx)], G, rho0);
+    const float p0 = pressure_of(rho[c], G, rho0);
+    const float pm = pressure_of(rho[(long long)wrapi(y - ey, ny) * nx + wrapi(x - ex, nx)], G, rho0);
+    const float d2 = pp - 2.0f * p0 + pm;
+    const int s = (d2 > 0.f) - (d2 < 0.f);
+    const int prev = sgn[c];
+    if (eps >= 0.f && !open[c] && (fabsf(d2) <= eps || (prev != 0 && s != prev))) {
+      open[c] = 1;
+      opened += 1;
+    }
+    sgn[c] = (int8_t)s;
+  }
+  if (opened) atomicAdd(flags + FLAG_OPENED, opened);
+}
+
+__global__ void k_mask(int nx, int ny, const int32_t* __restrict__ own, const uint8_t* __restrict__ open,
+                       uint8_t* __restrict__ mask) {
+  const long long N = (long long)nx * ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int o = own[c];
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    unsigned m = 0;
+    if (o >= 0 && !open[c]) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const long long nb = (long long)wrapi(y + cy(i), ny) * nx + wrapi(x + cx(i), nx);
+        const int on = own[nb];
+        if (on >= 0 && on != o && !open[nb]) m |= 1u << (i - 1);
+      }
+    }
+    mask[c] = (uint8_t)m;
+  }
+}
+
+// --- diagnostics: rho, u = (j + F/2)/rho, p (Eq. 29) ---
+template <int S>
+__global__ void k_fields(const FieldParams fp, const float* __restrict__ rho,
+                         const uint8_t* __restrict__ mask, uint32_t which, float* __restrict__ out) {
+  const int nx = fp.nx, ny = fp.ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < fp.N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    const float r = rho[c];
+    const float psi_c = fp.rho0 * (1.0f - expf(-r * fp.inv_rho0));
+    float v = 0.f;
+    if (which == LBM_FIELD_RHO) {
+      v = r;
+    } else if (which == LBM_FIELD_P) {
+      v = r * (1.0f / 3.0f) + fp.G * psi_c * psi_c * (1.0f / 6.0f);
+    } else {
+      float f[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = pulled<S>(fp.pops, fp, i, x, y);
+      const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+      const float jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+      const unsigned m = mask ? mask[c] : 0u;
+      float sx = 0.f, sy = 0.f;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        float s = fp.rho0 * (1.0f - expf(-rho[(long long)wrapi(y + cy(i), ny) * nx + wrapi(x + cx(i), nx)] * fp.inv_rho0));
+        if ((m >> (i - 1)) & 1u) s = psi_c;
+        sx += static_cast<float>(wq(i)) * s * cx(i);
+        sy += static_cast<float>(wq(i)) * s * cy(i);
+      }
+      const float F = -fp.G * psi_c * (which == LBM_FIELD_UX ? sx : sy);
+      v = ((which == LBM_FIELD_UX ? jx : jy) + 0.5f * F) / r;
+    }
+    out[c] = v;
+  }
+}
+
+template <int S>
+__global__ void k_pops_out(const FieldParams fp, int plane, float* __restrict__ out) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < fp.N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % fp.nx), y = (int)(c / fp.nx);
+    float v = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      if (i == plane) v = pulled<S>(fp.pops, fp, i, x, y);
+    out[c] = v;
+  }
+}
+
+// The stored buffer holds f_i at the source cell of the next pull: B_i(y) = f_i(y + e_i).
+template <int S>
+__global__ void k_init_from_rho(typename Store<S>::T* __restrict__ pops, const double* __restrict__ rho,
+                                int nx, int ny, FieldParams fp) {
+  const long long N = (long long)nx * ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % nx), y = (int)(c / nx);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const long long src = (long long)wrapi(y + cy(i), ny) * nx + wrapi(x + cx(i), nx);
+      const float f = (float)(wq(i) * rho[src]);
+      Store<S>::store(pops, (size_t)i * N + c, f, fp.wref[i]);
+    }
+  }
+}
+
+template <int S>
+__global__ void k_load_plane(typename Store<S>::T* __restrict__ pops, const float* __restrict__ fpl,
+                             int plane, int nx, int ny, float base) {
+  const long long N = (long long)nx * ny;
+  int ex = 0, ey = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (i == plane) {
+      ex = cx(i);
+      ey = cy(i);
+    }
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    const long long src = (long long)wrapi(y + ey, ny) * nx + wrapi(x + ex, nx);
+    Store<S>::store(pops, (size_t)plane * N + c, fpl[src], base);
+  }
+}
+
+__global__ void k_bubbles_rho(const lbm_bubble* __restrict__ b, int n, double rho_l, double rho_g,
+                              double width, int nx, int ny, double* __restrict__ rho) {
+  const long long N = (long long)nx * ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const double x = (double)(c % nx), y = (double)(c / nx);
+    double best = INFINITY;
+    for (int k = 0; k < n; ++k) {
+      double dx = fabs(x - b[k].cx), dy = fabs(y - b[k].cy);
+      dx = fmin(dx, nx - dx);
+      dy = fmin(dy, ny - dy);
+      const double s = sqrt(dx * dx + dy * dy) - b[k].r;
+      if (s < best) best = s;
+    }
+    const double v = n > 0 ? tanh(best / (0.5 * width)) : 1.0;
+    rho[c] = 0.5 * (rho_l + rho_g) + 0.5 * (rho_l - rho_g) * v;
+  }
+}
+
+// --- fixed-order FP64 reductions ---
+constexpr int kRedBlocks = 152 * 4;
+
+template <int NV>
+__device__ void block_reduce_store(double (&v)[NV], double* __restrict__ out) {
+  __shared__ double sh[NV][kThreads];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) sh[j][threadIdx.x] = v[j];
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) out[j * gridDim.x + blockIdx.x] = sh[j][0];
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_mass_partial(const FieldParams fp, double* partials) {
+  using T = typename Store<S>::T;
+  const T* p = static_cast<const T*>(fp.pops);
+  double acc[1] = {0.0};
+  for (int i = 0; i < Q; ++i) {
+    const float base = fp.wref[i];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < fp.N;
+         c += (long long)gridDim.x * blockDim.x)
+      acc[0] += (double)Store<S>::load(p, (size_t)i * fp.N + c, base);
+  }
+  block_reduce_store<1>(acc, partials);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads) k_sum_partials(const double* partials, int nparts, double* out) {
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] += partials[j * nparts + k];
+  block_reduce_store<NV>(acc, out);
+}
+
+__global__ void k_area(long long N, const int32_t* __restrict__ L, int32_t* __restrict__ area) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int l = L[c];
+    if (l >= 0) atomicAdd(area + l, 1);
+  }
+}
+
+// partial sums: [0] bubbles, [1] gas cells, [2] sum of equivalent diameters;
+// histogram counts are integers, accumulated exactly with atomics
+constexpr int kMaxBins = 64;
+constexpr int kStatVals = 3;
+
+__global__ void __launch_bounds__(kThreads) k_stats_partial(long long N, const int32_t* __restrict__ L,
+                                                            const int32_t* __restrict__ area, int nbins,
+                                                            double ldmin, double ldspan, double* partials,
+                                                            int* hist) {
+  double v[kStatVals] = {0.0, 0.0, 0.0};
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int l = L[c];
+    if (l < 0) continue;
+    v[1] += 1.0;
+    if (l == c) {
+      const double d = 2.0 * sqrt((double)area[c] / M_PI);
+      v[0] += 1.0;
+      v[2] += d;
+      if (nbins > 0) {
+        int b = (int)floor((log(d) - ldmin) / ldspan * nbins);
+        b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+        atomicAdd(hist + b, 1);
+      }
+    }
+  }
+  block_reduce_store<kStatVals>(v, partials);
+}
+
+}  // namespace
+
+int mass_partials_needed() { return kRedBlocks * kStatVals; }
+
+#define LBM_DISPATCH(storage, KERNEL, ...)                                  \
+  switch (storage) {                                                        \
+    case LBM_F32: KERNEL<LBM_F32><<<__VA_ARGS__>>>; break;                  \
+    case LBM_F16_DEV: KERNEL<LBM_F16_DEV><<<__VA_ARGS__>>>; break;          \
+    case LBM_BF16_DEV: KERNEL<LBM_BF16_DEV><<<__VA_ARGS__>>>; break;        \
+    default: return cudaErrorInvalidValue;                                  \
+  }
+
+cudaError_t launch_density(const FieldParams& fp, float* rho, cudaStream_t s) {
+  const unsigned b = blocks_for(fp.N);
+  switch (fp.storage) {
+    case LBM_F32: k_density<LBM_F32><<<b, kThreads, 0, s>>>(fp, rho); break;
+    case LBM_F16_DEV: k_density<LBM_F16_DEV><<<b, kThreads, 0, s>>>(fp, rho); break;
+    case LBM_BF16_DEV: k_density<LBM_BF16_DEV><<<b, kThreads, 0, s>>>(fp, rho); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_labels(const FieldParams& fp, const float* rho, float threshold, int32_t* label,
+                          int* flags, cudaStream_t s) {
+  const unsigned b = blocks_for(fp.N);
+  k_label_init<<<b, kThreads, 0, s>>>(rho, fp.N, threshold, label);
+  k_label_union<<<b, kThreads, 0, s>>>(fp.nx, fp.ny, label, flags);
+  k_label_flatten<<<b, kThreads, 0, s>>>(fp.N, label, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_owner(int nx, int ny, int R, const int32_t* label, int32_t* owner, cudaStream_t s) {
+  k_owner<<<blocks_for((long long)nx * ny), kThreads, 0, s>>>(nx, ny, R, label, owner);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rupture(int nx, int ny, float G, float rho0, float eps, const float* rho,
+                           const int32_t* owner, int8_t* sgn, uint8_t* open, int* flags,
+                           cudaStream_t s) {
+  k_rupture<<<blocks_for((long long)nx * ny), kThreads, 0, s>>>(nx, ny, G, rho0, eps, rho, owner, sgn,
+                                                                open, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask(int nx, int ny, const int32_t* owner, const uint8_t* open, uint8_t* mask,
+                        cudaStream_t s) {
+  k_mask<<<blocks_for((long long)nx * ny), kThreads, 0, s>>>(nx, ny, owner, open, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const FieldParams& fp, const float* rho, const uint8_t* mask, uint32_t which,
+                          float* out, cudaStream_t s) {
+  const unsigned b = blocks_for(fp.N);
+  switch (fp.storage) {
+    case LBM_F32: k_fields<LBM_F32><<<b, kThreads, 0, s>>>(fp, rho, mask, which, out); break;
+    case LBM_F16_DEV: k_fields<LBM_F16_DEV><<<b, kThreads, 0, s>>>(fp, rho, mask, which, out); break;
+    case LBM_BF16_DEV: k_fields<LBM_BF16_DEV><<<b, kThreads, 0, s>>>(fp, rho, mask, which, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pops_out(const FieldParams& fp, int plane, float* out, cudaStream_t s) {
+  const unsigned b = blocks_for(fp.N);
+  switch (fp.storage) {
+    case LBM_F32: k_pops_out<LBM_F32><<<b, kThreads, 0, s>>>(fp, plane, out); break;
+    case LBM_F16_DEV: k_pops_out<LBM_F16_DEV><<<b, kThreads, 0, s>>>(fp, plane, out); break;
+    case LBM_BF16_DEV: k_pops_out<LBM_BF16_DEV><<<b, kThreads, 0, s>>>(fp, plane, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_from_rho(int storage, void* pops, const double* rho, int nx, int ny,
+                                 const float* wref, cudaStream_t s) {
+  FieldParams fp{};
+  for (int i = 0; i < Q; ++i) fp.wref[i] = wref[i];
+  const unsigned b = blocks_for((long long)nx * ny);
+  switch (storage) {
+    case LBM_F32:
+      k_init_from_rho<LBM_F32><<<b, kThreads, 0, s>>>(static_cast<float*>(pops), rho, nx, ny, fp);
+      break;
+    case LBM_F16_DEV:
+      k_init_from_rho<LBM_F16_DEV><<<b, kThreads, 0, s>>>(static_cast<__half*>(pops), rho, nx, ny, fp);
+      break;
+    case LBM_BF16_DEV:
+      k_init_from_rho<LBM_BF16_DEV><<<b, kThreads, 0, s>>>(static_cast<__nv_bfloat16*>(pops), rho, nx,
+                                                            ny, fp);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_plane(int storage, void* pops, const float* f_plane, int plane, int nx, int ny,
+                              const float* wref, cudaStream_t s) {
+  const unsigned b = blocks_for((long long)nx * ny);
+  switch (storage) {
+    case LBM_F32:
+      k_load_plane<LBM_F32><<<b, kThreads, 0, s>>>(static_cast<float*>(pops), f_plane, plane, nx, ny,
+                                                    wref[plane]);
+      break;
+    case LBM_F16_DEV:
+      k_load_plane<LBM_F16_DEV><<<b, kThreads, 0, s>>>(static_cast<__half*>(pops), f_plane, plane, nx, ny,
+                                                        wref[plane]);
+      break;
+    case LBM_BF16_DEV:
+      k_load_plane<LBM_BF16_DEV><<<b, kThreads, 0, s>>>(static_cast<__nv_bfloat16*>(pops), f_plane,
+                                                         plane, nx, ny, wref[plane]);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bubbles_rho(const lbm_bubble* d_bubbles, int n, double rho_l, double rho_g,
+                               double width, int nx, int ny, double* rho, cudaStream_t s) {
+  k_bubbles_rho<<<blocks_for((long long)nx * ny), kThreads, 0, s>>>(d_bubbles, n, rho_l, rho_g, width,
+                                                                     nx, ny, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass(const FieldParams& fp, double* partials, int nparts, double* out_dev,
+                        cudaStream_t s) {
+  if (nparts < kRedBlocks) return cudaErrorInvalidValue;
+  switch (fp.storage) {
+    case LBM_F32: k_mass_partial<LBM_F32><<<kRedBlocks, kThreads, 0, s>>>(fp, partials); break;
+    case LBM_F16_DEV: k_mass_partial<LBM_F16_DEV><<<kRedBlocks, kThreads, 0, s>>>(fp, partials); break;
+    case LBM_BF16_DEV: k_mass_partial<LBM_BF16_DEV><<<kRedBlocks, kThreads, 0, s>>>(fp, partials); break;
+    default: return cudaErrorInvalidValue;
+  }
+  k_sum_partials<1><<<1, kThreads, 0, s>>>(partials, kRedBlocks, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(int nx, int ny, const int32_t* label, int32_t* area, double* partials, int nparts,
+                         double* out_dev, int* hist, int nbins, double dmin, double dmax, cudaStream_t s) {
+  if (nparts < kRedBlocks * kStatVals || nbins > kMaxBins) return cudaErrorInvalidValue;
+  const long long N = (long long)nx * ny;
+  cudaError_t e = cudaMemsetAsync(area, 0, sizeof(int32_t) * N, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(int) * kMaxBins, s);
+  if (e != cudaSuccess) return e;
+  k_area<<<blocks_for(N), kThreads, 0, s>>>(N, label, area);
+  const double ldmin = log(dmin > 0 ? dmin : 1.0);
+  const double ldspan = log(dmax > dmin && dmin > 0 ? dmax : 2.0 * (dmin > 0 ? dmin : 1.0)) - ldmin;
+  k_stats_partial<<<kRedBlocks, kThreads, 0, s>>>(N, label, area, nbins, ldmin, ldspan, partials, hist);
+  k_sum_partials<kStatVals><<<1, kThreads, 0, s>>>(partials, kRedBlocks, out_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

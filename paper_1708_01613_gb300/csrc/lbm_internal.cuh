@@ -1,0 +1,144 @@
+// Internal declarations shared by the CUDA translation units of liblbm.
+// Lattice: D2Q9 (arXiv 1708.01613, Sec. 2.1.1, Eqs. 15-16), directions
+// 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int Q = 9;
+
+__host__ __device__ constexpr int cx(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr double wq(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr float wqf(int i) {
+  return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+
+// Device flag slots (int32 each) in the workspace.
+enum Flag : int {
+  FLAG_NUMERIC = 0,   // NaN/Inf or rho <= 0 seen by the step kernel
+  FLAG_TIMEOUT = 1,   // a bounded device loop gave up
+  FLAG_OPENED = 2,    // cells opened by the latest rupture test
+  FLAG_HIST = 64,     // 64 histogram counters
+  FLAG_COUNT = 128
+};
+
+// Population storage: FP32 value, or a 16-bit deviation from w_i rho_ref.
+template <int S>
+struct Store;
+
+template <>
+struct Store<LBM_F32> {
+  using T = float;
+  static constexpr int bytes = 4;
+  __device__ static __forceinline__ float load(const T* p, size_t i, float) { return __ldg(p + i); }
+  __device__ static __forceinline__ void store(T* p, size_t i, float v, float) { p[i] = v; }
+};
+
+template <>
+struct Store<LBM_F16_DEV> {
+  using T = __half;
+  static constexpr int bytes = 2;
+  __device__ static __forceinline__ float load(const T* p, size_t i, float base) {
+    return base + __half2float(__ldg(p + i));
+  }
+  __device__ static __forceinline__ void store(T* p, size_t i, float v, float base) {
+    p[i] = __float2half_rn(v - base);
+  }
+};
+
+template <>
+struct Store<LBM_BF16_DEV> {
+  using T = __nv_bfloat16;
+  static constexpr int bytes = 2;
+  __device__ static __forceinline__ float load(const T* p, size_t i, float base) {
+    return base + __bfloat162float(__ldg(p + i));
+  }
+  __device__ static __forceinline__ void store(T* p, size_t i, float v, float base) {
+    p[i] = __float2bfloat16_rn(v - base);
+  }
+};
+
+inline int storage_bytes(int s) { return s == LBM_F32 ? 4 : 2; }
+
+// Arguments of the fused step kernel.
+struct StepParams {
+  const void* src;       // populations after collision of the previous step
+  void* dst;             // populations after collision of this step
+  const uint8_t* mask;   // blocked-edge mask (nullptr: plain Shan-Chen)
+  int* flags;            // device flag slots
+  int nx, ny;
+  long long N;           // nx * ny (plane stride)
+  int rows_per_chunk;    // rows marched by one CTA
+  float tau, inv_tau, G, rho0, inv_rho0;
+  float wref[Q];         // w_i * rho_ref (16-bit deviation base)
+};
+
+// Launch of the fused step (step.cu). Returns a cudaError_t.
+cudaError_t launch_step(int storage, const StepParams& p, cudaStream_t s);
+// Launch geometry the fused step uses for a box (for tests/benchmarks).
+void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk, int* block);
+
+// Barrier / field / reduction kernels (barrier.cu).
+struct Workspace {
+  void* pops[2];
+  float* rho;          // N: density of the current state (relabel, fields)
+  int32_t* label;      // N
+  int32_t* owner;      // N (barrier)
+  uint8_t* mask;       // N (barrier)
+  uint8_t* open;       // N (barrier)
+  int8_t* sgn;         // N (barrier)
+  int* flags;          // FLAG_COUNT
+  double* partials;    // reduction partials
+  int partial_count;
+};
+
+struct FieldParams {
+  const void* pops;    // current populations (post-collision of the last step)
+  int storage;
+  int nx, ny;
+  long long N;
+  float G, rho0, inv_rho0, tau;
+  float wref[Q];
+};
+
+cudaError_t launch_density(const FieldParams& fp, float* rho, cudaStream_t s);
+cudaError_t launch_labels(const FieldParams& fp, const float* rho, float threshold, int32_t* label,
+                          int* flags, cudaStream_t s);
+cudaError_t launch_owner(int nx, int ny, int R, const int32_t* label, int32_t* owner, cudaStream_t s);
+cudaError_t launch_rupture(int nx, int ny, float G, float rho0, float eps, const float* rho,
+                           const int32_t* owner, int8_t* sgn, uint8_t* open, int* flags,
+                           cudaStream_t s);
+cudaError_t launch_mask(int nx, int ny, const int32_t* owner, const uint8_t* open, uint8_t* mask,
+                        cudaStream_t s);
+cudaError_t launch_fields(const FieldParams& fp, const float* rho, const uint8_t* mask,
+                          uint32_t which, float* out, cudaStream_t s);
+cudaError_t launch_pops_out(const FieldParams& fp, int plane, float* out, cudaStream_t s);
+cudaError_t launch_init_from_rho(int storage, void* pops, const double* rho, int nx, int ny,
+                                 const float* wref, cudaStream_t s);
+cudaError_t launch_load_plane(int storage, void* pops, const float* f_plane, int plane, int nx,
+                              int ny, const float* wref, cudaStream_t s);
+cudaError_t launch_bubbles_rho(const lbm_bubble* d_bubbles, int n, double rho_l, double rho_g,
+                               double width, int nx, int ny, double* rho, cudaStream_t s);
+cudaError_t launch_mass(const FieldParams& fp, double* partials, int nparts, double* out_dev,
+                        cudaStream_t s);
+cudaError_t launch_stats(int nx, int ny, const int32_t* label, int32_t* area, double* partials,
+                         int nparts, double* out_dev, int* hist, int nbins, double dmin, double dmax,
+                         cudaStream_t s);
+constexpr int kMaxHistBins = 64;
+int mass_partials_needed();
+
+}  // namespace lbm

@@ -1,0 +1,291 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (infinity norm relative to the oracle field's infinity norm):
+FP32 storage 1e-5, FP16-deviation storage 2e-3 over short horizons; BF16 is
+reported. Integer outputs (labels, owners, masks) must be bit-exact wherever
+the float decision that makes them is not within rounding of its threshold.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle as O
+from paper_1708_01613_gb300 import LbmError, Simulation, make_config
+
+pytestmark = pytest.mark.gpu
+
+RL, RG = inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55
+TOL = {"f32": 1e-5, "f16": 2e-3}
+
+
+def rel_inf(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / np.max(np.abs(b)))
+
+
+def two_bubbles(nx=160, ny=80, R=20, gap=6.0):
+    return [[nx / 2 - R - gap / 2, ny / 2, R], [nx / 2 + R + gap / 2, ny / 2, R]]
+
+
+def gpu_sim(nx, ny, rho=None, bubbles=None, **kw):
+    storage = kw.pop("storage", "f32")
+    rho_ref = kw.pop("rho_ref", None)
+    if rho_ref is None:
+        rho_ref = float(np.mean(rho)) if rho is not None else 1.0
+    sim = Simulation(make_config(nx, ny, storage=storage, rho_ref=rho_ref, **kw))
+    if bubbles is not None:
+        sim.init_bubbles(bubbles, RL, RG, 4.0)
+    else:
+        sim.init_density(rho)
+    return sim
+
+
+def oracle_sim(nx, ny, rho, **kw):
+    s = O.OracleSim(O.make_params(nx, ny, **kw))
+    s.init_density(rho)
+    return s
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 128), (300, 70), (257, 9), (37, 5)])
+def test_init_populations_exact(nx, ny):
+    rho = inputs.noise_density(nx, ny, seed=3)
+    sim = gpu_sim(nx, ny, rho)
+    f = sim.read("pops")["pops"]
+    _, _, w = O.lattice()
+    want = (w[:, None, None] * rho[None]).astype(np.float32)
+    assert np.array_equal(f, want)
+    assert sim.steps_done == 0
+
+
+@pytest.mark.parametrize("nx,ny", [(128, 128), (300, 70), (257, 9), (37, 5)])
+def test_step_parity_fp32_spinodal(nx, ny):
+    """Config-1 physics (rho = 0.7 +- 1 %, G = -5.5) at sizes spanning several
+    strips and ragged tails."""
+    rho = inputs.noise_density(nx, ny, seed=1)
+    sim = gpu_sim(nx, ny, rho)
+    ref = oracle_sim(nx, ny, rho)
+    done = 0
+    for t in (1, 10, 100):
+        sim.step(t - done)
+        ref.step(t - done)
+        done = t
+        err = rel_inf(sim.read("pops")["pops"], ref.f)
+        print(f"{nx}x{ny} step {t}: rel err {err:.3e}")
+        if t <= 10:
+            assert err < TOL["f32"], (t, err)
+        else:
+            assert err < 1e-3, (t, err)  # unstable spinodal modes amplify rounding
+
+
+def _bits_equal_except_near(a, b, ok_mask):
+    """Equal everywhere except where ok_mask allows a difference."""
+    diff = a != b
+    return not np.any(diff & ~ok_mask)
+
+
+def test_barrier_parity_two_bubbles_fp32():
+    """Barrier on (K = 1): populations within 1e-5 and the owner map and
+    blocked-edge mask bit-exact at steps 1, 10, 100."""
+    nx, ny = 160, 80
+    b = two_bubbles(nx, ny, gap=6.0)
+    P = O.make_params(nx, ny, barrier=True)
+    rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
+    sim = gpu_sim(nx, ny, bubbles=b, barrier=True)
+    ref = oracle_sim(nx, ny, rho0, barrier=True)
+    assert np.array_equal(sim.read("pops")["pops"], (O.lattice()[2][:, None, None] * rho0[None]).astype(np.float32))
+    done = 0
+    for t in (1, 10, 100):
+        sim.step(t - done)
+        ref.step(t - done)
+        done = t
+        got = sim.read("pops", "owner", "mask", "open")
+        err = rel_inf(got["pops"], ref.f)
+        print(f"barrier step {t}: rel err {err:.3e}, blocked edges {int(np.count_nonzero(ref.mask))}")
+        assert err < TOL["f32"], (t, err)
+        assert np.array_equal(got["owner"], ref.owner)
+        assert np.array_equal(got["mask"], ref.mask)
+        assert np.array_equal(got["open"], ref.open)
+    assert np.count_nonzero(ref.mask) > 0
+
+
+def test_barrier_relabel_period_k():
+    nx, ny = 160, 80
+    b = two_bubbles(nx, ny, gap=6.0)
+    P = O.make_params(nx, ny, barrier=True, relabel_every=5)
+    rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
+    sim = gpu_sim(nx, ny, bubbles=b, barrier=True, relabel_every=5)
+    ref = oracle_sim(nx, ny, rho0, barrier=True, relabel_every=5)
+    sim.step(23)
+    ref.step(23)
+    got = sim.read("pops", "mask")
+    assert rel_inf(got["pops"], ref.f) < TOL["f32"]
+    assert np.array_equal(got["mask"], ref.mask)
+
+
+def test_fields_and_labels_parity():
+    nx, ny = 160, 80
+    b = two_bubbles(nx, ny, gap=6.0)
+    P = O.make_params(nx, ny, barrier=True)
+    rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
+    sim = gpu_sim(nx, ny, bubbles=b, barrier=True)
+    ref = oracle_sim(nx, ny, rho0, barrier=True)
+    sim.step(50)
+    ref.step(50)
+    got = sim.read("rho", "ux", "uy", "p", "label")
+    fl = ref.fields()
+    assert rel_inf(got["rho"], fl["rho"]) < TOL["f32"]
+    assert rel_inf(got["p"], fl["p"]) < TOL["f32"]
+    umax = max(np.max(np.abs(fl["ux"])), np.max(np.abs(fl["uy"])))
+    assert np.max(np.abs(got["ux"] - fl["ux"])) / umax < 1e-4
+    assert np.max(np.abs(got["uy"] - fl["uy"])) / umax < 1e-4
+    lab_ref = O.label(P, fl["rho"])
+    near = np.abs(fl["rho"] - math.log(2.0)) < 1e-5
+    assert _bits_equal_except_near(got["label"], lab_ref, near)
+    st = sim.stats(nbins=8, dmin=1.0, dmax=128.0)
+    so = O.stats(P, lab_ref, nbins=8, dmin=1.0, dmax=128.0)
+    assert st["n_bubbles"] == so["n_bubbles"] == 2
+    assert st["gas_fraction"] == pytest.approx(so["gas_fraction"], abs=1e-12)
+    assert st["mean_diameter"] == pytest.approx(so["mean_diameter"], rel=1e-12)
+    assert np.array_equal(st["hist"], so["hist"])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_16bit_storage_error(storage):
+    """FP16 deviation storage meets 2e-3 on rho over short horizons; BF16 is
+    reported (8 mantissa bits are not expected to meet it)."""
+    nx, ny = 160, 80
+    b = two_bubbles(nx, ny, gap=6.0)
+    P = O.make_params(nx, ny)
+    rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
+    rho_ref = float(np.mean(rho0))
+    sim = gpu_sim(nx, ny, bubbles=b, storage=storage, rho_ref=rho_ref)
+    ref = oracle_sim(nx, ny, rho0)
+    done = 0
+    for t in (1, 10, 100):
+        sim.step(t - done)
+        ref.step(t - done)
+        done = t
+        err = rel_inf(sim.read("rho")["rho"], ref.fields()["rho"])
+        print(f"{storage} step {t}: rho rel err {err:.3e}")
+        if storage == "f16":
+            assert err < TOL["f16"], (t, err)
+
+
+def test_mass_fp64_and_conservation():
+    nx, ny = 128, 128
+    rho = inputs.noise_density(nx, ny, seed=1)
+    sim = gpu_sim(nx, ny, rho)
+    m0 = sim.mass()
+    assert m0 == pytest.approx(float(np.sum(rho)), rel=1e-7)
+    sim.step(1000)
+    m1 = sim.mass()
+    print(f"fp32 mass drift over 1000 steps: {abs(m1 - m0) / m0:.3e}")
+    # FP32 collision rounding moves sum f by ~1e-8 relative per step; the FP64
+    # oracle conserves it to 1e-12 (see the oracle pins)
+    assert abs(m1 - m0) / m0 < 1e-4
+
+
+def test_resume_is_bitwise():
+    nx, ny = 128, 96
+    rho = inputs.noise_density(nx, ny, seed=5)
+    a = gpu_sim(nx, ny, rho)
+    a.step(30)
+    f = a.read("pops")["pops"]
+    b = Simulation(make_config(nx, ny))
+    b.load_populations(f)
+    assert np.array_equal(b.read("pops")["pops"], f)
+    a.step(30)
+    b.step(30)
+    assert np.array_equal(a.read("pops")["pops"], b.read("pops")["pops"])
+
+
+def test_stop_on_first_rupture_matches_oracle():
+    nx, ny = 160, 80
+    b = two_bubbles(nx, ny, gap=3.0)
+    P = O.make_params(nx, ny, barrier=True, stop_on_first_rupture=True)
+    rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
+    ref = oracle_sim(nx, ny, rho0, barrier=True, stop_on_first_rupture=True)
+    sim = gpu_sim(nx, ny, bubbles=b, barrier=True, stop_on_first_rupture=True)
+    n_ref = ref.step(500)
+    sim.step(500)
+    assert ref.halted and sim.halted
+    assert sim.steps_done == n_ref
+    assert np.array_equal(sim.read("open")["open"], ref.open)
+
+
+def test_numeric_fault_is_reported_not_raised_on_device():
+    nx, ny = 64, 64
+    sim = gpu_sim(nx, ny, np.full((ny, nx), -1.0))
+    sim.step(1)
+    with pytest.raises(LbmError) as e:
+        sim.sync()
+    assert e.value.code == 4  # LBM_ENUMERIC
+
+
+def _check_labels_valid(lab, gas):
+    """Valid min-index labelling: liquid -1; 4-neighbouring gas cells share a
+    label; every label is the index of a gas cell that carries its own index;
+    no cell's index is below its label (so the label is the component's min)."""
+    assert np.all((lab >= 0) == gas)
+    right = np.roll(lab, -1, axis=1)
+    down = np.roll(lab, -1, axis=0)
+    g_r = gas & np.roll(gas, -1, axis=1)
+    g_d = gas & np.roll(gas, -1, axis=0)
+    assert np.array_equal(lab[g_r], right[g_r]) and np.array_equal(lab[g_d], down[g_d])
+    flat = lab.ravel()
+    idx = np.arange(flat.size)
+    roots = flat[flat >= 0]
+    assert np.all(flat[roots] == roots)
+    assert np.all(roots <= idx[flat >= 0])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_full_size_8192_sampled(storage):
+    """The benchmark workload (8192^2, 400 bubbles, barrier on, K = 10) in the
+    benchmark's launch configuration: one step checked at 4096 sampled cells
+    against the oracle evaluated one cell at a time from the GPU's own input
+    state and mask; labels checked as a valid min-index labelling; owners
+    checked at sampled liquid cells by exhaustive window search."""
+    n = 8192
+    bub = inputs.poisson_disk_bubbles(n, n, 400, 8.0, 64.0, 2.0, seed=21)
+    P = O.make_params(n, n, barrier=True, relabel_every=10)
+    sim = Simulation(make_config(n, n, storage=storage, barrier=True, relabel_every=10,
+                                 rho_ref=float(RL)))
+    sim.init_bubbles(bub, RL, RG, 4.0)
+    lab = sim.read("label")["label"]  # labels of the density the t = 0 relabel sees
+    sim.step(3)  # t = 3: the next step does not relabel
+    before = sim.read("pops", "mask", "owner")
+    sim.step(1)
+    after = sim.read("pops")["pops"]
+    rng = np.random.default_rng(0)
+    gasy, gasx = np.nonzero(before["mask"])
+    cells = rng.choice(n * n, 3072, replace=False)
+    if len(gasy):
+        pick = rng.choice(len(gasy), min(1024, len(gasy)), replace=False)
+        cells = np.concatenate([cells, gasy[pick].astype(np.int64) * n + gasx[pick]])
+    f64 = before["pops"].astype(np.float64)
+    want = O.step_cells(P, f64, cells, before["mask"])
+    got = after.reshape(9, -1)[:, cells].T.astype(np.float64)
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    print(f"8192^2 {storage}: sampled one-step rel err {err:.3e}")
+    # FP32 storage: one FP32 step; FP16: plus one 16-bit rounding of the output
+    assert err < (1e-6 if storage == "f32" else 1e-3)
+    gas = lab >= 0
+    _check_labels_valid(lab, gas)
+    own = before["owner"]
+    R = 4
+    for c in cells[:512]:
+        y, x = divmod(int(c), n)
+        if gas[y, x]:
+            assert own[y, x] == lab[y, x]
+            continue
+        best = None
+        for dy in range(-R, R + 1):
+            for dx in range(-R, R + 1):
+                if dx * dx + dy * dy > R * R:
+                    continue
+                l = lab[(y + dy) % n, (x + dx) % n]
+                if l >= 0 and (best is None or (dx * dx + dy * dy, l) < best):
+                    best = (dx * dx + dy * dy, l)
+        assert own[y, x] == (best[1] if best else -1)
