@@ -178,6 +178,27 @@ const char* lbm_last_error(const lbm_handle* h);
 /* Frees the host handle (not the workspace). NULL is allowed. */
 void lbm_destroy(lbm_handle* h);
 
+/* Allocation-free FP64 mass (sum of all populations) of a caller-held
+ * population buffer: d_pops holds 9 * nx * ny values of `storage` (FP32
+ * values, or 16-bit deviations from w_i rho_ref), in any cell order. The
+ * paper has no counterpart: this entry point exists for callers that may not
+ * allocate device memory of their own (their device memory belongs to
+ * another allocator or pool, or cudaMalloc's implicit synchronisation is not
+ * acceptable) and so cannot supply the workspace lbm_create needs.
+ * It allocates nothing and needs no handle: the reduction's scratch is a
+ * fixed 32 KiB file-scope __device__ array kept by every GPU that loads the
+ * library until exit. Limit: nx * ny <= 2^28 cells; larger boxes return
+ * LBM_EINVAL. The result is written to d_out (one double of device memory)
+ * asynchronously on cuda_stream (NULL = legacy default stream).
+ * The first call on a device, with that device current, looks up the
+ * scratch's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. All calls share the scratch: calls whose work
+ * overlaps on the GPU race and may return wrong sums; order them on one
+ * stream. Each call writes every scratch slot it reads, so no clearing is
+ * needed. err (may be NULL) receives a message of at most err_len bytes. */
+int lbm_mass_noalloc(const void* d_pops, int32_t nx, int32_t ny, int32_t storage, double rho_ref,
+                     void* cuda_stream, double* d_out, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ SIGNATURES = {
     "lbm_sync": (C.c_int, [_vp]),
     "lbm_last_error": (C.c_char_p, [_vp]),
     "lbm_destroy": (None, [_vp]),
+    "lbm_mass_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _vp, _vp,
+                                   C.c_char_p, C.c_size_t]),
 }
 
 _lib = None
