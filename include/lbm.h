@@ -145,6 +145,12 @@ int lbm_step(lbm_handle* h, int64_t nsteps);
 /* Kernels this handle has launched since lbm_create (host-side count). */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 
+/* Selects the fused-step kernel: 0 = automatic (TMA-staged where the box
+ * allows it: nx % 16 == 0 and nx >= 272, else plain loads), 1 = plain-load
+ * kernel, 2 = TMA-staged kernel (LBM_ENOTSUP if the box does not allow it).
+ * Both compute the same arithmetic in the same order. */
+int lbm_set_step_variant(lbm_handle* h, int variant);
+
 /* Steps done since the last init/load. */
 int64_t lbm_steps_done(const lbm_handle* h);
 

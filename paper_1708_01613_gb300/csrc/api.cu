@@ -89,6 +89,7 @@ struct lbm_handle {
   int cur;
   int64_t t;
   int64_t launches;
+  int variant;
   int halted;
   float wref[Q];
   char err[320];
@@ -343,6 +344,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
   const lbm_config& c = h->cfg;
   StepParams p{};
   p.mask = nullptr;
+  p.force_generic = h->variant == 1 ? 1 : 0;
   p.flags = h->flags();
   p.nx = c.nx;
   p.ny = c.ny;
@@ -380,6 +382,15 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
 int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->t : -1; }
 
 int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : -1; }
+
+int lbm_set_step_variant(lbm_handle* h, int variant) {
+  if (!h) return LBM_EINVAL;
+  if (variant < 0 || variant > 2) return fail(h, LBM_EINVAL, "variant must be 0, 1 or 2");
+  if (variant == 2 && !step_tma_allowed(h->cfg.storage, h->cfg.nx))
+    return fail(h, LBM_ENOTSUP, "TMA-staged step needs nx %% 16 == 0 and nx >= 272");
+  h->variant = variant;
+  return LBM_OK;
+}
 
 int lbm_halted(const lbm_handle* h) { return h ? h->halted : 0; }
 

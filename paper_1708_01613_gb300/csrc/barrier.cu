@@ -146,6 +146,55 @@ __global__ void k_owner(int nx, int ny, int R, const int32_t* __restrict__ L, in
   }
 }
 
+// Tiled owner search: a 32 x 8 tile stages the labels of its window (tile
+// plus R on every side, wrapped) in shared memory. A tile with no gas cell
+// in that window writes -1 everywhere; otherwise each liquid cell scans the
+// window from shared memory. Same result as k_owner (same scan order).
+constexpr int kOTX = 32, kOTY = 8, kOMaxR = 16;
+
+__global__ void __launch_bounds__(kOTX * kOTY) k_owner_tiled(int nx, int ny, int R, const int32_t* __restrict__ L,
+                                                           int32_t* __restrict__ own) {
+  __shared__ int32_t sl[(kOTY + 2 * kOMaxR) * (kOTX + 2 * kOMaxR)];
+  const int W = kOTX + 2 * R, H = kOTY + 2 * R;
+  const int bx0 = blockIdx.x * kOTX, by0 = blockIdx.y * kOTY;
+  const int tid = threadIdx.y * kOTX + threadIdx.x;
+  int any = 0;
+  for (int k = tid; k < W * H; k += kOTX * kOTY) {
+    const int yy = k / W, xx = k - yy * W;
+    const int gy = wrapi(by0 - R + yy, ny), gx = wrapi(bx0 - R + xx, nx);
+    const int l = L[(long long)gy * nx + gx];
+    sl[k] = l;
+    any |= l >= 0;
+  }
+  any = __syncthreads_or(any);
+  const int x = bx0 + threadIdx.x, y = by0 + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  int result = -1;
+  if (any) {
+    const int* row0 = sl + (threadIdx.y + R) * W + threadIdx.x + R;
+    const int lc = row0[0];
+    if (lc >= 0) {
+      result = lc;
+    } else {
+      int bd = 0x7fffffff;
+      for (int dy = -R; dy <= R; ++dy) {
+        const int* rowp = row0 + dy * W;
+        for (int dx = -R; dx <= R; ++dx) {
+          const int d2 = dx * dx + dy * dy;
+          if (d2 > R * R || d2 > bd) continue;
+          const int l = rowp[dx];
+          if (l < 0) continue;
+          if (d2 < bd || l < result) {
+            bd = d2;
+            result = l;
+          }
+        }
+      }
+    }
+  }
+  own[(long long)y * nx + x] = result;
+}
+
 __device__ __forceinline__ float pressure_of(float rho, float G, float rho0) {
   const float s = rho0 * (1.0f - expf(-rho / rho0));
   return rho * (1.0f / 3.0f) + G * s * s * (1.0f / 6.0f);
@@ -434,7 +483,12 @@ cudaError_t launch_labels(const FieldParams& fp, const float* rho, float thresho
 }
 
 cudaError_t launch_owner(int nx, int ny, int R, const int32_t* label, int32_t* owner, cudaStream_t s) {
-  k_owner<<<blocks_for((long long)nx * ny), kThreads, 0, s>>>(nx, ny, R, label, owner);
+  if (R <= kOMaxR) {
+    dim3 grid((nx + kOTX - 1) / kOTX, (ny + kOTY - 1) / kOTY);
+    k_owner_tiled<<<grid, dim3(kOTX, kOTY), 0, s>>>(nx, ny, R, label, owner);
+  } else {
+    k_owner<<<blocks_for((long long)nx * ny), kThreads, 0, s>>>(nx, ny, R, label, owner);
+  }
   return cudaGetLastError();
 }
 

@@ -45,6 +45,7 @@ struct Store<LBM_F32> {
   using T = float;
   static constexpr int bytes = 4;
   __device__ static __forceinline__ float load(const T* p, size_t i, float) { return __ldg(p + i); }
+  __device__ static __forceinline__ float load_smem(const T* p, int i, float) { return p[i]; }
   __device__ static __forceinline__ void store(T* p, size_t i, float v, float) { p[i] = v; }
 };
 
@@ -54,6 +55,9 @@ struct Store<LBM_F16_DEV> {
   static constexpr int bytes = 2;
   __device__ static __forceinline__ float load(const T* p, size_t i, float base) {
     return base + __half2float(__ldg(p + i));
+  }
+  __device__ static __forceinline__ float load_smem(const T* p, int i, float base) {
+    return base + __half2float(p[i]);
   }
   __device__ static __forceinline__ void store(T* p, size_t i, float v, float base) {
     p[i] = __float2half_rn(v - base);
@@ -66,6 +70,9 @@ struct Store<LBM_BF16_DEV> {
   static constexpr int bytes = 2;
   __device__ static __forceinline__ float load(const T* p, size_t i, float base) {
     return base + __bfloat162float(__ldg(p + i));
+  }
+  __device__ static __forceinline__ float load_smem(const T* p, int i, float base) {
+    return base + __bfloat162float(p[i]);
   }
   __device__ static __forceinline__ void store(T* p, size_t i, float v, float base) {
     p[i] = __float2bfloat16_rn(v - base);
@@ -83,6 +90,7 @@ struct StepParams {
   int nx, ny;
   long long N;           // nx * ny (plane stride)
   int rows_per_chunk;    // rows marched by one CTA
+  int force_generic;     // 1: plain-load kernel even where TMA staging applies; 0/2: automatic
   float tau, inv_tau, G, rho0, inv_rho0;
   float wref[Q];         // w_i * rho_ref (16-bit deviation base)
 };
@@ -91,6 +99,8 @@ struct StepParams {
 cudaError_t launch_step(int storage, const StepParams& p, cudaStream_t s);
 // Launch geometry the fused step uses for a box (for tests/benchmarks).
 void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk, int* block);
+// Whether the TMA-staged step kernel can run on a box of width nx.
+bool step_tma_allowed(int storage, int nx);
 
 // Barrier / field / reduction kernels (barrier.cu).
 struct Workspace {

@@ -65,6 +65,7 @@ SIGNATURES = {
     "lbm_step": (C.c_int, [_vp, C.c_int64]),
     "lbm_steps_done": (C.c_int64, [_vp]),
     "lbm_kernel_launches": (C.c_int64, [_vp]),
+    "lbm_set_step_variant": (C.c_int, [_vp, C.c_int]),
     "lbm_halted": (C.c_int, [_vp]),
     "lbm_fields_bytes": (C.c_size_t, [_vp, C.c_uint32]),
     "lbm_read_fields": (C.c_int, [_vp, C.c_uint32, _vp, C.c_size_t, C.c_int]),
@@ -220,6 +221,10 @@ class Simulation:
             a = np.ascontiguousarray(np.asarray(f, dtype=np.float32))
             assert a.size == 9 * self.nx * self.ny
             self._call("lbm_load_populations", C.c_void_p(a.ctypes.data), 0)
+
+    def set_step_variant(self, variant: int) -> None:
+        """0 automatic, 1 plain-load kernel, 2 TMA-staged kernel."""
+        self._call("lbm_set_step_variant", int(variant))
 
     def step(self, n: int = 1) -> None:
         self._call("lbm_step", C.c_int64(int(n)))

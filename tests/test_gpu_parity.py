@@ -289,3 +289,60 @@ def test_full_size_8192_sampled(storage):
                 if l >= 0 and (best is None or (dx * dx + dy * dy, l) < best):
                     best = (dx * dx + dy * dy, l)
         assert own[y, x] == (best[1] if best else -1)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("nx,ny,barrier", [(528, 70, False), (272, 9, False), (320, 80, True)])
+def test_tma_staged_kernel_matches_plain_kernel_bitwise(storage, nx, ny, barrier):
+    """The TMA-staged fused step (ragged last strips, periodic wrap, barrier
+    mask staged alongside) gives bitwise the plain-load kernel's populations,
+    and the FP32 run stays within 1e-5 of the oracle."""
+    if barrier:
+        b = two_bubbles(nx, ny, R=20, gap=6.0)
+        rho = O.init_bubbles(O.make_params(nx, ny), b, RL, RG, 4.0)
+    else:
+        rho = inputs.noise_density(nx, ny, seed=9)
+    sims = []
+    for variant in (1, 2):
+        s = gpu_sim(nx, ny, rho, storage=storage, barrier=barrier, rho_ref=float(np.mean(rho)))
+        s.set_step_variant(variant)
+        s.step(40)
+        sims.append(s.read("pops", *(["mask"] if barrier else [])))
+    assert np.array_equal(sims[0]["pops"], sims[1]["pops"])
+    if barrier:
+        assert np.array_equal(sims[0]["mask"], sims[1]["mask"]) and sims[0]["mask"].any()
+    if storage == "f32":
+        ref = oracle_sim(nx, ny, rho, barrier=barrier)
+        ref.step(40)
+        err = rel_inf(sims[1]["pops"], ref.f)
+        print(f"tma {nx}x{ny} barrier={barrier}: rel err at step 40 {err:.3e}")
+        assert err < 1e-4 if not barrier else err < TOL["f32"]
+
+
+def test_step_variant_selection_errors():
+    sim = gpu_sim(128, 64, inputs.noise_density(128, 64, seed=1))
+    with pytest.raises(LbmError) as e:
+        sim.set_step_variant(2)  # 128 columns is too narrow for the staged kernel
+    assert e.value.code == 6
+    with pytest.raises(LbmError):
+        sim.set_step_variant(3)
+    sim.set_step_variant(1)
+    sim.step(1)
+
+
+@pytest.mark.parametrize("R", [0, 2, 6, 17])
+def test_owner_zone_radius_sweep(R):
+    """Owners and masks bit-exact against the oracle for several zone radii
+    (R <= 16 uses the tiled search, R = 17 the plain window search)."""
+    nx, ny = 160, 80
+    b = two_bubbles(nx, ny, gap=6.0)
+    P = O.make_params(nx, ny, barrier=True, zone_radius=R)
+    rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
+    sim = gpu_sim(nx, ny, bubbles=b, barrier=True, zone_radius=R)
+    ref = oracle_sim(nx, ny, rho0, barrier=True, zone_radius=R)
+    sim.step(5)
+    ref.step(5)
+    got = sim.read("owner", "mask", "pops")
+    assert np.array_equal(got["owner"], ref.owner)
+    assert np.array_equal(got["mask"], ref.mask)
+    assert rel_inf(got["pops"], ref.f) < TOL["f32"]
