@@ -8,28 +8,120 @@
 // The buffer read by a step holds the post-collision populations of the
 // previous step at their source cell; the step pulls f_i(x) from x - e_i.
 //
-// Geometry: a CTA owns a strip of BX consecutive columns and marches down
-// rows_per_chunk rows. For every row it pulls the populations of its cells
-// (plus one halo column each side), forms rho and psi once per cell, and
-// writes psi into a four-row ring in shared memory. One barrier later the
-// ring holds psi for rows r-2..r, so the force and collision of row r-1 can
-// run on the populations kept in registers from the previous iteration. The
-// only re-read of populations is the halo (two columns per strip, two rows
-// per chunk), which hits L2.
+// Both kernels march a strip of kBX columns down a chunk of rows. For every
+// row they pull the populations of the strip's cells and of one halo column
+// on each side, form rho and psi once per cell, and put psi into a four-row
+// ring in shared memory; one barrier later the ring holds psi for rows r-2..r
+// and the force and collision of row r-1 run on the populations kept in
+// registers. All per-cell arithmetic lives in the shared device functions
+// below, so the two kernels give bitwise the same populations.
+//
+//  - k_step_strip: plain global loads; any box size.
+//  - k_step_tma: the nine source rows of every output row (with halo) are
+//    copied into a ring of shared-memory stages by cp.async.bulk, issued
+//    NSTAGE-1 rows ahead by a ninth warp that also computes the two halo
+//    cells, so the eight compute warps are balanced and the bytes in flight
+//    do not depend on occupancy. Needs nx % 16 == 0 and nx >= kBX + 16.
 #include "lbm_internal.cuh"
 
 namespace lbm {
 namespace {
 
-constexpr int kBX = 256;
+constexpr int kBX = 256;           // columns per strip (= compute threads)
+constexpr int kTmaThreads = kBX + 32;
+constexpr float kW1 = 1.0f / 9.0f, kW5 = 1.0f / 36.0f, kW0 = 4.0f / 9.0f;
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// ---------------------------------------------------------------- cell math
+// Eq. 11: rho and j from the nine incoming populations.
+__device__ __forceinline__ void moments9(const float f[Q], float& rho, float& jx, float& jy) {
+  rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  jx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
+  jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
+}
+
+// Eq. 30.
+__device__ __forceinline__ float psi_of(float rho, const StepParams& p) {
+  return p.rho0 * (1.0f - __expf(-rho * p.inv_rho0));
+}
+
+// Eq. 22 with the barrier substitution: s[i] holds psi(x + e_i), or psi(x)
+// where the edge is blocked.
+__device__ __forceinline__ void force_of(const float s[Q], float psi_c, float G, float& Fx, float& Fy) {
+  const float sx = kW1 * (s[1] - s[3]) + kW5 * ((s[5] - s[7]) + (s[8] - s[6]));
+  const float sy = kW1 * (s[2] - s[4]) + kW5 * ((s[5] - s[7]) + (s[6] - s[8]));
+  Fx = -G * psi_c * sx;
+  Fy = -G * psi_c * sy;
+}
+
+// Eqs. 39-40 (u_eq = (j + tau F)/rho), Eq. 14 evaluated by opposite pairs,
+// Eq. 18 (BGK). f holds the incoming populations and receives the outgoing.
+template <bool TAU_ONE>
+__device__ __forceinline__ void collide(float f[Q], float rho, float jx, float jy, float Fx, float Fy,
+                                        const StepParams& p, int& bad) {
+  const float ir = __frcp_rn(rho);
+  const float ux = (jx + p.tau * Fx) * ir;
+  const float uy = (jy + p.tau * Fy) * ir;
+  bad |= !(rho > 0.f) | !(fabsf(ux) + fabsf(uy) < 1e30f);
+  const float a = rho * (1.0f - 1.5f * (ux * ux + uy * uy));
+  const float r3 = 3.0f * rho, r45 = 4.5f * rho;
+  float feq[Q];
+  feq[0] = kW0 * a;
+  {
+    const float s = a + r45 * ux * ux, t = r3 * ux;
+    feq[1] = kW1 * (s + t);
+    feq[3] = kW1 * (s - t);
+  }
+  {
+    const float s = a + r45 * uy * uy, t = r3 * uy;
+    feq[2] = kW1 * (s + t);
+    feq[4] = kW1 * (s - t);
+  }
+  {
+    const float e = ux + uy;
+    const float s = a + r45 * e * e, t = r3 * e;
+    feq[5] = kW5 * (s + t);
+    feq[7] = kW5 * (s - t);
+  }
+  {
+    const float e = uy - ux;
+    const float s = a + r45 * e * e, t = r3 * e;
+    feq[6] = kW5 * (s + t);
+    feq[8] = kW5 * (s - t);
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = TAU_ONE ? feq[i] : f[i] + (feq[i] - f[i]) * p.inv_tau;
+}
+
+// Force + collision + store of one cell from the psi ring.
+template <int S, bool MASKED, bool TAU_ONE>
+__device__ __forceinline__ void finish_cell(float f[Q], float rho, float jx, float jy, unsigned m,
+                                            const float (*ring)[kBX + 2], int sm, int s0, int sp, int jc,
+                                            const StepParams& p, typename Store<S>::T* __restrict__ dst,
+                                            size_t base, int& bad) {
+  const float psi_c = ring[s0][jc];
+  float s[Q];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) s[i] = ring[cy(i) > 0 ? sp : (cy(i) < 0 ? sm : s0)][jc + cx(i)];
+  if (MASKED && m) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if ((m >> (i - 1)) & 1u) s[i] = psi_c;
+  }
+  float Fx, Fy;
+  force_of(s, psi_c, p.G, Fx, Fy);
+  collide<TAU_ONE>(f, rho, jx, jy, Fx, Fy, p, bad);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Store<S>::store(dst, (size_t)i * p.N + base, f[i], p.wref[i]);
+}
+
+// ---------------------------------------------------------------- plain-load kernel
 template <int S>
-__device__ __forceinline__ void pull_cell(const typename Store<S>::T* __restrict__ src,
-                                          const StepParams& p, long long rowm, long long row0,
-                                          long long rowp, int xm, int x, int xp, float f[Q]) {
-  // f_i(x, r) = f_i^out(x - c_i, r - c_iy): rows r-1 (c_y = +1), r, r+1 (c_y = -1)
+__device__ __forceinline__ void pull_cell(const typename Store<S>::T* __restrict__ src, const StepParams& p,
+                                          long long rowm, long long row0, long long rowp, int xm, int x, int xp,
+                                          float f[Q]) {
+  // f_i(x, r) = f_i^out(x - c_ix, r - c_iy): rows r-1 (c_iy = +1), r, r+1 (c_iy = -1)
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const long long row = cy(i) > 0 ? rowm : (cy(i) < 0 ? rowp : row0);
@@ -38,11 +130,7 @@ __device__ __forceinline__ void pull_cell(const typename Store<S>::T* __restrict
   }
 }
 
-__device__ __forceinline__ float psi_of(float rho, const StepParams& p) {
-  return p.rho0 * (1.0f - expf(-rho * p.inv_rho0));
-}
-
-template <int S, bool MASKED>
+template <int S, bool MASKED, bool TAU_ONE>
 __global__ void __launch_bounds__(kBX) k_step_strip(const StepParams p) {
   using T = typename Store<S>::T;
   const T* __restrict__ src = static_cast<const T*>(p.src);
@@ -61,8 +149,6 @@ __global__ void __launch_bounds__(kBX) k_step_strip(const StepParams p) {
 
   const int xc = active ? x : last;
   const int xm = wrapi(xc - 1, nx), xp = wrapi(xc + 1, nx);
-  const bool do_left = tid == 0;
-  const bool do_right = x == last;
   const int xl = wrapi(x0 - 1, nx), xlm = wrapi(x0 - 2, nx);
   const int xr = wrapi(last + 1, nx), xrp = wrapi(last + 2, nx);
   const int jc = tid + 1;
@@ -70,67 +156,36 @@ __global__ void __launch_bounds__(kBX) k_step_strip(const StepParams p) {
   float fprev[Q];
   float rho_prev = 1.f, jx_prev = 0.f, jy_prev = 0.f;
   int bad = 0;
-
   for (int r = y0 - 1, k = 0; r <= y1; ++r, ++k) {
     const int rr = wrapi(r, ny);
     const long long row0 = (long long)rr * nx;
     const long long rowm = (long long)wrapi(rr - 1, ny) * nx;
     const long long rowp = (long long)wrapi(rr + 1, ny) * nx;
-    const int slot = k & 3;
     float f[Q];
     float rho = 1.f, jx = 0.f, jy = 0.f;
     if (active) {
       pull_cell<S>(src, p, rowm, row0, rowp, xm, x, xp, f);
-      rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-      jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-      jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-      ring[slot][jc] = psi_of(rho, p);
+      moments9(f, rho, jx, jy);
+      ring[k & 3][jc] = psi_of(rho, p);
     }
-    if (do_left) {
-      float h[Q];
-      pull_cell<S>(src, p, rowm, row0, rowp, xlm, xl, x0 == 0 ? wrapi(x0, nx) : x0, h);
-      const float rh = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-      ring[slot][0] = psi_of(rh, p);
+    if (tid == 0) {
+      float h[Q], rh, hx, hy;
+      pull_cell<S>(src, p, rowm, row0, rowp, xlm, xl, x0, h);
+      moments9(h, rh, hx, hy);
+      ring[k & 3][0] = psi_of(rh, p);
     }
-    if (do_right) {
-      float h[Q];
+    if (x == last) {
+      float h[Q], rh, hx, hy;
       pull_cell<S>(src, p, rowm, row0, rowp, last, xr, xrp, h);
-      const float rh = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-      ring[slot][last - x0 + 2] = psi_of(rh, p);
+      moments9(h, rh, hx, hy);
+      ring[k & 3][last - x0 + 2] = psi_of(rh, p);
     }
     __syncthreads();
     if (k >= 2 && active) {
-      // force, equilibrium and collision of row rc = r - 1
       const int rc = r - 1;
-      const int sm = (k - 2) & 3, s0 = (k - 1) & 3, sp = k & 3;
-      const float psi_c = ring[s0][jc];
-      float sx = 0.f, sy = 0.f;
-      unsigned m = 0;
-      if (MASKED) m = p.mask[(size_t)rc * nx + x];
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int sl = cy(i) > 0 ? sp : (cy(i) < 0 ? sm : s0);
-        float s = ring[sl][jc + cx(i)];
-        if (MASKED && ((m >> (i - 1)) & 1u)) s = psi_c;
-        const float ws = static_cast<float>(wq(i)) * s;
-        if (cx(i) != 0) sx += cx(i) > 0 ? ws : -ws;
-        if (cy(i) != 0) sy += cy(i) > 0 ? ws : -ws;
-      }
-      const float Fx = -p.G * psi_c * sx;
-      const float Fy = -p.G * psi_c * sy;
-      const float inv_rho = 1.0f / rho_prev;
-      const float ux = (jx_prev + p.tau * Fx) * inv_rho;
-      const float uy = (jy_prev + p.tau * Fy) * inv_rho;
-      const float uu = 1.5f * (ux * ux + uy * uy);
-      bad |= !(rho_prev > 0.f) | !(fabsf(ux) + fabsf(uy) < 1e30f);
-      const long long base = (long long)rc * nx + x;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const float eu = cx(i) * ux + cy(i) * uy;
-        const float feq = static_cast<float>(wq(i)) * rho_prev * (1.0f + 3.0f * eu + 4.5f * eu * eu - uu);
-        const float fo = fprev[i] + (feq - fprev[i]) * p.inv_tau;
-        Store<S>::store(dst, (size_t)i * p.N + base, fo, p.wref[i]);
-      }
+      const unsigned m = MASKED ? p.mask[(size_t)rc * nx + x] : 0u;
+      finish_cell<S, MASKED, TAU_ONE>(fprev, rho_prev, jx_prev, jy_prev, m, ring, (k - 2) & 3, (k - 1) & 3,
+                                      k & 3, jc, p, dst, (size_t)rc * nx + x, bad);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) fprev[i] = f[i];
@@ -141,18 +196,9 @@ __global__ void __launch_bounds__(kBX) k_step_strip(const StepParams p) {
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
 }
 
-// ---------------------------------------------------------------------------
-// TMA-staged variant. The same strip/row march, but the populations of each
-// output row (for plane i: source row r - c_iy, columns x0 - PAD .. x0 + W +
-// PAD, wrapped) are brought into a ring of NSTAGE shared-memory stages by
-// cp.async.bulk copies that one thread issues NSTAGE - 2 rows ahead; an
-// mbarrier per stage counts the bytes in. Every thread then reads its pulls
-// from shared memory, so the number of bytes in flight no longer depends on
-// occupancy. Halo columns arrive inside the same copies. Needs nx % 16 == 0
-// and nx >= W + 2 PAD (16-byte aligned, at most two pieces per row copy).
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+// ---------------------------------------------------------------- TMA-staged kernel
+__device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -182,7 +228,7 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait: false if the phase did not complete within `limit_ns`.
+// Bounded wait: false if the phase did not complete within limit_ns.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
@@ -203,25 +249,27 @@ template <int S>
 struct TmaGeom {
   using T = typename Store<S>::T;
   static constexpr int E = sizeof(T);
-  static constexpr int PAD = 16 / E;             // halo pad in elements: 16 bytes
-  static constexpr int WIN = kBX + 2 * PAD;      // elements per staged plane row
-  static constexpr int ROW_BYTES = WIN * E;      // multiple of 16
+  static constexpr int PAD = 16 / E;         // halo pad in elements: 16 bytes
+  static constexpr int WIN = kBX + 2 * PAD;  // elements per staged plane row
+  static constexpr int ROW_BYTES = WIN * E;  // multiple of 16
 };
 
-// Copy `len` elements of a periodic row starting at column `start` (may be
-// negative) into dst: one or two pieces.
+// Copy len elements of a periodic row starting at column start (may be
+// negative) into dst, in one or two pieces (len <= row length).
 template <typename T>
-__device__ __forceinline__ void copy_row_wrapped(T* dst, const T* row, int start, int len, int nx,
-                                                 uint64_t* bar) {
-  int s0 = start < 0 ? start + nx : start;
+__device__ __forceinline__ void copy_row_wrapped(T* dst, const T* row, int start, int len, int nx, uint64_t* bar) {
+  const int s0 = start < 0 ? start + nx : start;
   const int first = min(len, nx - s0);
   bulk_g2s(dst, row + s0, (uint32_t)(first * sizeof(T)), bar);
   if (first < len) bulk_g2s(dst + first, row, (uint32_t)((len - first) * sizeof(T)), bar);
 }
 
+// Issued by the lanes of the ninth warp: lane 0 arms the stage's mbarrier,
+// lanes 0..8 copy plane `lane`, lane 9 copies the mask row.
 template <int S, bool MASKED, int NSTAGE>
 __device__ __forceinline__ void issue_stage(const StepParams& p, const typename Store<S>::T* src,
-                                            unsigned char* stages, uint64_t* bars, int k, int y0, int x0) {
+                                            unsigned char* stages, uint64_t* bars, int k, int y0, int x0,
+                                            int lane) {
   using G = TmaGeom<S>;
   using T = typename G::T;
   constexpr uint32_t STAGE_BYTES = Q * G::ROW_BYTES + (MASKED ? kBX : 0);
@@ -230,23 +278,30 @@ __device__ __forceinline__ void issue_stage(const StepParams& p, const typename 
   uint64_t* bar = bars + slot;
   const int r = y0 - 1 + k;
   const int ny = p.ny, nx = p.nx;
-  mbar_expect_tx(bar, STAGE_BYTES);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    int g = r - cy(i);
+  if (lane < Q + (MASKED ? 1 : 0)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (lane == 0) mbar_expect_tx(bar, STAGE_BYTES);
+  __syncwarp();
+  if (lane < Q) {
+    const int i = lane;
+    const int ciy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    int g = r - ciy;
     g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
     g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
     const T* row = src + (size_t)i * p.N + (size_t)g * nx;
     copy_row_wrapped<T>(reinterpret_cast<T*>(st + i * G::ROW_BYTES), row, x0 - G::PAD, G::WIN, nx, bar);
-  }
-  if (MASKED) {  // columns x0 .. x0 + W (a ragged last strip wraps; those bytes are unused)
-    int g = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+  } else if (MASKED && lane == Q) {  // columns x0 .. x0+kBX (a ragged strip wraps; unused)
+    const int g = r < 0 ? r + ny : (r >= ny ? r - ny : r);
     copy_row_wrapped<uint8_t>(st + Q * G::ROW_BYTES, p.mask + (size_t)g * nx, x0, kBX, nx, bar);
   }
 }
 
-template <int S, bool MASKED, int NSTAGE, int MINB>
-__global__ void __launch_bounds__(kBX, MINB) k_step_tma(const StepParams p) {
+template <int S, bool MASKED, int NSTAGE>
+constexpr size_t tma_smem_bytes_c() {
+  return (size_t)NSTAGE * (Q * TmaGeom<S>::ROW_BYTES + (MASKED ? kBX : 0)) + 4 * (kBX + 2) * 4 + NSTAGE * 8 + 16;
+}
+
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma(const StepParams p) {
   using G = TmaGeom<S>;
   using T = typename G::T;
   constexpr int STAGE_BYTES = Q * G::ROW_BYTES + (MASKED ? kBX : 0);
@@ -260,13 +315,15 @@ __global__ void __launch_bounds__(kBX, MINB) k_step_tma(const StepParams p) {
   T* __restrict__ dst = static_cast<T*>(p.dst);
   const int nx = p.nx, ny = p.ny;
   const int tid = threadIdx.x;
+  const bool helper = tid >= kBX;  // the ninth warp
+  const int lane = tid & 31;
   const int x0 = blockIdx.x * kBX;
-  const int width = min(kBX, nx - x0);  // active columns of this strip
-  const bool active = tid < width;
+  const int width = min(kBX, nx - x0);
+  const bool active = !helper && tid < width;
   const int y0 = blockIdx.y * p.rows_per_chunk;
   const int y1 = min(y0 + p.rows_per_chunk, ny);
   if (y0 >= y1) return;
-  const int nst = (y1 - y0) + 2;  // stages: rows y0-1 .. y1
+  const int nst = (y1 - y0) + 2;  // stages = rows y0-1 .. y1
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) mbar_init(bars + s, 1);
@@ -274,103 +331,78 @@ __global__ void __launch_bounds__(kBX, MINB) k_step_tma(const StepParams p) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0)
-    for (int k = 0; k < NSTAGE - 2 && k < nst; ++k) issue_stage<S, MASKED, NSTAGE>(p, src, stages, bars, k, y0, x0);
+  if (helper)
+    for (int k = 0; k < NSTAGE - 1 && k < nst; ++k) issue_stage<S, MASKED, NSTAGE>(p, src, stages, bars, k, y0, x0, lane);
+
+  // halo lanes of the helper warp: lanes 0..8 pull plane `lane` of the left
+  // halo cell (column x0-1), lanes 16..24 of the right one (column x0+width)
+  const int hplane = lane & 15;
+  const bool hlane = helper && hplane < Q;
+  const int hcx = (hplane == 1 || hplane == 5 || hplane == 8) ? 1 : ((hplane == 3 || hplane == 6 || hplane == 7) ? -1 : 0);
+  const int hpos = (lane < 16 ? G::PAD - 1 : G::PAD + width) - hcx;
+  float hbase = 0.f;  // selected without dynamic indexing of the parameter block
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (hlane && i == hplane) hbase = p.wref[i];
 
   const int jc = tid + 1;
-  const int pos = G::PAD + tid;  // window position of this thread's cell
+  const int pos = G::PAD + tid;
+  float fprev[Q];
   float rho_prev = 1.f, jx_prev = 0.f, jy_prev = 0.f;
+  unsigned m_prev = 0;
   int bad = 0;
   int k_abort = 0;
   for (int k = 0; k < nst; ++k) {
     const int slot = k % NSTAGE;
     const unsigned char* st = stages + (size_t)slot * STAGE_BYTES;
     if (!mbar_wait(bars + slot, (uint32_t)((k / NSTAGE) & 1))) *abort_flag = 1;
+    float f[Q];
     float rho = 1.f, jx = 0.f, jy = 0.f;
-    {
-      float f[Q];
-      if (active) {
+    unsigned m = 0;
+    if (active) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-          f[i] = Store<S>::load_smem(reinterpret_cast<const T*>(st + i * G::ROW_BYTES), pos - cx(i), p.wref[i]);
-        rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-        jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-        ring[k & 3][jc] = psi_of(rho, p);
-      }
-      // halo cells: column x0 - 1 (window PAD - 1) and x0 + width (window PAD + width)
-      if (tid == 0 || tid == width - 1) {
-        const int hp = tid == 0 ? G::PAD - 1 : G::PAD + width;
-        float h[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-          h[i] = Store<S>::load_smem(reinterpret_cast<const T*>(st + i * G::ROW_BYTES), hp - cx(i), p.wref[i]);
-        const float rh = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-        ring[k & 3][tid == 0 ? 0 : width + 1] = psi_of(rh, p);
-      }
-      if (tid == 0 && width == 1) {  // a one-column strip needs both halos from this thread
-        float h[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-          h[i] = Store<S>::load_smem(reinterpret_cast<const T*>(st + i * G::ROW_BYTES), G::PAD + 1 - cx(i), p.wref[i]);
-        const float rh = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-        ring[k & 3][2] = psi_of(rh, p);
-      }
+      for (int i = 0; i < Q; ++i)
+        f[i] = Store<S>::load_smem(reinterpret_cast<const T*>(st + i * G::ROW_BYTES), pos - cx(i), p.wref[i]);
+      moments9(f, rho, jx, jy);
+      ring[k & 3][jc] = psi_of(rho, p);
+      if (MASKED) m = st[Q * G::ROW_BYTES + tid];
+    } else if (helper) {
+      // same summation order as moments9: ((f0+f1)+(f2+f3)) + ((f4+f5)+(f6+f7)) + f8
+      const float v = hlane ? Store<S>::load_smem(reinterpret_cast<const T*>(st + hplane * G::ROW_BYTES), hpos, hbase)
+                            : 0.f;
+      const float t1 = v + __shfl_xor_sync(0xffffffffu, v, 1);
+      const float t2 = t1 + __shfl_xor_sync(0xffffffffu, t1, 2);
+      const float t3 = t2 + __shfl_xor_sync(0xffffffffu, t2, 4);
+      const float rh = t3 + __shfl_xor_sync(0xffffffffu, t2, 8);
+      if (lane == 0) ring[k & 3][0] = psi_of(rh, p);
+      if (lane == 16) ring[k & 3][width + 1] = psi_of(rh, p);
     }
     __syncthreads();
     if (*abort_flag) {
       k_abort = k;
       break;
     }
-    if (tid == 0 && k + NSTAGE - 2 < nst) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_stage<S, MASKED, NSTAGE>(p, src, stages, bars, k + NSTAGE - 2, y0, x0);
+    if (helper) {
+      if (k + NSTAGE - 1 < nst) issue_stage<S, MASKED, NSTAGE>(p, src, stages, bars, k + NSTAGE - 1, y0, x0, lane);
+    } else if (k >= 2 && active) {
+      const int rc = y0 + k - 2;  // row collided now
+      finish_cell<S, MASKED, TAU_ONE>(fprev, rho_prev, jx_prev, jy_prev, m_prev, ring, (k - 2) & 3, (k - 1) & 3,
+                                      k & 3, jc, p, dst, (size_t)rc * nx + x0 + tid, bad);
     }
-    if (k >= 2 && active) {
-      const int rc = y0 - 1 + k - 1;  // row collided now
-      const unsigned char* sp = stages + (size_t)((k - 1) % NSTAGE) * STAGE_BYTES;
-      const int sm = (k - 2) & 3, s0 = (k - 1) & 3, s1 = k & 3;
-      const float psi_c = ring[s0][jc];
-      unsigned m = 0;
-      if (MASKED) m = sp[Q * G::ROW_BYTES + tid];
-      float sx = 0.f, sy = 0.f;
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int sl = cy(i) > 0 ? s1 : (cy(i) < 0 ? sm : s0);
-        float s = ring[sl][jc + cx(i)];
-        if (MASKED && ((m >> (i - 1)) & 1u)) s = psi_c;
-        const float ws = static_cast<float>(wq(i)) * s;
-        if (cx(i) != 0) sx += cx(i) > 0 ? ws : -ws;
-        if (cy(i) != 0) sy += cy(i) > 0 ? ws : -ws;
-      }
-      const float Fx = -p.G * psi_c * sx;
-      const float Fy = -p.G * psi_c * sy;
-      const float inv_rho = 1.0f / rho_prev;
-      const float ux = (jx_prev + p.tau * Fx) * inv_rho;
-      const float uy = (jy_prev + p.tau * Fy) * inv_rho;
-      const float uu = 1.5f * (ux * ux + uy * uy);
-      bad |= !(rho_prev > 0.f) | !(fabsf(ux) + fabsf(uy) < 1e30f);
-      const size_t base = (size_t)rc * nx + x0 + tid;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const float fi = Store<S>::load_smem(reinterpret_cast<const T*>(sp + i * G::ROW_BYTES), pos - cx(i), p.wref[i]);
-        const float eu = cx(i) * ux + cy(i) * uy;
-        const float feq = static_cast<float>(wq(i)) * rho_prev * (1.0f + 3.0f * eu + 4.5f * eu * eu - uu);
-        Store<S>::store(dst, (size_t)i * p.N + base, fi + (feq - fi) * p.inv_tau, p.wref[i]);
-      }
-    }
+    for (int i = 0; i < Q; ++i) fprev[i] = f[i];
     rho_prev = rho;
     jx_prev = jx;
     jy_prev = jy;
+    m_prev = m;
   }
   if (*abort_flag) {
     // a stage never completed: record it, then wait (bounded) for the copies
     // of every stage issued and not consumed before the CTA leaves
     if (tid == 0) {
       atomicOr(p.flags + FLAG_TIMEOUT, 1);
-      const int issued = min(nst, k_abort + NSTAGE - 2);
-      for (int q = k_abort; q < issued; ++q)
-        mbar_wait(bars + q % NSTAGE, (uint32_t)((q / NSTAGE) & 1), 500000000ull);
+      const int issued = min(nst, k_abort + NSTAGE - 1);
+      for (int q = k_abort; q < issued; ++q) mbar_wait(bars + q % NSTAGE, (uint32_t)((q / NSTAGE) & 1), 500000000ull);
     }
     __syncthreads();
     return;
@@ -379,46 +411,78 @@ __global__ void __launch_bounds__(kBX, MINB) k_step_tma(const StepParams p) {
 }
 
 template <int S>
-constexpr int tma_stages() { return S == LBM_F32 ? 6 : 10; }
-template <int S>
-constexpr int tma_minblocks() { return S == LBM_F32 ? 3 : 4; }
-
-template <int S, bool MASKED>
-size_t tma_smem_bytes() {
-  using G = TmaGeom<S>;
-  return (size_t)tma_stages<S>() * (Q * G::ROW_BYTES + (MASKED ? kBX : 0)) + 4 * (kBX + 2) * 4 +
-         tma_stages<S>() * 8 + 16;
-}
+constexpr int tma_stages() { return S == LBM_F32 ? 5 : 8; }
+constexpr int kTmaMinBlocks = 3;
 
 template <int S>
 bool tma_ok(int nx) {
   return nx % 16 == 0 && nx >= TmaGeom<S>::WIN;
 }
 
-template <int S, bool MASKED>
-cudaError_t launch_tma(const StepParams& q, dim3 grid, cudaStream_t s) {
-  auto kern = k_step_tma<S, MASKED, tma_stages<S>(), tma_minblocks<S>()>;
-  const size_t smem = tma_smem_bytes<S, MASKED>();
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<grid, kBX, smem, s>>>(q);
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 152;
+  }
+  return n;
+}
+
+// Rows per chunk so that all CTAs are resident at once (one wave).
+void tma_geometry(int nx, int ny, int resident_per_sm, int* gx, int* gy, int* rows) {
+  *gx = (nx + kBX - 1) / kBX;
+  const int resident = resident_per_sm * sm_count();
+  int g = resident / *gx;
+  if (g < 1) g = 1;
+  if (g > ny) g = ny;
+  *rows = (ny + g - 1) / g;
+  *gy = (ny + *rows - 1) / *rows;
+}
+
+template <int S, bool MASKED, bool TAU_ONE>
+cudaError_t launch_tma(const StepParams& p, cudaStream_t s) {
+  constexpr int NS = tma_stages<S>();
+  auto kern = k_step_tma<S, MASKED, TAU_ONE, NS, kTmaMinBlocks>;
+  constexpr size_t smem = tma_smem_bytes_c<S, MASKED, NS>();
+  static int resident = 0;  // per instantiation
+  if (resident == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTmaThreads, smem);
+    if (e != cudaSuccess) return e;
+    resident = occ > 0 ? occ : 1;
+  }
+  int gx, gy, rows;
+  tma_geometry(p.nx, p.ny, resident, &gx, &gy, &rows);
+  StepParams q = p;
+  q.rows_per_chunk = rows;
+  kern<<<dim3(gx, gy), kTmaThreads, smem, s>>>(q);
   return cudaGetLastError();
 }
 
-template <int S>
-cudaError_t launch_typed(const StepParams& p, cudaStream_t s) {
+template <int S, bool MASKED, bool TAU_ONE>
+cudaError_t launch_strip(const StepParams& p, cudaStream_t s) {
   int gx, gy, rows, block;
   step_geometry(p.nx, p.ny, &gx, &gy, &rows, &block);
   StepParams q = p;
   q.rows_per_chunk = rows;
-  dim3 grid(gx, gy);
-  if (p.force_generic != 1 && tma_ok<S>(p.nx))
-    return p.mask ? launch_tma<S, true>(q, grid, s) : launch_tma<S, false>(q, grid, s);
-  if (p.mask)
-    k_step_strip<S, true><<<grid, block, 0, s>>>(q);
-  else
-    k_step_strip<S, false><<<grid, block, 0, s>>>(q);
+  k_step_strip<S, MASKED, TAU_ONE><<<dim3(gx, gy), block, 0, s>>>(q);
   return cudaGetLastError();
+}
+
+template <int S, bool MASKED, bool TAU_ONE>
+cudaError_t launch_variant(const StepParams& p, cudaStream_t s) {
+  if (p.force_generic != 1 && tma_ok<S>(p.nx)) return launch_tma<S, MASKED, TAU_ONE>(p, s);
+  return launch_strip<S, MASKED, TAU_ONE>(p, s);
+}
+
+template <int S>
+cudaError_t launch_typed(const StepParams& p, cudaStream_t s) {
+  const bool tau_one = p.tau == 1.0f;
+  if (p.mask) return tau_one ? launch_variant<S, true, true>(p, s) : launch_variant<S, true, false>(p, s);
+  return tau_one ? launch_variant<S, false, true>(p, s) : launch_variant<S, false, false>(p, s);
 }
 
 }  // namespace
@@ -438,7 +502,8 @@ void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk
 }
 
 bool step_tma_allowed(int storage, int nx) {
-  return storage == LBM_F32 ? tma_ok<LBM_F32>(nx) : (storage == LBM_F16_DEV ? tma_ok<LBM_F16_DEV>(nx) : tma_ok<LBM_BF16_DEV>(nx));
+  return storage == LBM_F32 ? tma_ok<LBM_F32>(nx)
+                            : (storage == LBM_F16_DEV ? tma_ok<LBM_F16_DEV>(nx) : tma_ok<LBM_BF16_DEV>(nx));
 }
 
 cudaError_t launch_step(int storage, const StepParams& p, cudaStream_t s) {
