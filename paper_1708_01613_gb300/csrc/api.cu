@@ -24,8 +24,8 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t pops[2], rho, label, owner, mask, open, sgn, flags, partials, scalars, total;
-  int nparts;
+  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, flags, partials, scalars, total;
+  int nparts, ntiles;
 };
 
 bool valid_config(const lbm_config* c, char* why, size_t n) {
@@ -69,6 +69,8 @@ Layout layout_for(const lbm_config& c) {
     L.mask = take(N);
     L.open = take(N);
     L.sgn = take(N);
+    L.ntiles = relabel_tile_count(c.nx, c.ny);
+    L.tiles = take(3 * (size_t)L.ntiles);  // gas, active, previous active
   }
   L.flags = take(sizeof(int) * FLAG_COUNT);
   L.nparts = mass_partials_needed();
@@ -101,6 +103,7 @@ struct lbm_handle {
   uint8_t* mask() { return cfg.barrier ? reinterpret_cast<uint8_t*>(ws + L.mask) : nullptr; }
   uint8_t* open() { return cfg.barrier ? reinterpret_cast<uint8_t*>(ws + L.open) : nullptr; }
   int8_t* sgn() { return cfg.barrier ? reinterpret_cast<int8_t*>(ws + L.sgn) : nullptr; }
+  uint8_t* tiles(int k) { return reinterpret_cast<uint8_t*>(ws + L.tiles) + (size_t)k * L.ntiles; }
   int* flags() { return reinterpret_cast<int*>(ws + L.flags); }
   double* partials() { return reinterpret_cast<double*>(ws + L.partials); }
   double* scalars() { return reinterpret_cast<double*>(ws + L.scalars); }
@@ -163,6 +166,7 @@ int reset_state(lbm_handle* h) {
     CUDA_TRY(h, cudaMemsetAsync(h->open(), 0, h->N(), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->sgn(), 0, h->N(), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->owner(), 0xff, 4 * h->N(), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->tiles(0), 0, 3 * (size_t)h->L.ntiles, h->stream));
   }
   h->t = 0;
   h->halted = 0;
@@ -173,6 +177,13 @@ int reset_state(lbm_handle* h) {
 int relabel(lbm_handle* h) {
   const FieldParams fp = field_params(h);
   const lbm_config& c = h->cfg;
+  if (relabel_tiled_ok(c.nx, c.ny, c.zone_radius)) {
+    CUDA_TRY(h, launch_relabel_tiled(fp, (float)c.gas_threshold, c.zone_radius, (float)c.G, (float)c.rho0,
+                                     (float)c.rupture_eps, h->rho(), h->label(), h->owner(), h->sgn(), h->open(),
+                                     h->mask(), h->tiles(0), h->tiles(1), h->tiles(2), h->flags(), h->stream));
+    h->launches += 7;
+    return LBM_OK;
+  }
   CUDA_TRY(h, launch_density(fp, h->rho(), h->stream));
   CUDA_TRY(h, launch_labels(fp, h->rho(), (float)c.gas_threshold, h->label(), h->flags(), h->stream));
   CUDA_TRY(h, launch_owner(c.nx, c.ny, c.zone_radius, h->label(), h->owner(), h->stream));

@@ -450,6 +450,191 @@ __global__ void __launch_bounds__(kThreads) k_stats_partial(long long N, const i
   block_reduce_store<kStatVals>(v, partials);
 }
 
+// ---------------------------------------------------------------------------
+// Tiled barrier pipeline (boxes with nx % 32 == 0 and ny % 8 == 0). The box is
+// cut into 32 x 8 tiles. The density pass also writes the initial labels and
+// one gas flag per tile; a tile is active when a gas cell lies within the
+// tile span that R_z can reach. Owners, rupture signs and masks can only be
+// non-trivial in active tiles (a defined owner needs gas within R_z), so the
+// later kernels skip every tile that is inactive now and was inactive at the
+// previous relabel: its owner/sign/mask are already -1/0/0. A tile that just
+// became inactive is reset to those values. Results equal the untiled kernels.
+constexpr int kTX = 32, kTY = 8;
+
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+template <int S>
+__global__ void __launch_bounds__(kTX * kTY) kt_density_label(const FieldParams fp, float th, float* __restrict__ rho,
+                                                              int32_t* __restrict__ L, uint8_t* __restrict__ tile_gas) {
+  using T = typename Store<S>::T;
+  const T* p = static_cast<const T*>(fp.pops);
+  const int nx = fp.nx, ny = fp.ny;
+  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
+  const size_t r0 = (size_t)y * nx, rm = (size_t)wrap1(y - 1, ny) * nx, rp = (size_t)wrap1(y + 1, ny) * nx;
+  float f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+    const int xs = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : x);
+    f[i] = Store<S>::load(p, (size_t)i * fp.N + row + xs, fp.wref[i]);
+  }
+  const float r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const size_t c = r0 + x;
+  rho[c] = r;
+  const bool gas = r < th;
+  L[c] = gas ? (int32_t)c : -1;
+  const int any = __syncthreads_or(gas);
+  if (threadIdx.x == 0 && threadIdx.y == 0) tile_gas[blockIdx.y * gridDim.x + blockIdx.x] = (uint8_t)(any != 0);
+}
+
+__global__ void kt_active(const uint8_t* __restrict__ gas, uint8_t* __restrict__ active, int ntx, int nty, int spx,
+                          int spy) {
+  const int ntiles = ntx * nty;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+    const int ty = t / ntx, tx = t - ty * ntx;
+    int a = 0;
+    for (int dy = -spy; dy <= spy && !a; ++dy) {
+      const int yy = wrapi(ty + dy, nty);
+      for (int dx = -spx; dx <= spx; ++dx) a |= gas[yy * ntx + wrapi(tx + dx, ntx)];
+    }
+    active[t] = (uint8_t)(a != 0);
+  }
+}
+
+__global__ void __launch_bounds__(kTX * kTY) kt_union(int nx, int ny, int32_t* L, const uint8_t* __restrict__ tile_gas,
+                                                      int* flags) {
+  if (!tile_gas[blockIdx.y * gridDim.x + blockIdx.x]) return;
+  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  const int c = y * nx + x;
+  if (L[c] < 0) return;
+  int fail = 0;
+  const int right = y * nx + (x + 1 == nx ? 0 : x + 1);
+  const int down = (y + 1 == ny ? 0 : y + 1) * nx + x;
+  if (L[right] >= 0) unite(L, c, right, &fail);
+  if (L[down] >= 0) unite(L, c, down, &fail);
+  if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
+}
+
+__global__ void __launch_bounds__(kTX * kTY) kt_flatten(int nx, int32_t* L, const uint8_t* __restrict__ tile_gas,
+                                                        int* flags) {
+  if (!tile_gas[blockIdx.y * gridDim.x + blockIdx.x]) return;
+  const int c = (blockIdx.y * kTY + threadIdx.y) * nx + blockIdx.x * kTX + threadIdx.x;
+  if (L[c] < 0) return;
+  int fail = 0;
+  L[c] = find_root(L, c, &fail);
+  if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
+}
+
+__global__ void __launch_bounds__(kTX * kTY) kt_owner(int nx, int ny, int R, const int32_t* __restrict__ L,
+                                                      int32_t* __restrict__ own, const uint8_t* __restrict__ active,
+                                                      const uint8_t* __restrict__ prev) {
+  __shared__ int32_t sl[(kTY + 2 * kOMaxR) * (kTX + 2 * kOMaxR)];
+  const int t = blockIdx.y * gridDim.x + blockIdx.x;
+  const int act = active[t], prv = prev[t];
+  if (!act && !prv) return;
+  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  const size_t c = (size_t)y * nx + x;
+  if (!act) {
+    own[c] = -1;
+    return;
+  }
+  const int W = kTX + 2 * R, H = kTY + 2 * R;
+  const int bx0 = blockIdx.x * kTX - R, by0 = blockIdx.y * kTY - R;
+  for (int yy = threadIdx.y; yy < H; yy += kTY) {
+    const size_t row = (size_t)wrap1(by0 + yy, ny) * nx;
+    for (int xx = threadIdx.x; xx < W; xx += kTX) sl[yy * W + xx] = L[row + wrap1(bx0 + xx, nx)];
+  }
+  __syncthreads();
+  const int* row0 = sl + (threadIdx.y + R) * W + threadIdx.x + R;
+  int result = row0[0];
+  if (result < 0) {
+    int bd = 0x7fffffff;
+    for (int dy = -R; dy <= R; ++dy) {
+      const int* rowp = row0 + dy * W;
+      for (int dx = -R; dx <= R; ++dx) {
+        const int d2 = dx * dx + dy * dy;
+        if (d2 > R * R || d2 > bd) continue;
+        const int l = rowp[dx];
+        if (l < 0) continue;
+        if (d2 < bd || l < result) {
+          bd = d2;
+          result = l;
+        }
+      }
+    }
+  }
+  own[c] = result;
+}
+
+__global__ void __launch_bounds__(kTX * kTY) kt_rupture(int nx, int ny, float G, float rho0, float eps,
+                                                        const float* __restrict__ rho, const int32_t* __restrict__ own,
+                                                        int8_t* __restrict__ sgn, uint8_t* __restrict__ open,
+                                                        const uint8_t* __restrict__ active,
+                                                        const uint8_t* __restrict__ prev, int* flags) {
+  const int t = blockIdx.y * gridDim.x + blockIdx.x;
+  const int act = active[t], prv = prev[t];
+  if (!act && !prv) return;
+  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  const size_t c = (size_t)y * nx + x;
+  const int o = act ? own[c] : -1;
+  int dir = 0;
+  if (o >= 0) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int on = own[(size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx)];
+      if (dir == 0 && on >= 0 && on != o) dir = i;
+    }
+  }
+  int opened = 0;
+  if (dir == 0) {
+    sgn[c] = 0;
+  } else {
+    int ex = 0, ey = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (i == dir) {
+        ex = cx(i);
+        ey = cy(i);
+      }
+    const float pp = pressure_of(rho[(size_t)wrap1(y + ey, ny) * nx + wrap1(x + ex, nx)], G, rho0);
+    const float p0 = pressure_of(rho[c], G, rho0);
+    const float pm = pressure_of(rho[(size_t)wrap1(y - ey, ny) * nx + wrap1(x - ex, nx)], G, rho0);
+    const float d2 = pp - 2.0f * p0 + pm;
+    const int sg = (d2 > 0.f) - (d2 < 0.f);
+    const int prevs = sgn[c];
+    if (eps >= 0.f && !open[c] && (fabsf(d2) <= eps || (prevs != 0 && sg != prevs))) {
+      open[c] = 1;
+      opened = 1;
+    }
+    sgn[c] = (int8_t)sg;
+  }
+  const int n = __syncthreads_count(opened);
+  if (n && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(flags + FLAG_OPENED, n);
+}
+
+__global__ void __launch_bounds__(kTX * kTY) kt_mask(int nx, int ny, const int32_t* __restrict__ own,
+                                                     const uint8_t* __restrict__ open, uint8_t* __restrict__ mask,
+                                                     const uint8_t* __restrict__ active,
+                                                     const uint8_t* __restrict__ prev) {
+  const int t = blockIdx.y * gridDim.x + blockIdx.x;
+  const int act = active[t], prv = prev[t];
+  if (!act && !prv) return;
+  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  const size_t c = (size_t)y * nx + x;
+  unsigned m = 0;
+  const int o = act ? own[c] : -1;
+  if (o >= 0 && !open[c]) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const size_t nb = (size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx);
+      const int on = own[nb];
+      if (on >= 0 && on != o && !open[nb]) m |= 1u << (i - 1);
+    }
+  }
+  mask[c] = (uint8_t)m;
+}
+
 }  // namespace
 
 int mass_partials_needed() { return kRedBlocks * kStatVals; }
@@ -604,6 +789,35 @@ cudaError_t launch_stats(int nx, int ny, const int32_t* label, int32_t* area, do
   k_stats_partial<<<kRedBlocks, kThreads, 0, s>>>(N, label, area, nbins, ldmin, ldspan, partials, hist);
   k_sum_partials<kStatVals><<<1, kThreads, 0, s>>>(partials, kRedBlocks, out_dev);
   return cudaGetLastError();
+}
+
+bool relabel_tiled_ok(int nx, int ny, int R) { return nx % kTX == 0 && ny % kTY == 0 && R <= kOMaxR; }
+
+int relabel_tile_count(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY); }
+
+cudaError_t launch_relabel_tiled(const FieldParams& fp, float threshold, int R, float G, float rho0, float eps,
+                                 float* rho, int32_t* label, int32_t* owner, int8_t* sgn, uint8_t* open,
+                                 uint8_t* mask, uint8_t* tile_gas, uint8_t* tile_active, uint8_t* tile_prev,
+                                 int* flags, cudaStream_t s) {
+  const int nx = fp.nx, ny = fp.ny;
+  const int ntx = nx / kTX, nty = ny / kTY;
+  const dim3 grid(ntx, nty), block(kTX, kTY);
+  switch (fp.storage) {
+    case LBM_F32: kt_density_label<LBM_F32><<<grid, block, 0, s>>>(fp, threshold, rho, label, tile_gas); break;
+    case LBM_F16_DEV: kt_density_label<LBM_F16_DEV><<<grid, block, 0, s>>>(fp, threshold, rho, label, tile_gas); break;
+    case LBM_BF16_DEV: kt_density_label<LBM_BF16_DEV><<<grid, block, 0, s>>>(fp, threshold, rho, label, tile_gas); break;
+    default: return cudaErrorInvalidValue;
+  }
+  const int spx = (R + kTX - 1) / kTX, spy = (R + kTY - 1) / kTY;
+  kt_active<<<blocks_for((long long)ntx * nty), kThreads, 0, s>>>(tile_gas, tile_active, ntx, nty, spx, spy);
+  kt_union<<<grid, block, 0, s>>>(nx, ny, label, tile_gas, flags);
+  kt_flatten<<<grid, block, 0, s>>>(nx, label, tile_gas, flags);
+  kt_owner<<<grid, block, 0, s>>>(nx, ny, R, label, owner, tile_active, tile_prev);
+  kt_rupture<<<grid, block, 0, s>>>(nx, ny, G, rho0, eps, rho, owner, sgn, open, tile_active, tile_prev, flags);
+  kt_mask<<<grid, block, 0, s>>>(nx, ny, owner, open, mask, tile_active, tile_prev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(tile_prev, tile_active, (size_t)ntx * nty, cudaMemcpyDeviceToDevice, s);
 }
 
 }  // namespace lbm

@@ -149,6 +149,14 @@ cudaError_t launch_stats(int nx, int ny, const int32_t* label, int32_t* area, do
                          int nparts, double* out_dev, int* hist, int nbins, double dmin, double dmax,
                          cudaStream_t s);
 constexpr int kMaxHistBins = 64;
+// Tiled barrier pipeline (barrier.cu): density + labels + tile flags, then
+// union, flatten, owner, rupture and mask restricted to tiles near gas.
+bool relabel_tiled_ok(int nx, int ny, int R);
+int relabel_tile_count(int nx, int ny);
+cudaError_t launch_relabel_tiled(const FieldParams& fp, float threshold, int R, float G, float rho0, float eps,
+                                 float* rho, int32_t* label, int32_t* owner, int8_t* sgn, uint8_t* open,
+                                 uint8_t* mask, uint8_t* tile_gas, uint8_t* tile_active, uint8_t* tile_prev,
+                                 int* flags, cudaStream_t s);
 int mass_partials_needed();
 
 }  // namespace lbm

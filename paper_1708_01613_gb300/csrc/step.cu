@@ -410,9 +410,12 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma(const StepParams
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
 }
 
+// Stage ring depth and CTAs per SM, from measured sweeps at 8192^2: with
+// four CTAs per SM, prefetching two rows ahead (FP32) gave more DRAM
+// throughput than deeper rings (more reads in flight lowered it).
 template <int S>
-constexpr int tma_stages() { return S == LBM_F32 ? 5 : 8; }
-constexpr int kTmaMinBlocks = 3;
+constexpr int tma_stages() { return S == LBM_F32 ? 3 : 6; }
+constexpr int kTmaMinBlocks = 4;
 
 template <int S>
 bool tma_ok(int nx) {

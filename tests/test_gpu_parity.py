@@ -84,10 +84,11 @@ def _bits_equal_except_near(a, b, ok_mask):
     return not np.any(diff & ~ok_mask)
 
 
-def test_barrier_parity_two_bubbles_fp32():
+@pytest.mark.parametrize("nx,ny", [(160, 80), (164, 84)])
+def test_barrier_parity_two_bubbles_fp32(nx, ny):
     """Barrier on (K = 1): populations within 1e-5 and the owner map and
-    blocked-edge mask bit-exact at steps 1, 10, 100."""
-    nx, ny = 160, 80
+    blocked-edge mask bit-exact at steps 1, 10, 100 (160 x 80 runs the tiled
+    relabel pipeline, 164 x 84 the untiled one)."""
     b = two_bubbles(nx, ny, gap=6.0)
     P = O.make_params(nx, ny, barrier=True)
     rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
@@ -346,3 +347,25 @@ def test_owner_zone_radius_sweep(R):
     assert np.array_equal(got["owner"], ref.owner)
     assert np.array_equal(got["mask"], ref.mask)
     assert rel_inf(got["pops"], ref.f) < TOL["f32"]
+
+
+def test_barrier_state_clears_when_a_bubble_dissolves():
+    """A small bubble in a closed box at coexistence density dissolves; its
+    interaction zone must disappear from the owner map and mask (tiles that
+    stop being active are reset)."""
+    nx, ny = 96, 96
+    b = [[48.0, 48.0, 10.0], [70.0, 48.0, 8.0]]
+    P = O.make_params(nx, ny, barrier=True, rupture_eps=-1.0)
+    rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
+    sim = gpu_sim(nx, ny, bubbles=b, barrier=True, rupture_eps=-1.0)
+    ref = oracle_sim(nx, ny, rho0, barrier=True, rupture_eps=-1.0)
+    done = 0
+    for t in (1, 200, 900):
+        sim.step(t - done)
+        ref.step(t - done)
+        done = t
+        got = sim.read("owner", "mask", "pops")
+        assert np.array_equal(got["owner"], ref.owner), t
+        assert np.array_equal(got["mask"], ref.mask), t
+        assert rel_inf(got["pops"], ref.f) < 1e-4
+    assert np.all(ref.owner == -1)  # everything dissolved by step 900
