@@ -145,10 +145,13 @@ int lbm_step(lbm_handle* h, int64_t nsteps);
 /* Kernels this handle has launched since lbm_create (host-side count). */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 
-/* Selects the fused-step kernel: 0 = automatic (TMA-staged where the box
- * allows it: nx % 16 == 0 and nx >= 272, else plain loads), 1 = plain-load
- * kernel, 2 = TMA-staged kernel (LBM_ENOTSUP if the box does not allow it).
- * Both compute the same arithmetic in the same order. */
+/* Selects the fused-step kernel: 0 = automatic, 1 = plain-load kernel (any
+ * box), 2 = TMA-staged kernel with one cell per thread (nx % 16 == 0 and
+ * nx >= 272), 3 = TMA-staged kernel with two cells per thread and packed FP32
+ * arithmetic (nx % 16 == 0 and nx >= 528). Automatic picks 3 for 16-bit
+ * storage and 2 for FP32 where the box allows, else 1. A variant the box
+ * does not allow returns LBM_ENOTSUP. All variants compute the same
+ * operations in the same order and give bitwise the same populations. */
 int lbm_set_step_variant(lbm_handle* h, int variant);
 
 /* Steps done since the last init/load. */

@@ -24,7 +24,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, flags, partials, scalars, total;
+  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, tile_list, flags, partials, scalars, total;
   int nparts, ntiles;
 };
 
@@ -71,6 +71,7 @@ Layout layout_for(const lbm_config& c) {
     L.sgn = take(N);
     L.ntiles = relabel_tile_count(c.nx, c.ny);
     L.tiles = take(3 * (size_t)L.ntiles);  // gas, active, previous active
+    L.tile_list = take(4 * (size_t)L.ntiles);
   }
   L.flags = take(sizeof(int) * FLAG_COUNT);
   L.nparts = mass_partials_needed();
@@ -180,7 +181,8 @@ int relabel(lbm_handle* h) {
   if (relabel_tiled_ok(c.nx, c.ny, c.zone_radius)) {
     CUDA_TRY(h, launch_relabel_tiled(fp, (float)c.gas_threshold, c.zone_radius, (float)c.G, (float)c.rho0,
                                      (float)c.rupture_eps, h->rho(), h->label(), h->owner(), h->sgn(), h->open(),
-                                     h->mask(), h->tiles(0), h->tiles(1), h->tiles(2), h->flags(), h->stream));
+                                     h->mask(), h->tiles(0), h->tiles(1), h->tiles(2),
+                                     reinterpret_cast<int*>(h->ws + h->L.tile_list), h->flags(), h->stream));
     h->launches += 7;
     return LBM_OK;
   }
@@ -355,7 +357,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
   const lbm_config& c = h->cfg;
   StepParams p{};
   p.mask = nullptr;
-  p.force_generic = h->variant == 1 ? 1 : 0;
+  p.force_generic = h->variant;
   p.flags = h->flags();
   p.nx = c.nx;
   p.ny = c.ny;
@@ -396,9 +398,11 @@ int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : -1; 
 
 int lbm_set_step_variant(lbm_handle* h, int variant) {
   if (!h) return LBM_EINVAL;
-  if (variant < 0 || variant > 2) return fail(h, LBM_EINVAL, "variant must be 0, 1 or 2");
+  if (variant < 0 || variant > 3) return fail(h, LBM_EINVAL, "variant must be 0, 1, 2 or 3");
   if (variant == 2 && !step_tma_allowed(h->cfg.storage, h->cfg.nx))
     return fail(h, LBM_ENOTSUP, "TMA-staged step needs nx %% 16 == 0 and nx >= 272");
+  if (variant == 3 && !step_tma2_allowed(h->cfg.storage, h->cfg.nx))
+    return fail(h, LBM_ENOTSUP, "two-cell staged step needs nx %% 16 == 0 and nx >= 528");
   h->variant = variant;
   return LBM_OK;
 }

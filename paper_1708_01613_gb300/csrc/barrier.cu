@@ -488,8 +488,11 @@ __global__ void __launch_bounds__(kTX * kTY) kt_density_label(const FieldParams 
   if (threadIdx.x == 0 && threadIdx.y == 0) tile_gas[blockIdx.y * gridDim.x + blockIdx.x] = (uint8_t)(any != 0);
 }
 
-__global__ void kt_active(const uint8_t* __restrict__ gas, uint8_t* __restrict__ active, int ntx, int nty, int spx,
-                          int spy) {
+// Also appends every tile that needs a visit (active now or at the previous
+// relabel) to `list`; the order of the list does not affect any result.
+__global__ void kt_active(const uint8_t* __restrict__ gas, uint8_t* __restrict__ active,
+                          const uint8_t* __restrict__ prev, int* __restrict__ list, int* __restrict__ count, int ntx,
+                          int nty, int spx, int spy) {
   const int ntiles = ntx * nty;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
     const int ty = t / ntx, tx = t - ty * ntx;
@@ -499,48 +502,60 @@ __global__ void kt_active(const uint8_t* __restrict__ gas, uint8_t* __restrict__
       for (int dx = -spx; dx <= spx; ++dx) a |= gas[yy * ntx + wrapi(tx + dx, ntx)];
     }
     active[t] = (uint8_t)(a != 0);
+    if (a || prev[t]) list[atomicAdd(count, 1)] = t;
   }
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_union(int nx, int ny, int32_t* L, const uint8_t* __restrict__ tile_gas,
-                                                      int* flags) {
-  if (!tile_gas[blockIdx.y * gridDim.x + blockIdx.x]) return;
-  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
-  const int c = y * nx + x;
-  if (L[c] < 0) return;
+__global__ void __launch_bounds__(kTX * kTY) kt_union(int nx, int ny, int ntx, int32_t* L,
+                                                      const uint8_t* __restrict__ tile_gas, const int* __restrict__ list,
+                                                      const int* __restrict__ count, int* flags) {
+  const int n = *count;
   int fail = 0;
-  const int right = y * nx + (x + 1 == nx ? 0 : x + 1);
-  const int down = (y + 1 == ny ? 0 : y + 1) * nx + x;
-  if (L[right] >= 0) unite(L, c, right, &fail);
-  if (L[down] >= 0) unite(L, c, down, &fail);
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const int t = list[w];
+    if (!tile_gas[t]) continue;
+    const int x = (t % ntx) * kTX + threadIdx.x, y = (t / ntx) * kTY + threadIdx.y;
+    const int c = y * nx + x;
+    if (L[c] < 0) continue;
+    const int right = y * nx + (x + 1 == nx ? 0 : x + 1);
+    const int down = (y + 1 == ny ? 0 : y + 1) * nx + x;
+    if (L[right] >= 0) unite(L, c, right, &fail);
+    if (L[down] >= 0) unite(L, c, down, &fail);
+  }
   if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_flatten(int nx, int32_t* L, const uint8_t* __restrict__ tile_gas,
+__global__ void __launch_bounds__(kTX * kTY) kt_flatten(int nx, int ntx, int32_t* L, const uint8_t* __restrict__ tile_gas,
+                                                        const int* __restrict__ list, const int* __restrict__ count,
                                                         int* flags) {
-  if (!tile_gas[blockIdx.y * gridDim.x + blockIdx.x]) return;
-  const int c = (blockIdx.y * kTY + threadIdx.y) * nx + blockIdx.x * kTX + threadIdx.x;
-  if (L[c] < 0) return;
+  const int n = *count;
   int fail = 0;
-  L[c] = find_root(L, c, &fail);
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    const int t = list[w];
+    if (!tile_gas[t]) continue;
+    const int c = ((t / ntx) * kTY + threadIdx.y) * nx + (t % ntx) * kTX + threadIdx.x;
+    if (L[c] >= 0) L[c] = find_root(L, c, &fail);
+  }
   if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_owner(int nx, int ny, int R, const int32_t* __restrict__ L,
+__global__ void __launch_bounds__(kTX * kTY) kt_owner(int nx, int ny, int ntx, int R, const int32_t* __restrict__ L,
                                                       int32_t* __restrict__ own, const uint8_t* __restrict__ active,
-                                                      const uint8_t* __restrict__ prev) {
+                                                      const int* __restrict__ list, const int* __restrict__ count) {
   __shared__ int32_t sl[(kTY + 2 * kOMaxR) * (kTX + 2 * kOMaxR)];
-  const int t = blockIdx.y * gridDim.x + blockIdx.x;
-  const int act = active[t], prv = prev[t];
-  if (!act && !prv) return;
-  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  const int n = *count;
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+  const int t = list[w];
+  const int tx = t % ntx, ty = t / ntx;
+  const int x = tx * kTX + threadIdx.x, y = ty * kTY + threadIdx.y;
   const size_t c = (size_t)y * nx + x;
-  if (!act) {
+  if (!active[t]) {  // went quiet since the previous relabel
     own[c] = -1;
-    return;
+    continue;
   }
   const int W = kTX + 2 * R, H = kTY + 2 * R;
-  const int bx0 = blockIdx.x * kTX - R, by0 = blockIdx.y * kTY - R;
+  const int bx0 = tx * kTX - R, by0 = ty * kTY - R;
+  __syncthreads();  // the previous tile's window is no longer read
   for (int yy = threadIdx.y; yy < H; yy += kTY) {
     const size_t row = (size_t)wrap1(by0 + yy, ny) * nx;
     for (int xx = threadIdx.x; xx < W; xx += kTX) sl[yy * W + xx] = L[row + wrap1(bx0 + xx, nx)];
@@ -565,17 +580,20 @@ __global__ void __launch_bounds__(kTX * kTY) kt_owner(int nx, int ny, int R, con
     }
   }
   own[c] = result;
+  }
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_rupture(int nx, int ny, float G, float rho0, float eps,
+__global__ void __launch_bounds__(kTX * kTY) kt_rupture(int nx, int ny, int ntx, float G, float rho0, float eps,
                                                         const float* __restrict__ rho, const int32_t* __restrict__ own,
                                                         int8_t* __restrict__ sgn, uint8_t* __restrict__ open,
                                                         const uint8_t* __restrict__ active,
-                                                        const uint8_t* __restrict__ prev, int* flags) {
-  const int t = blockIdx.y * gridDim.x + blockIdx.x;
-  const int act = active[t], prv = prev[t];
-  if (!act && !prv) return;
-  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+                                                        const int* __restrict__ list, const int* __restrict__ count,
+                                                        int* flags) {
+  const int nw = *count;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+  const int t = list[w];
+  const int act = active[t];
+  const int x = (t % ntx) * kTX + threadIdx.x, y = (t / ntx) * kTY + threadIdx.y;
   const size_t c = (size_t)y * nx + x;
   const int o = act ? own[c] : -1;
   int dir = 0;
@@ -611,16 +629,18 @@ __global__ void __launch_bounds__(kTX * kTY) kt_rupture(int nx, int ny, float G,
   }
   const int n = __syncthreads_count(opened);
   if (n && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(flags + FLAG_OPENED, n);
+  }
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_mask(int nx, int ny, const int32_t* __restrict__ own,
+__global__ void __launch_bounds__(kTX * kTY) kt_mask(int nx, int ny, int ntx, const int32_t* __restrict__ own,
                                                      const uint8_t* __restrict__ open, uint8_t* __restrict__ mask,
                                                      const uint8_t* __restrict__ active,
-                                                     const uint8_t* __restrict__ prev) {
-  const int t = blockIdx.y * gridDim.x + blockIdx.x;
-  const int act = active[t], prv = prev[t];
-  if (!act && !prv) return;
-  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+                                                     const int* __restrict__ list, const int* __restrict__ count) {
+  const int nw = *count;
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+  const int t = list[w];
+  const int act = active[t];
+  const int x = (t % ntx) * kTX + threadIdx.x, y = (t / ntx) * kTY + threadIdx.y;
   const size_t c = (size_t)y * nx + x;
   unsigned m = 0;
   const int o = act ? own[c] : -1;
@@ -633,6 +653,7 @@ __global__ void __launch_bounds__(kTX * kTY) kt_mask(int nx, int ny, const int32
     }
   }
   mask[c] = (uint8_t)m;
+  }
 }
 
 }  // namespace
@@ -798,7 +819,7 @@ int relabel_tile_count(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + 
 cudaError_t launch_relabel_tiled(const FieldParams& fp, float threshold, int R, float G, float rho0, float eps,
                                  float* rho, int32_t* label, int32_t* owner, int8_t* sgn, uint8_t* open,
                                  uint8_t* mask, uint8_t* tile_gas, uint8_t* tile_active, uint8_t* tile_prev,
-                                 int* flags, cudaStream_t s) {
+                                 int* tile_list, int* flags, cudaStream_t s) {
   const int nx = fp.nx, ny = fp.ny;
   const int ntx = nx / kTX, nty = ny / kTY;
   const dim3 grid(ntx, nty), block(kTX, kTY);
@@ -809,13 +830,19 @@ cudaError_t launch_relabel_tiled(const FieldParams& fp, float threshold, int R, 
     default: return cudaErrorInvalidValue;
   }
   const int spx = (R + kTX - 1) / kTX, spy = (R + kTY - 1) / kTY;
-  kt_active<<<blocks_for((long long)ntx * nty), kThreads, 0, s>>>(tile_gas, tile_active, ntx, nty, spx, spy);
-  kt_union<<<grid, block, 0, s>>>(nx, ny, label, tile_gas, flags);
-  kt_flatten<<<grid, block, 0, s>>>(nx, label, tile_gas, flags);
-  kt_owner<<<grid, block, 0, s>>>(nx, ny, R, label, owner, tile_active, tile_prev);
-  kt_rupture<<<grid, block, 0, s>>>(nx, ny, G, rho0, eps, rho, owner, sgn, open, tile_active, tile_prev, flags);
-  kt_mask<<<grid, block, 0, s>>>(nx, ny, owner, open, mask, tile_active, tile_prev);
-  cudaError_t e = cudaGetLastError();
+  int* count = flags + FLAG_TILES;
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  kt_active<<<blocks_for((long long)ntx * nty), kThreads, 0, s>>>(tile_gas, tile_active, tile_prev, tile_list, count,
+                                                                 ntx, nty, spx, spy);
+  const int wgrid = 152 * 8;  // tiles are taken from the list in a grid-stride loop
+  kt_union<<<wgrid, block, 0, s>>>(nx, ny, ntx, label, tile_gas, tile_list, count, flags);
+  kt_flatten<<<wgrid, block, 0, s>>>(nx, ntx, label, tile_gas, tile_list, count, flags);
+  kt_owner<<<wgrid, block, 0, s>>>(nx, ny, ntx, R, label, owner, tile_active, tile_list, count);
+  kt_rupture<<<wgrid, block, 0, s>>>(nx, ny, ntx, G, rho0, eps, rho, owner, sgn, open, tile_active, tile_list, count,
+                                     flags);
+  kt_mask<<<wgrid, block, 0, s>>>(nx, ny, ntx, owner, open, mask, tile_active, tile_list, count);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaMemcpyAsync(tile_prev, tile_active, (size_t)ntx * nty, cudaMemcpyDeviceToDevice, s);
 }

@@ -32,11 +32,14 @@ enum Flag : int {
   FLAG_NUMERIC = 0,   // NaN/Inf or rho <= 0 seen by the step kernel
   FLAG_TIMEOUT = 1,   // a bounded device loop gave up
   FLAG_OPENED = 2,    // cells opened by the latest rupture test
+  FLAG_TILES = 3,     // tiles in the relabel work list
   FLAG_HIST = 64,     // 64 histogram counters
   FLAG_COUNT = 128
 };
 
 // Population storage: FP32 value, or a 16-bit deviation from w_i rho_ref.
+// Decode and encode are explicitly rounded single operations so that every
+// kernel (scalar or packed) turns a stored value into the same float.
 template <int S>
 struct Store;
 
@@ -54,13 +57,13 @@ struct Store<LBM_F16_DEV> {
   using T = __half;
   static constexpr int bytes = 2;
   __device__ static __forceinline__ float load(const T* p, size_t i, float base) {
-    return base + __half2float(__ldg(p + i));
+    return __fadd_rn(base, __half2float(__ldg(p + i)));
   }
   __device__ static __forceinline__ float load_smem(const T* p, int i, float base) {
-    return base + __half2float(p[i]);
+    return __fadd_rn(base, __half2float(p[i]));
   }
   __device__ static __forceinline__ void store(T* p, size_t i, float v, float base) {
-    p[i] = __float2half_rn(v - base);
+    p[i] = __float2half_rn(__fsub_rn(v, base));
   }
 };
 
@@ -69,13 +72,13 @@ struct Store<LBM_BF16_DEV> {
   using T = __nv_bfloat16;
   static constexpr int bytes = 2;
   __device__ static __forceinline__ float load(const T* p, size_t i, float base) {
-    return base + __bfloat162float(__ldg(p + i));
+    return __fadd_rn(base, __bfloat162float(__ldg(p + i)));
   }
   __device__ static __forceinline__ float load_smem(const T* p, int i, float base) {
-    return base + __bfloat162float(p[i]);
+    return __fadd_rn(base, __bfloat162float(p[i]));
   }
   __device__ static __forceinline__ void store(T* p, size_t i, float v, float base) {
-    p[i] = __float2bfloat16_rn(v - base);
+    p[i] = __float2bfloat16_rn(__fsub_rn(v, base));
   }
 };
 
@@ -90,7 +93,7 @@ struct StepParams {
   int nx, ny;
   long long N;           // nx * ny (plane stride)
   int rows_per_chunk;    // rows marched by one CTA
-  int force_generic;     // 1: plain-load kernel even where TMA staging applies; 0/2: automatic
+  int force_generic;     // kernel variant: 0 automatic, 1 plain loads, 2 one-cell staged, 3 two-cell staged
   float tau, inv_tau, G, rho0, inv_rho0;
   float wref[Q];         // w_i * rho_ref (16-bit deviation base)
 };
@@ -101,6 +104,8 @@ cudaError_t launch_step(int storage, const StepParams& p, cudaStream_t s);
 void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk, int* block);
 // Whether the TMA-staged step kernel can run on a box of width nx.
 bool step_tma_allowed(int storage, int nx);
+// Whether the two-cell staged step kernel can run on a box of width nx.
+bool step_tma2_allowed(int storage, int nx);
 
 // Barrier / field / reduction kernels (barrier.cu).
 struct Workspace {
@@ -156,7 +161,7 @@ int relabel_tile_count(int nx, int ny);
 cudaError_t launch_relabel_tiled(const FieldParams& fp, float threshold, int R, float G, float rho0, float eps,
                                  float* rho, int32_t* label, int32_t* owner, int8_t* sgn, uint8_t* open,
                                  uint8_t* mask, uint8_t* tile_gas, uint8_t* tile_active, uint8_t* tile_prev,
-                                 int* flags, cudaStream_t s);
+                                 int* tile_list, int* flags, cudaStream_t s);
 int mass_partials_needed();
 
 }  // namespace lbm

@@ -34,64 +34,111 @@ constexpr float kW1 = 1.0f / 9.0f, kW5 = 1.0f / 36.0f, kW0 = 4.0f / 9.0f;
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // ---------------------------------------------------------------- cell math
+// The per-cell arithmetic is written once for V = float (one cell) and
+// V = float2 (two neighbouring cells, packed FP32 instructions), with every
+// operation an explicitly rounded add, multiply or fused multiply-add, so all
+// kernels produce bitwise the same populations.
+template <typename V>
+struct VOps;
+
+template <>
+struct VOps<float> {
+  static __device__ __forceinline__ float set(float a) { return a; }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+  static __device__ __forceinline__ float ex(float a) { return __expf(a); }
+  static __device__ __forceinline__ int bad(float rho) { return !(rho > 0.f && rho < 1e30f); }
+};
+
+template <>
+struct VOps<float2> {
+  static __device__ __forceinline__ float2 set(float a) { return make_float2(a, a); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+  }
+  static __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+  static __device__ __forceinline__ float2 ex(float2 a) { return make_float2(__expf(a.x), __expf(a.y)); }
+  static __device__ __forceinline__ int bad(float2 rho) { return VOps<float>::bad(rho.x) | VOps<float>::bad(rho.y); }
+};
+
 // Eq. 11: rho and j from the nine incoming populations.
-__device__ __forceinline__ void moments9(const float f[Q], float& rho, float& jx, float& jy) {
-  rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-  jx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
-  jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
+template <typename V>
+__device__ __forceinline__ void moments9(const V f[Q], V& rho, V& jx, V& jy) {
+  using O = VOps<V>;
+  rho = O::add(O::add(O::add(f[0], f[1]), O::add(f[2], f[3])), O::add(O::add(f[4], f[5]), O::add(f[6], f[7])));
+  rho = O::add(rho, f[8]);
+  jx = O::add(O::sub(f[1], f[3]), O::add(O::sub(f[5], f[7]), O::sub(f[8], f[6])));
+  jy = O::add(O::sub(f[2], f[4]), O::add(O::sub(f[5], f[7]), O::sub(f[6], f[8])));
 }
 
 // Eq. 30.
-__device__ __forceinline__ float psi_of(float rho, const StepParams& p) {
-  return p.rho0 * (1.0f - __expf(-rho * p.inv_rho0));
+template <typename V>
+__device__ __forceinline__ V psi_of(V rho, const StepParams& p) {
+  using O = VOps<V>;
+  return O::mul(O::set(p.rho0), O::sub(O::set(1.0f), O::ex(O::mul(rho, O::set(-p.inv_rho0)))));
 }
 
 // Eq. 22 with the barrier substitution: s[i] holds psi(x + e_i), or psi(x)
 // where the edge is blocked.
-__device__ __forceinline__ void force_of(const float s[Q], float psi_c, float G, float& Fx, float& Fy) {
-  const float sx = kW1 * (s[1] - s[3]) + kW5 * ((s[5] - s[7]) + (s[8] - s[6]));
-  const float sy = kW1 * (s[2] - s[4]) + kW5 * ((s[5] - s[7]) + (s[6] - s[8]));
-  Fx = -G * psi_c * sx;
-  Fy = -G * psi_c * sy;
+template <typename V>
+__device__ __forceinline__ void force_of(const V s[Q], V psi_c, float G, V& Fx, V& Fy) {
+  using O = VOps<V>;
+  const V w1 = O::set(kW1), w5 = O::set(kW5);
+  const V d57 = O::sub(s[5], s[7]);
+  const V sx = O::fma(w1, O::sub(s[1], s[3]), O::mul(w5, O::add(d57, O::sub(s[8], s[6]))));
+  const V sy = O::fma(w1, O::sub(s[2], s[4]), O::mul(w5, O::add(d57, O::sub(s[6], s[8]))));
+  const V gp = O::mul(O::set(-G), psi_c);
+  Fx = O::mul(gp, sx);
+  Fy = O::mul(gp, sy);
 }
 
 // Eqs. 39-40 (u_eq = (j + tau F)/rho), Eq. 14 evaluated by opposite pairs,
 // Eq. 18 (BGK). f holds the incoming populations and receives the outgoing.
-template <bool TAU_ONE>
-__device__ __forceinline__ void collide(float f[Q], float rho, float jx, float jy, float Fx, float Fy,
-                                        const StepParams& p, int& bad) {
-  const float ir = __frcp_rn(rho);
-  const float ux = (jx + p.tau * Fx) * ir;
-  const float uy = (jy + p.tau * Fy) * ir;
-  bad |= !(rho > 0.f) | !(fabsf(ux) + fabsf(uy) < 1e30f);
-  const float a = rho * (1.0f - 1.5f * (ux * ux + uy * uy));
-  const float r3 = 3.0f * rho, r45 = 4.5f * rho;
-  float feq[Q];
-  feq[0] = kW0 * a;
+template <bool TAU_ONE, typename V>
+__device__ __forceinline__ void collide(V f[Q], V rho, V jx, V jy, V Fx, V Fy, const StepParams& p, int& bad) {
+  using O = VOps<V>;
+  const V ir = O::rcp(rho);
+  const V tau = O::set(p.tau);
+  const V ux = O::mul(O::fma(tau, Fx, jx), ir);
+  const V uy = O::mul(O::fma(tau, Fy, jy), ir);
+  bad |= O::bad(rho);
+  const V uu = O::fma(ux, ux, O::mul(uy, uy));
+  const V a = O::mul(rho, O::fma(O::set(-1.5f), uu, O::set(1.0f)));
+  const V r3 = O::mul(O::set(3.0f), rho), r45 = O::mul(O::set(4.5f), rho);
+  const V w1 = O::set(kW1), w5 = O::set(kW5);
+  V feq[Q];
+  feq[0] = O::mul(O::set(kW0), a);
   {
-    const float s = a + r45 * ux * ux, t = r3 * ux;
-    feq[1] = kW1 * (s + t);
-    feq[3] = kW1 * (s - t);
+    const V s = O::fma(O::mul(r45, ux), ux, a), t = O::mul(r3, ux);
+    feq[1] = O::mul(w1, O::add(s, t));
+    feq[3] = O::mul(w1, O::sub(s, t));
   }
   {
-    const float s = a + r45 * uy * uy, t = r3 * uy;
-    feq[2] = kW1 * (s + t);
-    feq[4] = kW1 * (s - t);
+    const V s = O::fma(O::mul(r45, uy), uy, a), t = O::mul(r3, uy);
+    feq[2] = O::mul(w1, O::add(s, t));
+    feq[4] = O::mul(w1, O::sub(s, t));
   }
   {
-    const float e = ux + uy;
-    const float s = a + r45 * e * e, t = r3 * e;
-    feq[5] = kW5 * (s + t);
-    feq[7] = kW5 * (s - t);
+    const V e = O::add(ux, uy);
+    const V s = O::fma(O::mul(r45, e), e, a), t = O::mul(r3, e);
+    feq[5] = O::mul(w5, O::add(s, t));
+    feq[7] = O::mul(w5, O::sub(s, t));
   }
   {
-    const float e = uy - ux;
-    const float s = a + r45 * e * e, t = r3 * e;
-    feq[6] = kW5 * (s + t);
-    feq[8] = kW5 * (s - t);
+    const V e = O::sub(uy, ux);
+    const V s = O::fma(O::mul(r45, e), e, a), t = O::mul(r3, e);
+    feq[6] = O::mul(w5, O::add(s, t));
+    feq[8] = O::mul(w5, O::sub(s, t));
   }
+  const V om = O::set(p.inv_tau);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] = TAU_ONE ? feq[i] : f[i] + (feq[i] - f[i]) * p.inv_tau;
+  for (int i = 0; i < Q; ++i) f[i] = TAU_ONE ? feq[i] : O::fma(O::sub(feq[i], f[i]), om, f[i]);
 }
 
 // Force + collision + store of one cell from the psi ring.
@@ -410,6 +457,245 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma(const StepParams
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
 }
 
+// ---------------------------------------------------------------- two-cell staged kernel
+// The staged march with two neighbouring cells per thread: a CTA owns a
+// strip of kBX2 = 512 columns, 256 compute threads (cells 2t and 2t+1) plus
+// the helper warp. Pairs are read from the stage with one 32-bit (16-bit
+// storage) or 64-bit (FP32) shared load where aligned, and with two loads and
+// a byte permute where the pull shifts them by one column; the arithmetic
+// runs on float2 (packed FP32); outputs leave as half2/bfloat162/float2.
+constexpr int kBX2 = 512;
+
+template <int S>
+struct TmaGeom2 {
+  using T = typename Store<S>::T;
+  static constexpr int E = sizeof(T);
+  static constexpr int PAD = 16 / E;
+  static constexpr int WIN = kBX2 + 2 * PAD;
+  static constexpr int ROW_BYTES = WIN * E;
+  static constexpr int STAGE_BYTES_MASKED = Q * ROW_BYTES + kBX2;
+};
+
+// Two consecutive staged values (window positions pos, pos+1) as floats.
+template <int S>
+__device__ __forceinline__ float2 load_pair(const unsigned char* row, int pos, int shift, float base);
+
+template <>
+__device__ __forceinline__ float2 load_pair<LBM_F32>(const unsigned char* row, int pos, int shift, float) {
+  const float* r = reinterpret_cast<const float*>(row);
+  if (shift == 0) return *reinterpret_cast<const float2*>(r + pos);  // pos even: 8-byte aligned
+  return make_float2(r[pos], r[pos + 1]);
+}
+
+__device__ __forceinline__ uint32_t pair_bits_16(const unsigned char* row, int pos, int shift) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(row);
+  if (shift == 0) return w[pos >> 1];  // pos even
+  // pos odd: high half of the word at pos-1 and low half of the word at pos+1
+  return __byte_perm(w[(pos - 1) >> 1], w[(pos + 1) >> 1], 0x5432);
+}
+
+// 16-bit pairs are decoded element by element with the same conversion and
+// rounded add as the one-cell kernels (the packed conversions and adds gave
+// different results for small deviations), so all kernels agree bitwise.
+template <>
+__device__ __forceinline__ float2 load_pair<LBM_F16_DEV>(const unsigned char* row, int pos, int shift, float base) {
+  const uint32_t b = pair_bits_16(row, pos, shift);
+  const __half2 h = *reinterpret_cast<const __half2*>(&b);
+  return make_float2(__fadd_rn(base, __low2float(h)), __fadd_rn(base, __high2float(h)));
+}
+
+template <>
+__device__ __forceinline__ float2 load_pair<LBM_BF16_DEV>(const unsigned char* row, int pos, int shift, float base) {
+  const uint32_t b = pair_bits_16(row, pos, shift);
+  const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&b);
+  return make_float2(__fadd_rn(base, __low2float(h)), __fadd_rn(base, __high2float(h)));
+}
+
+template <int S>
+__device__ __forceinline__ void store_pair(typename Store<S>::T* dst, size_t idx, float2 v, float base);
+
+template <>
+__device__ __forceinline__ void store_pair<LBM_F32>(float* dst, size_t idx, float2 v, float) {
+  *reinterpret_cast<float2*>(dst + idx) = v;  // idx even
+}
+
+template <>
+__device__ __forceinline__ void store_pair<LBM_F16_DEV>(__half* dst, size_t idx, float2 v, float base) {
+  *reinterpret_cast<__half2*>(dst + idx) =
+      __halves2half2(__float2half_rn(__fsub_rn(v.x, base)), __float2half_rn(__fsub_rn(v.y, base)));
+}
+
+template <>
+__device__ __forceinline__ void store_pair<LBM_BF16_DEV>(__nv_bfloat16* dst, size_t idx, float2 v, float base) {
+  *reinterpret_cast<__nv_bfloat162*>(dst + idx) =
+      __halves2bfloat162(__float2bfloat16_rn(__fsub_rn(v.x, base)), __float2bfloat16_rn(__fsub_rn(v.y, base)));
+}
+
+template <int S, bool MASKED, int NSTAGE>
+__device__ __forceinline__ void issue_stage2(const StepParams& p, const typename Store<S>::T* src,
+                                             unsigned char* stages, uint64_t* bars, int k, int y0, int x0, int lane) {
+  using G = TmaGeom2<S>;
+  using T = typename G::T;
+  constexpr uint32_t STAGE_BYTES = Q * G::ROW_BYTES + (MASKED ? kBX2 : 0);
+  const int slot = k % NSTAGE;
+  unsigned char* st = stages + (size_t)slot * STAGE_BYTES;
+  uint64_t* bar = bars + slot;
+  const int r = y0 - 1 + k;
+  const int ny = p.ny, nx = p.nx;
+  if (lane < Q + (MASKED ? 1 : 0)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (lane == 0) mbar_expect_tx(bar, STAGE_BYTES);
+  __syncwarp();
+  if (lane < Q) {
+    const int i = lane;
+    const int ciy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    int g = r - ciy;
+    g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
+    g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
+    const T* row = src + (size_t)i * p.N + (size_t)g * nx;
+    copy_row_wrapped<T>(reinterpret_cast<T*>(st + i * G::ROW_BYTES), row, x0 - G::PAD, G::WIN, nx, bar);
+  } else if (MASKED && lane == Q) {
+    const int g = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+    copy_row_wrapped<uint8_t>(st + Q * G::ROW_BYTES, p.mask + (size_t)g * nx, x0, kBX2, nx, bar);
+  }
+}
+
+template <int S, bool MASKED, int NSTAGE>
+constexpr size_t tma2_smem_bytes_c() {
+  return (size_t)NSTAGE * (Q * TmaGeom2<S>::ROW_BYTES + (MASKED ? kBX2 : 0)) + 4 * (kBX2 + 4) * 4 + NSTAGE * 8 + 16;
+}
+
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParams p) {
+  using G = TmaGeom2<S>;
+  using T = typename G::T;
+  using O = VOps<float2>;
+  constexpr int STAGE_BYTES = Q * G::ROW_BYTES + (MASKED ? kBX2 : 0);
+  constexpr int RW = kBX2 + 4;  // ring row: cell column c at index c + 2, halos at 1 and width + 2
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* stages = smem;
+  float(*ring)[RW] = reinterpret_cast<float(*)[RW]>(smem + (size_t)NSTAGE * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE_BYTES + 4 * RW * 4);
+  int* abort_flag = reinterpret_cast<int*>(bars + NSTAGE);
+
+  const T* __restrict__ src = static_cast<const T*>(p.src);
+  T* __restrict__ dst = static_cast<T*>(p.dst);
+  const int nx = p.nx, ny = p.ny;
+  const int tid = threadIdx.x;
+  const bool helper = tid >= kBX;
+  const int lane = tid & 31;
+  const int x0 = blockIdx.x * kBX2;
+  const int width = min(kBX2, nx - x0);  // a multiple of 16
+  const bool active = !helper && 2 * tid < width;
+  const int y0 = blockIdx.y * p.rows_per_chunk;
+  const int y1 = min(y0 + p.rows_per_chunk, ny);
+  if (y0 >= y1) return;
+  const int nst = (y1 - y0) + 2;
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(bars + s, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (helper)
+    for (int k = 0; k < NSTAGE - 1 && k < nst; ++k) issue_stage2<S, MASKED, NSTAGE>(p, src, stages, bars, k, y0, x0, lane);
+
+  const int hplane = lane & 15;
+  const bool hlane = helper && hplane < Q;
+  const int hcx = (hplane == 1 || hplane == 5 || hplane == 8) ? 1 : ((hplane == 3 || hplane == 6 || hplane == 7) ? -1 : 0);
+  const int hpos = (lane < 16 ? G::PAD - 1 : G::PAD + width) - hcx;
+  float hbase = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (hlane && i == hplane) hbase = p.wref[i];
+
+  const int jc = 2 * tid + 2;      // ring index of the first cell of the pair
+  const int pos = G::PAD + 2 * tid;  // window position of the first cell
+  float2 fprev[Q];
+  float2 rho_prev = make_float2(1.f, 1.f), jx_prev = make_float2(0.f, 0.f), jy_prev = make_float2(0.f, 0.f);
+  unsigned m_prev = 0;
+  int bad = 0;
+  int k_abort = 0;
+  for (int k = 0; k < nst; ++k) {
+    const int slot = k % NSTAGE;
+    const unsigned char* st = stages + (size_t)slot * STAGE_BYTES;
+    if (!mbar_wait(bars + slot, (uint32_t)((k / NSTAGE) & 1))) *abort_flag = 1;
+    float2 f[Q];
+    float2 rho = make_float2(1.f, 1.f), jx = make_float2(0.f, 0.f), jy = make_float2(0.f, 0.f);
+    unsigned m = 0;
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = load_pair<S>(st + i * G::ROW_BYTES, pos - cx(i), cx(i), p.wref[i]);
+      moments9(f, rho, jx, jy);
+      *reinterpret_cast<float2*>(&ring[k & 3][jc]) = psi_of(rho, p);
+      if (MASKED) m = *reinterpret_cast<const uint16_t*>(st + Q * G::ROW_BYTES + 2 * tid);
+    } else if (helper) {
+      const float v = hlane ? Store<S>::load_smem(reinterpret_cast<const T*>(st + hplane * G::ROW_BYTES), hpos, hbase)
+                            : 0.f;
+      const float t1 = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, 1));
+      const float t2 = __fadd_rn(t1, __shfl_xor_sync(0xffffffffu, t1, 2));
+      const float t3 = __fadd_rn(t2, __shfl_xor_sync(0xffffffffu, t2, 4));
+      const float rh = __fadd_rn(t3, __shfl_xor_sync(0xffffffffu, t2, 8));
+      if (lane == 0) ring[k & 3][1] = psi_of(rh, p);
+      if (lane == 16) ring[k & 3][width + 2] = psi_of(rh, p);
+    }
+    __syncthreads();
+    if (*abort_flag) {
+      k_abort = k;
+      break;
+    }
+    if (helper) {
+      if (k + NSTAGE - 1 < nst) issue_stage2<S, MASKED, NSTAGE>(p, src, stages, bars, k + NSTAGE - 1, y0, x0, lane);
+    } else if (k >= 2 && active) {
+      const int rc = y0 + k - 2;
+      const int srow[3] = {(k - 2) & 3, (k - 1) & 3, k & 3};  // rows rc-1, rc, rc+1
+      float2 nb[3][3];  // [row][left, centre, right] for the pair
+#pragma unroll
+      for (int r3 = 0; r3 < 3; ++r3) {
+        const float* rr = ring[srow[r3]];
+        const float2 c2 = *reinterpret_cast<const float2*>(rr + jc);
+        nb[r3][0] = make_float2(rr[jc - 1], c2.x);
+        nb[r3][1] = c2;
+        nb[r3][2] = make_float2(c2.y, rr[jc + 2]);
+      }
+      const float2 psi_c = nb[1][1];
+      float2 sv[Q];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) sv[i] = nb[cy(i) + 1][cx(i) + 1];
+      if (MASKED && m_prev) {
+        const unsigned ma = m_prev & 0xffu, mb = m_prev >> 8;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          if ((ma >> (i - 1)) & 1u) sv[i].x = psi_c.x;
+          if ((mb >> (i - 1)) & 1u) sv[i].y = psi_c.y;
+        }
+      }
+      float2 Fx, Fy;
+      force_of(sv, psi_c, p.G, Fx, Fy);
+      collide<TAU_ONE>(fprev, rho_prev, jx_prev, jy_prev, Fx, Fy, p, bad);
+      const size_t base = (size_t)rc * nx + x0 + 2 * tid;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) store_pair<S>(dst, (size_t)i * p.N + base, fprev[i], p.wref[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fprev[i] = f[i];
+    rho_prev = rho;
+    jx_prev = jx;
+    jy_prev = jy;
+    m_prev = m;
+  }
+  if (*abort_flag) {
+    if (tid == 0) {
+      atomicOr(p.flags + FLAG_TIMEOUT, 1);
+      const int issued = min(nst, k_abort + NSTAGE - 1);
+      for (int q = k_abort; q < issued; ++q) mbar_wait(bars + q % NSTAGE, (uint32_t)((q / NSTAGE) & 1), 500000000ull);
+    }
+    __syncthreads();
+    return;
+  }
+  if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
+}
+
 // Stage ring depth and CTAs per SM, from measured sweeps at 8192^2: with
 // four CTAs per SM, prefetching two rows ahead (FP32) gave more DRAM
 // throughput than deeper rings (more reads in flight lowered it).
@@ -465,6 +751,41 @@ cudaError_t launch_tma(const StepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int S>
+constexpr int tma2_stages() { return S == LBM_F32 ? 3 : 4; }
+constexpr int kTma2MinBlocks = 3;
+
+template <int S>
+bool tma2_ok(int nx) {
+  return nx % 16 == 0 && nx >= TmaGeom2<S>::WIN;
+}
+
+template <int S, bool MASKED, bool TAU_ONE>
+cudaError_t launch_tma2(const StepParams& p, cudaStream_t s) {
+  constexpr int NS = tma2_stages<S>();
+  // the relaxation blend (tau != 1) keeps both population sets live: fewer CTAs
+  auto kern = k_step_tma2<S, MASKED, TAU_ONE, NS, TAU_ONE ? kTma2MinBlocks : 2>;
+  constexpr size_t smem = tma2_smem_bytes_c<S, MASKED, NS>();
+  static int resident = 0;  // per instantiation
+  if (resident == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTmaThreads, smem);
+    if (e != cudaSuccess) return e;
+    resident = occ > 0 ? occ : 1;
+  }
+  const int gx = (p.nx + kBX2 - 1) / kBX2;
+  int g = resident * sm_count() / gx;
+  if (g < 1) g = 1;
+  if (g > p.ny) g = p.ny;
+  StepParams q = p;
+  q.rows_per_chunk = (p.ny + g - 1) / g;
+  const int gy = (p.ny + q.rows_per_chunk - 1) / q.rows_per_chunk;
+  kern<<<dim3(gx, gy), kTmaThreads, smem, s>>>(q);
+  return cudaGetLastError();
+}
+
 template <int S, bool MASKED, bool TAU_ONE>
 cudaError_t launch_strip(const StepParams& p, cudaStream_t s) {
   int gx, gy, rows, block;
@@ -475,9 +796,17 @@ cudaError_t launch_strip(const StepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Variant 0 (automatic): the two-cell staged kernel for 16-bit storage and
+// the one-cell staged kernel for FP32 (the faster of the two, measured),
+// falling back to plain loads where staging does not apply; 1: plain loads;
+// 2: one-cell staged; 3: two-cell staged.
 template <int S, bool MASKED, bool TAU_ONE>
 cudaError_t launch_variant(const StepParams& p, cudaStream_t s) {
-  if (p.force_generic != 1 && tma_ok<S>(p.nx)) return launch_tma<S, MASKED, TAU_ONE>(p, s);
+  const int v = p.force_generic;
+  if (v == 3 || (v == 0 && S != LBM_F32 && tma2_ok<S>(p.nx))) {
+    if (tma2_ok<S>(p.nx)) return launch_tma2<S, MASKED, TAU_ONE>(p, s);
+  }
+  if (v != 1 && tma_ok<S>(p.nx)) return launch_tma<S, MASKED, TAU_ONE>(p, s);
   return launch_strip<S, MASKED, TAU_ONE>(p, s);
 }
 
@@ -507,6 +836,11 @@ void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk
 bool step_tma_allowed(int storage, int nx) {
   return storage == LBM_F32 ? tma_ok<LBM_F32>(nx)
                             : (storage == LBM_F16_DEV ? tma_ok<LBM_F16_DEV>(nx) : tma_ok<LBM_BF16_DEV>(nx));
+}
+
+bool step_tma2_allowed(int storage, int nx) {
+  return storage == LBM_F32 ? tma2_ok<LBM_F32>(nx)
+                            : (storage == LBM_F16_DEV ? tma2_ok<LBM_F16_DEV>(nx) : tma2_ok<LBM_BF16_DEV>(nx));
 }
 
 cudaError_t launch_step(int storage, const StepParams& p, cudaStream_t s) {
