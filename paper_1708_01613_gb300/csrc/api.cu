@@ -367,6 +367,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
   p.G = (float)c.G;
   p.rho0 = (float)c.rho0;
   p.inv_rho0 = (float)(1.0 / c.rho0);
+  p.rho_ref = (float)c.rho_ref;
   for (int i = 0; i < Q; ++i) p.wref[i] = h->wref[i];
   for (int64_t s = 0; s < nsteps && !h->halted; ++s) {
     bool stop_after = false;

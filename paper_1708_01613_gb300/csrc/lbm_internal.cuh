@@ -50,6 +50,10 @@ struct Store<LBM_F32> {
   __device__ static __forceinline__ float load(const T* p, size_t i, float) { return __ldg(p + i); }
   __device__ static __forceinline__ float load_smem(const T* p, int i, float) { return p[i]; }
   __device__ static __forceinline__ void store(T* p, size_t i, float v, float) { p[i] = v; }
+  // raw stored value (FP32: the population itself)
+  __device__ static __forceinline__ float raw(const T* p, size_t i) { return __ldg(p + i); }
+  __device__ static __forceinline__ float raw_smem(const T* p, int i) { return p[i]; }
+  __device__ static __forceinline__ void store_raw(T* p, size_t i, float v) { p[i] = v; }
 };
 
 template <>
@@ -65,6 +69,10 @@ struct Store<LBM_F16_DEV> {
   __device__ static __forceinline__ void store(T* p, size_t i, float v, float base) {
     p[i] = __float2half_rn(__fsub_rn(v, base));
   }
+  // raw stored value: the deviation g = f - w_i rho_ref
+  __device__ static __forceinline__ float raw(const T* p, size_t i) { return __half2float(__ldg(p + i)); }
+  __device__ static __forceinline__ float raw_smem(const T* p, int i) { return __half2float(p[i]); }
+  __device__ static __forceinline__ void store_raw(T* p, size_t i, float g) { p[i] = __float2half_rn(g); }
 };
 
 template <>
@@ -80,6 +88,9 @@ struct Store<LBM_BF16_DEV> {
   __device__ static __forceinline__ void store(T* p, size_t i, float v, float base) {
     p[i] = __float2bfloat16_rn(__fsub_rn(v, base));
   }
+  __device__ static __forceinline__ float raw(const T* p, size_t i) { return __bfloat162float(__ldg(p + i)); }
+  __device__ static __forceinline__ float raw_smem(const T* p, int i) { return __bfloat162float(p[i]); }
+  __device__ static __forceinline__ void store_raw(T* p, size_t i, float g) { p[i] = __float2bfloat16_rn(g); }
 };
 
 inline int storage_bytes(int s) { return s == LBM_F32 ? 4 : 2; }
@@ -95,6 +106,7 @@ struct StepParams {
   int rows_per_chunk;    // rows marched by one CTA
   int force_generic;     // kernel variant: 0 automatic, 1 plain loads, 2 one-cell staged, 3 two-cell staged
   float tau, inv_tau, G, rho0, inv_rho0;
+  float rho_ref;         // reference density of 16-bit deviations
   float wref[Q];         // w_i * rho_ref (16-bit deviation base)
 };
 

@@ -77,6 +77,14 @@ __device__ __forceinline__ void moments9(const V f[Q], V& rho, V& jx, V& jy) {
   jy = O::add(O::sub(f[2], f[4]), O::add(O::sub(f[5], f[7]), O::sub(f[6], f[8])));
 }
 
+// Full density from the summed stored values: for 16-bit storage (DEV) the
+// stored values are deviations g_i = f_i - w_i rho_ref, whose sum is
+// rho - rho_ref (the weights sum to one).
+template <bool DEV, typename V>
+__device__ __forceinline__ V full_rho(V rho_raw, const StepParams& p) {
+  return DEV ? VOps<V>::add(VOps<V>::set(p.rho_ref), rho_raw) : rho_raw;
+}
+
 // Eq. 30.
 template <typename V>
 __device__ __forceinline__ V psi_of(V rho, const StepParams& p) {
@@ -99,17 +107,21 @@ __device__ __forceinline__ void force_of(const V s[Q], V psi_c, float G, V& Fx, 
 }
 
 // Eqs. 39-40 (u_eq = (j + tau F)/rho), Eq. 14 evaluated by opposite pairs,
-// Eq. 18 (BGK). f holds the incoming populations and receives the outgoing.
-template <bool TAU_ONE, typename V>
-__device__ __forceinline__ void collide(V f[Q], V rho, V jx, V jy, V Fx, V Fy, const StepParams& p, int& bad) {
+// Eq. 18 (BGK). f holds the incoming stored values and receives the outgoing
+// ones. With DEV the values are deviations from w_i rho_ref: j is unchanged
+// (sum e_i w_i = 0) and the equilibrium deviation is
+// w_i (rho - rho_ref - 1.5 rho u^2 + rho (3 e.u + 4.5 (e.u)^2)).
+template <bool TAU_ONE, bool DEV, typename V>
+__device__ __forceinline__ void collide(V f[Q], V rho_raw, V jx, V jy, V Fx, V Fy, const StepParams& p, int& bad) {
   using O = VOps<V>;
+  const V rho = full_rho<DEV>(rho_raw, p);
   const V ir = O::rcp(rho);
   const V tau = O::set(p.tau);
   const V ux = O::mul(O::fma(tau, Fx, jx), ir);
   const V uy = O::mul(O::fma(tau, Fy, jy), ir);
   bad |= O::bad(rho);
   const V uu = O::fma(ux, ux, O::mul(uy, uy));
-  const V a = O::mul(rho, O::fma(O::set(-1.5f), uu, O::set(1.0f)));
+  const V a = DEV ? O::fma(O::mul(O::set(-1.5f), rho), uu, rho_raw) : O::mul(rho, O::fma(O::set(-1.5f), uu, O::set(1.0f)));
   const V r3 = O::mul(O::set(3.0f), rho), r45 = O::mul(O::set(4.5f), rho);
   const V w1 = O::set(kW1), w5 = O::set(kW5);
   V feq[Q];
@@ -158,9 +170,9 @@ __device__ __forceinline__ void finish_cell(float f[Q], float rho, float jx, flo
   }
   float Fx, Fy;
   force_of(s, psi_c, p.G, Fx, Fy);
-  collide<TAU_ONE>(f, rho, jx, jy, Fx, Fy, p, bad);
+  collide<TAU_ONE, S != LBM_F32>(f, rho, jx, jy, Fx, Fy, p, bad);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Store<S>::store(dst, (size_t)i * p.N + base, f[i], p.wref[i]);
+  for (int i = 0; i < Q; ++i) Store<S>::store_raw(dst, (size_t)i * p.N + base, f[i]);
 }
 
 // ---------------------------------------------------------------- plain-load kernel
@@ -173,7 +185,7 @@ __device__ __forceinline__ void pull_cell(const typename Store<S>::T* __restrict
   for (int i = 0; i < Q; ++i) {
     const long long row = cy(i) > 0 ? rowm : (cy(i) < 0 ? rowp : row0);
     const int xs = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : x);
-    f[i] = Store<S>::load(src, (size_t)i * p.N + row + xs, p.wref[i]);
+    f[i] = Store<S>::raw(src, (size_t)i * p.N + row + xs);
   }
 }
 
@@ -213,19 +225,19 @@ __global__ void __launch_bounds__(kBX) k_step_strip(const StepParams p) {
     if (active) {
       pull_cell<S>(src, p, rowm, row0, rowp, xm, x, xp, f);
       moments9(f, rho, jx, jy);
-      ring[k & 3][jc] = psi_of(rho, p);
+      ring[k & 3][jc] = psi_of(full_rho<S != LBM_F32>(rho, p), p);
     }
     if (tid == 0) {
       float h[Q], rh, hx, hy;
       pull_cell<S>(src, p, rowm, row0, rowp, xlm, xl, x0, h);
       moments9(h, rh, hx, hy);
-      ring[k & 3][0] = psi_of(rh, p);
+      ring[k & 3][0] = psi_of(full_rho<S != LBM_F32>(rh, p), p);
     }
     if (x == last) {
       float h[Q], rh, hx, hy;
       pull_cell<S>(src, p, rowm, row0, rowp, last, xr, xrp, h);
       moments9(h, rh, hx, hy);
-      ring[k & 3][last - x0 + 2] = psi_of(rh, p);
+      ring[k & 3][last - x0 + 2] = psi_of(full_rho<S != LBM_F32>(rh, p), p);
     }
     __syncthreads();
     if (k >= 2 && active) {
@@ -387,10 +399,6 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma(const StepParams
   const bool hlane = helper && hplane < Q;
   const int hcx = (hplane == 1 || hplane == 5 || hplane == 8) ? 1 : ((hplane == 3 || hplane == 6 || hplane == 7) ? -1 : 0);
   const int hpos = (lane < 16 ? G::PAD - 1 : G::PAD + width) - hcx;
-  float hbase = 0.f;  // selected without dynamic indexing of the parameter block
-#pragma unroll
-  for (int i = 0; i < Q; ++i)
-    if (hlane && i == hplane) hbase = p.wref[i];
 
   const int jc = tid + 1;
   const int pos = G::PAD + tid;
@@ -409,18 +417,17 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma(const StepParams
     if (active) {
 #pragma unroll
       for (int i = 0; i < Q; ++i)
-        f[i] = Store<S>::load_smem(reinterpret_cast<const T*>(st + i * G::ROW_BYTES), pos - cx(i), p.wref[i]);
+        f[i] = Store<S>::raw_smem(reinterpret_cast<const T*>(st + i * G::ROW_BYTES), pos - cx(i));
       moments9(f, rho, jx, jy);
-      ring[k & 3][jc] = psi_of(rho, p);
+      ring[k & 3][jc] = psi_of(full_rho<S != LBM_F32>(rho, p), p);
       if (MASKED) m = st[Q * G::ROW_BYTES + tid];
     } else if (helper) {
       // same summation order as moments9: ((f0+f1)+(f2+f3)) + ((f4+f5)+(f6+f7)) + f8
-      const float v = hlane ? Store<S>::load_smem(reinterpret_cast<const T*>(st + hplane * G::ROW_BYTES), hpos, hbase)
-                            : 0.f;
-      const float t1 = v + __shfl_xor_sync(0xffffffffu, v, 1);
-      const float t2 = t1 + __shfl_xor_sync(0xffffffffu, t1, 2);
-      const float t3 = t2 + __shfl_xor_sync(0xffffffffu, t2, 4);
-      const float rh = t3 + __shfl_xor_sync(0xffffffffu, t2, 8);
+      const float v = hlane ? Store<S>::raw_smem(reinterpret_cast<const T*>(st + hplane * G::ROW_BYTES), hpos) : 0.f;
+      const float t1 = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, 1));
+      const float t2 = __fadd_rn(t1, __shfl_xor_sync(0xffffffffu, t1, 2));
+      const float t3 = __fadd_rn(t2, __shfl_xor_sync(0xffffffffu, t2, 4));
+      const float rh = full_rho<S != LBM_F32>(__fadd_rn(t3, __shfl_xor_sync(0xffffffffu, t2, 8)), p);
       if (lane == 0) ring[k & 3][0] = psi_of(rh, p);
       if (lane == 16) ring[k & 3][width + 1] = psi_of(rh, p);
     }
@@ -476,12 +483,12 @@ struct TmaGeom2 {
   static constexpr int STAGE_BYTES_MASKED = Q * ROW_BYTES + kBX2;
 };
 
-// Two consecutive staged values (window positions pos, pos+1) as floats.
+// Two consecutive staged raw values (window positions pos, pos+1) as floats.
 template <int S>
-__device__ __forceinline__ float2 load_pair(const unsigned char* row, int pos, int shift, float base);
+__device__ __forceinline__ float2 load_pair(const unsigned char* row, int pos, int shift);
 
 template <>
-__device__ __forceinline__ float2 load_pair<LBM_F32>(const unsigned char* row, int pos, int shift, float) {
+__device__ __forceinline__ float2 load_pair<LBM_F32>(const unsigned char* row, int pos, int shift) {
   const float* r = reinterpret_cast<const float*>(row);
   if (shift == 0) return *reinterpret_cast<const float2*>(r + pos);  // pos even: 8-byte aligned
   return make_float2(r[pos], r[pos + 1]);
@@ -494,41 +501,39 @@ __device__ __forceinline__ uint32_t pair_bits_16(const unsigned char* row, int p
   return __byte_perm(w[(pos - 1) >> 1], w[(pos + 1) >> 1], 0x5432);
 }
 
-// 16-bit pairs are decoded element by element with the same conversion and
-// rounded add as the one-cell kernels (the packed conversions and adds gave
-// different results for small deviations), so all kernels agree bitwise.
+// 16-bit pairs are converted element by element with the same conversion as
+// the one-cell kernels (the packed conversions gave different results for
+// small deviations), so all kernels agree bitwise.
 template <>
-__device__ __forceinline__ float2 load_pair<LBM_F16_DEV>(const unsigned char* row, int pos, int shift, float base) {
+__device__ __forceinline__ float2 load_pair<LBM_F16_DEV>(const unsigned char* row, int pos, int shift) {
   const uint32_t b = pair_bits_16(row, pos, shift);
   const __half2 h = *reinterpret_cast<const __half2*>(&b);
-  return make_float2(__fadd_rn(base, __low2float(h)), __fadd_rn(base, __high2float(h)));
+  return make_float2(__low2float(h), __high2float(h));
 }
 
 template <>
-__device__ __forceinline__ float2 load_pair<LBM_BF16_DEV>(const unsigned char* row, int pos, int shift, float base) {
+__device__ __forceinline__ float2 load_pair<LBM_BF16_DEV>(const unsigned char* row, int pos, int shift) {
   const uint32_t b = pair_bits_16(row, pos, shift);
   const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&b);
-  return make_float2(__fadd_rn(base, __low2float(h)), __fadd_rn(base, __high2float(h)));
+  return make_float2(__low2float(h), __high2float(h));
 }
 
 template <int S>
-__device__ __forceinline__ void store_pair(typename Store<S>::T* dst, size_t idx, float2 v, float base);
+__device__ __forceinline__ void store_pair(typename Store<S>::T* dst, size_t idx, float2 v);
 
 template <>
-__device__ __forceinline__ void store_pair<LBM_F32>(float* dst, size_t idx, float2 v, float) {
+__device__ __forceinline__ void store_pair<LBM_F32>(float* dst, size_t idx, float2 v) {
   *reinterpret_cast<float2*>(dst + idx) = v;  // idx even
 }
 
 template <>
-__device__ __forceinline__ void store_pair<LBM_F16_DEV>(__half* dst, size_t idx, float2 v, float base) {
-  *reinterpret_cast<__half2*>(dst + idx) =
-      __halves2half2(__float2half_rn(__fsub_rn(v.x, base)), __float2half_rn(__fsub_rn(v.y, base)));
+__device__ __forceinline__ void store_pair<LBM_F16_DEV>(__half* dst, size_t idx, float2 v) {
+  *reinterpret_cast<__half2*>(dst + idx) = __halves2half2(__float2half_rn(v.x), __float2half_rn(v.y));
 }
 
 template <>
-__device__ __forceinline__ void store_pair<LBM_BF16_DEV>(__nv_bfloat16* dst, size_t idx, float2 v, float base) {
-  *reinterpret_cast<__nv_bfloat162*>(dst + idx) =
-      __halves2bfloat162(__float2bfloat16_rn(__fsub_rn(v.x, base)), __float2bfloat16_rn(__fsub_rn(v.y, base)));
+__device__ __forceinline__ void store_pair<LBM_BF16_DEV>(__nv_bfloat16* dst, size_t idx, float2 v) {
+  *reinterpret_cast<__nv_bfloat162*>(dst + idx) = __halves2bfloat162(__float2bfloat16_rn(v.x), __float2bfloat16_rn(v.y));
 }
 
 template <int S, bool MASKED, int NSTAGE>
@@ -604,10 +609,6 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
   const bool hlane = helper && hplane < Q;
   const int hcx = (hplane == 1 || hplane == 5 || hplane == 8) ? 1 : ((hplane == 3 || hplane == 6 || hplane == 7) ? -1 : 0);
   const int hpos = (lane < 16 ? G::PAD - 1 : G::PAD + width) - hcx;
-  float hbase = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i)
-    if (hlane && i == hplane) hbase = p.wref[i];
 
   const int jc = 2 * tid + 2;      // ring index of the first cell of the pair
   const int pos = G::PAD + 2 * tid;  // window position of the first cell
@@ -625,17 +626,16 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
     unsigned m = 0;
     if (active) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = load_pair<S>(st + i * G::ROW_BYTES, pos - cx(i), cx(i), p.wref[i]);
+      for (int i = 0; i < Q; ++i) f[i] = load_pair<S>(st + i * G::ROW_BYTES, pos - cx(i), cx(i));
       moments9(f, rho, jx, jy);
-      *reinterpret_cast<float2*>(&ring[k & 3][jc]) = psi_of(rho, p);
+      *reinterpret_cast<float2*>(&ring[k & 3][jc]) = psi_of(full_rho<S != LBM_F32>(rho, p), p);
       if (MASKED) m = *reinterpret_cast<const uint16_t*>(st + Q * G::ROW_BYTES + 2 * tid);
     } else if (helper) {
-      const float v = hlane ? Store<S>::load_smem(reinterpret_cast<const T*>(st + hplane * G::ROW_BYTES), hpos, hbase)
-                            : 0.f;
+      const float v = hlane ? Store<S>::raw_smem(reinterpret_cast<const T*>(st + hplane * G::ROW_BYTES), hpos) : 0.f;
       const float t1 = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, 1));
       const float t2 = __fadd_rn(t1, __shfl_xor_sync(0xffffffffu, t1, 2));
       const float t3 = __fadd_rn(t2, __shfl_xor_sync(0xffffffffu, t2, 4));
-      const float rh = __fadd_rn(t3, __shfl_xor_sync(0xffffffffu, t2, 8));
+      const float rh = full_rho<S != LBM_F32>(__fadd_rn(t3, __shfl_xor_sync(0xffffffffu, t2, 8)), p);
       if (lane == 0) ring[k & 3][1] = psi_of(rh, p);
       if (lane == 16) ring[k & 3][width + 2] = psi_of(rh, p);
     }
@@ -672,10 +672,10 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
       }
       float2 Fx, Fy;
       force_of(sv, psi_c, p.G, Fx, Fy);
-      collide<TAU_ONE>(fprev, rho_prev, jx_prev, jy_prev, Fx, Fy, p, bad);
+      collide<TAU_ONE, S != LBM_F32>(fprev, rho_prev, jx_prev, jy_prev, Fx, Fy, p, bad);
       const size_t base = (size_t)rc * nx + x0 + 2 * tid;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) store_pair<S>(dst, (size_t)i * p.N + base, fprev[i], p.wref[i]);
+      for (int i = 0; i < Q; ++i) store_pair<S>(dst, (size_t)i * p.N + base, fprev[i]);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) fprev[i] = f[i];
@@ -751,9 +751,11 @@ cudaError_t launch_tma(const StepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Measured at 8192^2 (FP16): 4 stages at 4 CTAs per SM (56 registers, no
+// spills) beat deeper rings and 3 or 5 CTAs per SM.
 template <int S>
 constexpr int tma2_stages() { return S == LBM_F32 ? 3 : 4; }
-constexpr int kTma2MinBlocks = 3;
+constexpr int kTma2MinBlocks = 4;
 
 template <int S>
 bool tma2_ok(int nx) {
