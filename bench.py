@@ -42,6 +42,8 @@ WORKLOADS = {
                     "G=-5.5, tau=1, psi=1-exp(-rho), film barrier on (R_z=4)"),
     "small": dict(n=2048, bubbles=25, rmin=8.0, rmax=64.0, seed=21,
                   desc="2048^2 periodic D2Q9, 25 Poisson-disk bubbles r 8-64 (profiling case)"),
+    "mid": dict(n=4096, bubbles=100, rmin=8.0, rmax=64.0, seed=21,
+                desc="4096^2 periodic D2Q9, 100 Poisson-disk bubbles r 8-64 (profiling case, state > L2)"),
 }
 
 
@@ -235,7 +237,7 @@ def run_gpu(args, world, rank, local):
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_cell": bytes_cell,
-                "kernel": "k_step_tma" if n % 16 == 0 else "k_step_strip",
+                "kernel": ("k_step_tma" if storage == "f32" else "k_step_tma2") if n % 16 == 0 else "k_step_strip",
                 "kernel_ms_avg": round(kern_ms, 5),
                 "kernel_mlups": round(N / (kern_ms * 1e-3) / 1e6, 1),
                 "roofline_mlups": round(peak * 1e9 / bytes_cell / 1e6, 1)}
