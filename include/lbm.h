@@ -147,11 +147,11 @@ int64_t lbm_kernel_launches(const lbm_handle* h);
 
 /* Selects the fused-step kernel: 0 = automatic, 1 = plain-load kernel (any
  * box), 2 = TMA-staged kernel with one cell per thread (nx % 16 == 0 and
- * nx >= 272), 3 = TMA-staged kernel with two cells per thread and packed FP32
- * arithmetic (nx % 16 == 0 and nx >= 528). Automatic picks 3 for 16-bit
- * storage and 2 for FP32 where the box allows, else 1. A variant the box
- * does not allow returns LBM_ENOTSUP. All variants compute the same
- * operations in the same order and give bitwise the same populations. */
+ * nx >= 272), 3 = TMA-staged kernel with two cells per thread
+ * (nx % 16 == 0). Automatic picks 3 for 16-bit storage and 2 for FP32 where
+ * the box allows, else 1. A variant the box does not allow returns
+ * LBM_ENOTSUP. All variants compute the same operations in the same order
+ * and give bitwise the same populations. */
 int lbm_set_step_variant(lbm_handle* h, int variant);
 
 /* Steps done since the last init/load. */
@@ -186,6 +186,64 @@ const char* lbm_last_error(const lbm_handle* h);
 
 /* Frees the host handle (not the workspace). NULL is allowed. */
 void lbm_destroy(lbm_handle* h);
+
+/* ---------------------------------------------------------------------
+ * Batches: many boxes advanced together. Not in the paper; it serves runs
+ * of many independent foam simulations on one GPU. Every step of a batch is
+ * one persistent launch of the two-cell staged kernel over a list of work
+ * items (box, column strip, row chunk) of all active boxes, preceded, when a
+ * relabel is due, by each box's barrier pipeline; blocks of steps are
+ * captured as CUDA graphs and replayed. Each box evolves bitwise as it would
+ * when stepped alone with lbm_step.
+ *
+ * Rules: all boxes share storage, barrier setting and relabel period, are
+ * on one device, are at the same step count, have nx % 16 == 0, and do not
+ * stop on rupture. The batch works on a stream of its own (created by
+ * lbm_batch_create; the legacy default stream cannot be captured into a
+ * graph), ordered by events after earlier work on the first box's stream,
+ * and later work on that stream is ordered after each lbm_batch_step. A box
+ * in a batch may not be stepped with lbm_step. */
+typedef struct lbm_batch lbm_batch;
+
+/* Device bytes lbm_batch_create needs for these boxes (0 if invalid). */
+size_t lbm_batch_workspace_bytes(lbm_handle* const* handles, int32_t n);
+
+/* Creates a batch over n handles with a caller-owned device workspace
+ * (256-byte aligned). LBM_EINVAL / LBM_ENOTSUP / LBM_ENOMEM on rule or size
+ * violations. */
+int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, size_t bytes, lbm_batch** out);
+
+/* Work-item shape: strip width 256 or 512 columns, chunk height a multiple
+ * of 8 rows. Changes invalidate the captured graphs. */
+int lbm_batch_set_tiles(lbm_batch* b, int32_t strip_width, int32_t chunk_rows);
+int lbm_batch_get_tiles(const lbm_batch* b, int32_t* strip_width, int32_t* chunk_rows);
+
+/* Autotuner: times every (strip width, chunk height) candidate for
+ * trial_steps steps on the batch itself and keeps the fastest. The boxes
+ * advance by (trial_steps + 1) steps per candidate (10 candidates), as
+ * ordinary steps (relabels included). */
+int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, float* best_ms_per_step);
+
+/* 1 (default): replay captured graphs of whole relabel periods; 0: launch
+ * step by step. Results are identical. */
+int lbm_batch_use_graph(lbm_batch* b, int enable);
+
+/* Excludes (0) or re-includes (1) box `index`; a box re-included must be at
+ * the batch's step count. */
+int lbm_batch_set_active(lbm_batch* b, int32_t index, int active);
+
+/* Enqueues nsteps steps of every active box (asynchronous). */
+int lbm_batch_step(lbm_batch* b, int64_t nsteps);
+
+/* Synchronises the batch stream and reports device faults of any box. */
+int lbm_batch_sync(lbm_batch* b);
+
+int64_t lbm_batch_steps_done(const lbm_batch* b);
+int64_t lbm_batch_kernel_launches(const lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Frees the batch (not the workspace); the boxes can be stepped alone again. */
+void lbm_batch_destroy(lbm_batch* b);
 
 /* Allocation-free FP64 mass (sum of all populations) of a caller-held
  * population buffer: d_pops holds 9 * nx * ny values of `storage` (FP32

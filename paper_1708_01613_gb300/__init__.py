@@ -5,6 +5,7 @@ The compute path is the CUDA library ``liblbm.so`` (C ABI in include/lbm.h);
 ``paper_1708_01613_gb300.lbm`` is its ctypes binding.
 """
 from .lbm import (  # noqa: F401
+    Batch,
     LbmError,
     Simulation,
     lbm_config,

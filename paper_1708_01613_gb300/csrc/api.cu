@@ -14,7 +14,7 @@
 
 #include <new>
 
-#include "lbm_internal.cuh"
+#include "handle.cuh"
 
 using namespace lbm;
 
@@ -23,10 +23,7 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-struct Layout {
-  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, tile_list, flags, partials, scalars, total;
-  int nparts, ntiles;
-};
+
 
 bool valid_config(const lbm_config* c, char* why, size_t n) {
   if (!c) return snprintf(why, n, "config is NULL"), false;
@@ -83,34 +80,7 @@ Layout layout_for(const lbm_config& c) {
 
 }  // namespace
 
-struct lbm_handle {
-  lbm_config cfg;
-  Layout L;
-  char* ws;
-  cudaStream_t stream;
-  int device;
-  int cur;
-  int64_t t;
-  int64_t launches;
-  int variant;
-  int halted;
-  float wref[Q];
-  char err[320];
 
-  void* pops(int k) { return ws + L.pops[k]; }
-  float* rho() { return reinterpret_cast<float*>(ws + L.rho); }
-  int32_t* label() { return reinterpret_cast<int32_t*>(ws + L.label); }
-  int32_t* owner() { return cfg.barrier ? reinterpret_cast<int32_t*>(ws + L.owner) : nullptr; }
-  uint8_t* mask() { return cfg.barrier ? reinterpret_cast<uint8_t*>(ws + L.mask) : nullptr; }
-  uint8_t* open() { return cfg.barrier ? reinterpret_cast<uint8_t*>(ws + L.open) : nullptr; }
-  int8_t* sgn() { return cfg.barrier ? reinterpret_cast<int8_t*>(ws + L.sgn) : nullptr; }
-  uint8_t* tiles(int k) { return reinterpret_cast<uint8_t*>(ws + L.tiles) + (size_t)k * L.ntiles; }
-  int* flags() { return reinterpret_cast<int*>(ws + L.flags); }
-  double* partials() { return reinterpret_cast<double*>(ws + L.partials); }
-  double* scalars() { return reinterpret_cast<double*>(ws + L.scalars); }
-  size_t N() const { return (size_t)cfg.nx * cfg.ny; }
-  size_t pops_bytes() const { return Q * N() * storage_bytes(cfg.storage); }
-};
 
 namespace {
 
@@ -222,6 +192,43 @@ size_t field_bytes(const lbm_handle* h, uint32_t bit) {
 constexpr uint32_t kAllFields = (LBM_FIELD_POPS << 1) - 1;
 
 }  // namespace
+
+namespace lbm {
+
+int handle_fail(lbm_handle* h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int handle_relabel(lbm_handle* h) { return relabel(h); }
+
+int handle_check_flags(lbm_handle* h) { return check_flags(h); }
+
+StepParams handle_step_params(lbm_handle* h) {
+  const lbm_config& c = h->cfg;
+  StepParams p{};
+  p.mask = c.barrier ? h->mask() : nullptr;
+  p.force_generic = h->variant;
+  p.flags = h->flags();
+  p.nx = c.nx;
+  p.ny = c.ny;
+  p.N = (long long)h->N();
+  p.tau = (float)c.tau;
+  p.inv_tau = (float)(1.0 / c.tau);
+  p.G = (float)c.G;
+  p.rho0 = (float)c.rho0;
+  p.inv_rho0 = (float)(1.0 / c.rho0);
+  p.rho_ref = (float)c.rho_ref;
+  for (int i = 0; i < Q; ++i) p.wref[i] = h->wref[i];
+  return p;
+}
+
+}  // namespace lbm
 
 extern "C" {
 
@@ -352,23 +359,11 @@ int lbm_load_populations(lbm_handle* h, const float* f, int src_is_device) {
 int lbm_step(lbm_handle* h, int64_t nsteps) {
   if (!h) return LBM_EINVAL;
   if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
+  if (h->in_batch) return fail(h, LBM_EINVAL, "handle belongs to a batch; step it through lbm_batch_step");
   int rc = select_device(h);
   if (rc) return rc;
   const lbm_config& c = h->cfg;
-  StepParams p{};
-  p.mask = nullptr;
-  p.force_generic = h->variant;
-  p.flags = h->flags();
-  p.nx = c.nx;
-  p.ny = c.ny;
-  p.N = (long long)h->N();
-  p.tau = (float)c.tau;
-  p.inv_tau = (float)(1.0 / c.tau);
-  p.G = (float)c.G;
-  p.rho0 = (float)c.rho0;
-  p.inv_rho0 = (float)(1.0 / c.rho0);
-  p.rho_ref = (float)c.rho_ref;
-  for (int i = 0; i < Q; ++i) p.wref[i] = h->wref[i];
+  StepParams p = handle_step_params(h);
   for (int64_t s = 0; s < nsteps && !h->halted; ++s) {
     bool stop_after = false;
     if (c.barrier && h->t % c.relabel_every == 0) {
@@ -383,7 +378,6 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     }
     p.src = h->pops(h->cur);
     p.dst = h->pops(1 - h->cur);
-    p.mask = c.barrier ? h->mask() : nullptr;
     CUDA_TRY(h, launch_step(c.storage, p, h->stream));
     h->launches += 1;
     h->cur ^= 1;
@@ -403,7 +397,7 @@ int lbm_set_step_variant(lbm_handle* h, int variant) {
   if (variant == 2 && !step_tma_allowed(h->cfg.storage, h->cfg.nx))
     return fail(h, LBM_ENOTSUP, "TMA-staged step needs nx %% 16 == 0 and nx >= 272");
   if (variant == 3 && !step_tma2_allowed(h->cfg.storage, h->cfg.nx))
-    return fail(h, LBM_ENOTSUP, "two-cell staged step needs nx %% 16 == 0 and nx >= 528");
+    return fail(h, LBM_ENOTSUP, "two-cell staged step needs nx %% 16 == 0");
   h->variant = variant;
   return LBM_OK;
 }

@@ -1,0 +1,432 @@
+// Batched time stepping of many boxes (C ABI lbm_batch_*, include/lbm.h).
+//
+// A batch advances several independent boxes together: every step is one
+// persistent launch of the two-cell staged kernel over a list of work items
+// (box, column strip, row chunk) that covers all active boxes, preceded, when
+// a relabel is due, by each box's barrier pipeline. Blocks of K steps (K =
+// relabel period) are captured once as CUDA graphs and replayed. The strip
+// width and chunk height of the work items are picked by lbm_batch_tune,
+// which times the candidates on the batch itself. Per-cell arithmetic is the
+// one of the single-box kernels, so every box evolves bitwise as it would
+// alone.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "handle.cuh"
+
+using namespace lbm;
+
+struct lbm_batch {
+  std::vector<lbm_handle*> h;
+  std::vector<int> active;
+  std::vector<int> base_cur;   // h[i]->cur when the descriptors were uploaded
+  int n = 0;
+  int storage = 0, masked = 0, tau_one = 1, K = 1;
+  int64_t t = 0;               // common step counter
+  int par = 0;                 // steps since upload, mod 2
+  cudaStream_t stream = nullptr;      // the batch's own stream (capturable)
+  cudaStream_t ext = nullptr;         // the boxes' stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  BatchInst* d_insts = nullptr;
+  BatchItem* d_items = nullptr;
+  int* d_counter = nullptr;
+  int max_items = 0;
+  int nitems = 0;
+  std::vector<BatchItem> items;
+  int strip = 512, rows = 0;
+  int use_graph = 1;
+  int dirty = 1;               // descriptors/items must be re-uploaded
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // K-step block starting at parity 0 / 1
+  int64_t launches = 0;
+  char err[320] = {0};
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int bfail(lbm_batch* b, int code, const char* fmt, ...) {
+  if (b) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b->err, sizeof(b->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define BCUDA(b, expr)                                                               \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess) return bfail((b), LBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Upper bound of work items for any tile choice the batch accepts.
+int max_items_for(lbm_handle* const* hs, int n) {
+  long long m = 0;
+  for (int i = 0; i < n; ++i) m += (long long)((hs[i]->cfg.nx + 255) / 256) * ((hs[i]->cfg.ny + 7) / 8);
+  return m > 0x7fffffff ? 0x7fffffff : (int)m;
+}
+
+void drop_graphs(lbm_batch* b) {
+  for (int k = 0; k < 2; ++k)
+    if (b->graph[k]) {
+      cudaGraphExecDestroy(b->graph[k]);
+      b->graph[k] = nullptr;
+    }
+}
+
+void build_items(lbm_batch* b) {
+  b->items.clear();
+  for (int i = 0; i < b->n; ++i) {
+    if (!b->active[i]) continue;
+    const int nx = b->h[i]->cfg.nx, ny = b->h[i]->cfg.ny;
+    for (int x0 = 0; x0 < nx; x0 += b->strip)
+      for (int y0 = 0; y0 < ny; y0 += b->rows) {
+        BatchItem it;
+        it.inst = i;
+        it.x0 = x0;
+        it.width = std::min(b->strip, nx - x0);
+        it.y0 = y0;
+        it.y1 = std::min(y0 + b->rows, ny);
+        b->items.push_back(it);
+      }
+  }
+  // largest items first: the dynamic queue then balances like LPT scheduling
+  std::stable_sort(b->items.begin(), b->items.end(), [](const BatchItem& a, const BatchItem& c) {
+    return (long long)a.width * (a.y1 - a.y0) > (long long)c.width * (c.y1 - c.y0);
+  });
+  b->nitems = (int)b->items.size();
+}
+
+// Re-uploads descriptors and items (host-synchronous copies).
+int upload(lbm_batch* b) {
+  if (!b->dirty) return LBM_OK;
+  std::vector<BatchInst> insts(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    lbm_handle* h = b->h[i];
+    BatchInst& d = insts[i];
+    memset(&d, 0, sizeof(d));
+    d.pops0 = h->pops(0);
+    d.pops1 = h->pops(1);
+    d.mask = h->cfg.barrier ? h->mask() : nullptr;
+    d.flags = h->flags();
+    d.nx = h->cfg.nx;
+    d.ny = h->cfg.ny;
+    d.tau = (float)h->cfg.tau;
+    d.inv_tau = (float)(1.0 / h->cfg.tau);
+    d.G = (float)h->cfg.G;
+    d.rho0 = (float)h->cfg.rho0;
+    d.inv_rho0 = (float)(1.0 / h->cfg.rho0);
+    d.rho_ref = (float)h->cfg.rho_ref;
+    d.cur = h->cur;
+    b->base_cur[i] = h->cur;
+  }
+  build_items(b);
+  if (b->nitems > b->max_items) return bfail(b, LBM_EINVAL, "too many work items (%d > %d)", b->nitems, b->max_items);
+  BCUDA(b, cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice, b->stream));
+  if (b->nitems)
+    BCUDA(b, cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(BatchItem) * b->nitems, cudaMemcpyHostToDevice,
+                             b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  b->par = 0;
+  b->dirty = 0;
+  drop_graphs(b);
+  return LBM_OK;
+}
+
+// Host bookkeeping after `n` steps of every active box.
+void advance(lbm_batch* b, int64_t n) {
+  b->t += n;
+  b->par ^= (int)(n & 1);
+  for (int i = 0; i < b->n; ++i)
+    if (b->active[i]) {
+      b->h[i]->t += n;
+      b->h[i]->cur = b->base_cur[i] ^ b->par;
+    }
+}
+
+// Enqueues one step (relabels when due, then the batched kernel).
+int enqueue_step(lbm_batch* b, int parity, bool relabel_now) {
+  int rc;
+  if (b->masked && relabel_now)
+    for (int i = 0; i < b->n; ++i) {
+      if (!b->active[i]) continue;
+      lbm_handle* h = b->h[i];
+      const int saved = h->cur;
+      h->cur = b->base_cur[i] ^ parity;
+      cudaStream_t hs = h->stream;
+      h->stream = b->stream;
+      rc = handle_relabel(h);
+      h->stream = hs;
+      h->cur = saved;
+      if (rc) return bfail(b, rc, "relabel of box %d: %s", i, h->err);
+      b->launches += 7;
+    }
+  BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items, b->nitems,
+                             b->d_counter, parity, b->stream));
+  b->launches += 1;
+  return LBM_OK;
+}
+
+int build_graph(lbm_batch* b, int start_parity) {
+  cudaGraph_t g = nullptr;
+  BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  const int64_t saved = b->launches;
+  int rc = LBM_OK;
+  for (int j = 0; j < b->K && rc == LBM_OK; ++j) rc = enqueue_step(b, start_parity ^ (j & 1), b->masked && j == 0);
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  b->launches = saved;  // counted again at every replay
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&b->graph[start_parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) return bfail(b, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+  return LBM_OK;
+}
+
+// The batch works on its own stream (the legacy default stream cannot be
+// captured); events order it after earlier work on the boxes' stream and
+// order later work there after it.
+int enter(lbm_batch* b) {
+  BCUDA(b, cudaEventRecord(b->ev_in, b->ext));
+  BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+  return LBM_OK;
+}
+
+int leave(lbm_batch* b) {
+  BCUDA(b, cudaEventRecord(b->ev_out, b->stream));
+  BCUDA(b, cudaStreamWaitEvent(b->ext, b->ev_out, 0));
+  return LBM_OK;
+}
+
+int active_count(const lbm_batch* b) {
+  int c = 0;
+  for (int i = 0; i < b->n; ++i) c += b->active[i] != 0;
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_batch_workspace_bytes(lbm_handle* const* handles, int32_t n) {
+  if (!handles || n <= 0) return 0;
+  for (int i = 0; i < n; ++i)
+    if (!handles[i]) return 0;
+  const int mi = max_items_for(handles, n);
+  return align_up(sizeof(BatchInst) * (size_t)n) + align_up(sizeof(BatchItem) * (size_t)mi) + kAlign;
+}
+
+int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, size_t bytes, lbm_batch** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!handles || n <= 0 || !d_workspace || ((uintptr_t)d_workspace % kAlign)) return LBM_EINVAL;
+  if (bytes < lbm_batch_workspace_bytes(handles, n)) return LBM_ENOMEM;
+  lbm_handle* h0 = handles[0];
+  for (int i = 0; i < n; ++i) {
+    lbm_handle* h = handles[i];
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == h) return LBM_EINVAL;  // a box appears twice
+    if (h->in_batch) return LBM_EINVAL;
+    if (h->cfg.storage != h0->cfg.storage || h->cfg.barrier != h0->cfg.barrier) return LBM_EINVAL;
+    if (h->cfg.barrier && h->cfg.relabel_every != h0->cfg.relabel_every) return LBM_EINVAL;
+    if (h->cfg.stop_on_first_rupture) return LBM_ENOTSUP;
+    if (h->t != h0->t || h->device != h0->device || h->halted) return LBM_EINVAL;
+    if (h->cfg.nx % 16 != 0) return LBM_ENOTSUP;  // bulk copies need 16-byte rows
+  }
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ENOMEM;
+  b->n = n;
+  b->h.assign(handles, handles + n);
+  b->active.assign(n, 1);
+  b->base_cur.assign(n, 0);
+  b->storage = h0->cfg.storage;
+  b->masked = h0->cfg.barrier;
+  // graph block: one relabel period with the barrier, else 16 steps
+  b->K = h0->cfg.barrier ? h0->cfg.relabel_every : 16;
+  b->t = h0->t;
+  b->tau_one = 1;
+  for (int i = 0; i < n; ++i) b->tau_one &= (float)handles[i]->cfg.tau == 1.0f;
+  b->ext = h0->stream;
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    delete b;
+    return LBM_ECUDA;
+  }
+  b->ws = static_cast<char*>(d_workspace);
+  b->ws_bytes = bytes;
+  b->max_items = max_items_for(handles, n);
+  b->d_insts = reinterpret_cast<BatchInst*>(b->ws);
+  b->d_items = reinterpret_cast<BatchItem*>(b->ws + align_up(sizeof(BatchInst) * (size_t)n));
+  b->d_counter = reinterpret_cast<int*>(b->ws + align_up(sizeof(BatchInst) * (size_t)n) +
+                                        align_up(sizeof(BatchItem) * (size_t)b->max_items));
+  // default tiles: full-width strips, chunks giving ~4 items per resident CTA
+  long long cells = 0;
+  for (int i = 0; i < n; ++i) cells += (long long)handles[i]->cfg.nx * handles[i]->cfg.ny;
+  const int res = batch_resident_ctas(b->storage, b->masked != 0, b->tau_one != 0);
+  long long r = res > 0 ? cells / ((long long)512 * 4 * res) : 128;
+  r = std::max(32LL, std::min(512LL, (r + 7) / 8 * 8));
+  b->rows = (int)r;
+  for (int i = 0; i < n; ++i) handles[i]->in_batch = 1;
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_set_tiles(lbm_batch* b, int32_t strip_width, int32_t chunk_rows) {
+  if (!b) return LBM_EINVAL;
+  if (strip_width != 256 && strip_width != 512) return bfail(b, LBM_EINVAL, "strip width must be 256 or 512");
+  if (chunk_rows < 8 || chunk_rows % 8) return bfail(b, LBM_EINVAL, "chunk rows must be a multiple of 8, >= 8");
+  if (strip_width != b->strip || chunk_rows != b->rows) {
+    b->strip = strip_width;
+    b->rows = chunk_rows;
+    b->dirty = 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_get_tiles(const lbm_batch* b, int32_t* strip_width, int32_t* chunk_rows) {
+  if (!b) return LBM_EINVAL;
+  if (strip_width) *strip_width = b->strip;
+  if (chunk_rows) *chunk_rows = b->rows;
+  return LBM_OK;
+}
+
+int lbm_batch_set_active(lbm_batch* b, int32_t index, int active) {
+  if (!b) return LBM_EINVAL;
+  if (index < 0 || index >= b->n) return bfail(b, LBM_EINVAL, "index out of range");
+  const int a = active ? 1 : 0;
+  if (a && !b->active[index] && b->h[index]->t != b->t)
+    return bfail(b, LBM_EINVAL, "box %d is at step %lld, the batch at %lld", index, (long long)b->h[index]->t,
+                 (long long)b->t);
+  if (b->active[index] != a) {
+    b->active[index] = a;
+    b->dirty = 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_use_graph(lbm_batch* b, int enable) {
+  if (!b) return LBM_EINVAL;
+  b->use_graph = enable ? 1 : 0;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+  if (!b) return LBM_EINVAL;
+  if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps < 0");
+  if (active_count(b) == 0 || nsteps == 0) return LBM_OK;
+  int rc;
+  if ((rc = enter(b))) return rc;
+  if ((rc = upload(b))) return rc;
+  int64_t left = nsteps;
+  // single steps until the step counter reaches a relabel boundary
+  while (left > 0 && (!b->use_graph || b->t % b->K != 0 || left < b->K)) {
+    if ((rc = enqueue_step(b, b->par, b->masked && b->t % b->K == 0))) return rc;
+    advance(b, 1);
+    --left;
+  }
+  while (left >= b->K) {
+    const int p = b->par;
+    if (!b->graph[p] && (rc = build_graph(b, p))) return rc;
+    BCUDA(b, cudaGraphLaunch(b->graph[p], b->stream));
+    b->launches += b->K + (b->masked ? 7LL * active_count(b) : 0);
+    advance(b, b->K);
+    left -= b->K;
+  }
+  while (left > 0) {
+    if ((rc = enqueue_step(b, b->par, b->masked && b->t % b->K == 0))) return rc;
+    advance(b, 1);
+    --left;
+  }
+  return leave(b);
+}
+
+int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, float* best_ms_per_step) {
+  if (!b) return LBM_EINVAL;
+  if (trial_steps < 1) return bfail(b, LBM_EINVAL, "trial_steps must be >= 1");
+  if (active_count(b) == 0) return bfail(b, LBM_EINVAL, "no active box");
+  static const int strips[2] = {512, 256};
+  static const int rowsc[5] = {32, 64, 128, 256, 512};
+  const int use_graph = b->use_graph;
+  b->use_graph = 0;
+  cudaEvent_t e0, e1;
+  BCUDA(b, cudaEventCreate(&e0));
+  BCUDA(b, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bs = b->strip, br = b->rows, rc = LBM_OK;
+  for (int si = 0; si < 2 && rc == LBM_OK; ++si)
+    for (int ri = 0; ri < 5 && rc == LBM_OK; ++ri) {
+      if ((rc = lbm_batch_set_tiles(b, strips[si], rowsc[ri]))) break;
+      if ((rc = lbm_batch_step(b, 1))) break;  // upload + warm-up
+      cudaEventRecord(e0, b->stream);
+      if ((rc = lbm_batch_step(b, trial_steps))) break;
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = bfail(b, LBM_ECUDA, "event synchronize failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= trial_steps;
+      if (ms < best) {
+        best = ms;
+        bs = strips[si];
+        br = rowsc[ri];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->use_graph = use_graph;
+  if (rc) return rc;
+  if ((rc = lbm_batch_set_tiles(b, bs, br))) return rc;
+  if (best_ms_per_step) *best_ms_per_step = best;
+  return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch* b) {
+  if (!b) return LBM_EINVAL;
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->ext));
+  for (int i = 0; i < b->n; ++i) {
+    cudaStream_t hs = b->h[i]->stream;
+    b->h[i]->stream = b->stream;
+    const int rc = handle_check_flags(b->h[i]);
+    b->h[i]->stream = hs;
+    if (rc) return bfail(b, rc, "box %d: %s", i, b->h[i]->err);
+  }
+  return LBM_OK;
+}
+
+int64_t lbm_batch_steps_done(const lbm_batch* b) { return b ? b->t : -1; }
+
+int64_t lbm_batch_kernel_launches(const lbm_batch* b) { return b ? b->launches : -1; }
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : "batch is NULL"; }
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  cudaEventDestroy(b->ev_in);
+  cudaEventDestroy(b->ev_out);
+  cudaStreamDestroy(b->stream);
+  for (lbm_handle* h : b->h) h->in_batch = 0;
+  delete b;
+}
+
+}  // extern "C"

@@ -110,12 +110,35 @@ struct StepParams {
   float wref[Q];         // w_i * rho_ref (16-bit deviation base)
 };
 
+// One box of a batched launch (device array).
+struct BatchInst {
+  void* pops0;
+  void* pops1;
+  const uint8_t* mask;  // nullptr: plain Shan-Chen
+  int* flags;
+  int nx, ny;
+  float tau, inv_tau, G, rho0, inv_rho0, rho_ref;
+  int cur;              // buffer holding the state when parity == 0
+  int pad;
+};
+
+// One work item of a batched launch: columns x0 .. x0+width, rows y0 .. y1.
+struct BatchItem {
+  int inst, x0, width, y0, y1;
+};
+
 // Launch of the fused step (step.cu). Returns a cudaError_t.
 cudaError_t launch_step(int storage, const StepParams& p, cudaStream_t s);
 // Launch geometry the fused step uses for a box (for tests/benchmarks).
 void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk, int* block);
 // Whether the TMA-staged step kernel can run on a box of width nx.
 bool step_tma_allowed(int storage, int nx);
+// Batched fused step (two-cell staged march over a list of work items of
+// many boxes); resets *counter and launches one persistent grid.
+cudaError_t launch_step_batch(int storage, bool masked, bool tau_one, const BatchInst* insts, const BatchItem* items,
+                              int nitems, int* counter, int parity, cudaStream_t s);
+// CTAs of the batched kernel that fit the GPU at once.
+int batch_resident_ctas(int storage, bool masked, bool tau_one);
 // Whether the two-cell staged step kernel can run on a box of width nx.
 bool step_tma2_allowed(int storage, int nx);
 

@@ -480,7 +480,6 @@ struct TmaGeom2 {
   static constexpr int PAD = 16 / E;
   static constexpr int WIN = kBX2 + 2 * PAD;
   static constexpr int ROW_BYTES = WIN * E;
-  static constexpr int STAGE_BYTES_MASKED = Q * ROW_BYTES + kBX2;
 };
 
 // Two consecutive staged raw values (window positions pos, pos+1) as floats.
@@ -536,19 +535,42 @@ __device__ __forceinline__ void store_pair<LBM_BF16_DEV>(__nv_bfloat16* dst, siz
   *reinterpret_cast<__nv_bfloat162*>(dst + idx) = __halves2bfloat162(__float2bfloat16_rn(v.x), __float2bfloat16_rn(v.y));
 }
 
+// Copy len elements of a periodic row starting at column start (-nx <= start
+// < nx) into dst, wrapping as often as needed (len <= nx + 32: at most three
+// pieces). Every piece starts and ends on a 16-byte boundary when nx, start
+// and len are multiples of 16 bytes' worth of elements.
+template <typename T>
+__device__ __forceinline__ void copy_row_wrapped3(T* dst, const T* row, int start, int len, int nx, uint64_t* bar) {
+  const int s0 = start < 0 ? start + nx : start;
+  const int first = min(len, nx - s0);
+  bulk_g2s(dst, row + s0, (uint32_t)(first * sizeof(T)), bar);
+  if (first < len) {  // wrapped past the end of the row: restart at column 0
+    const int second = min(len - first, nx);
+    bulk_g2s(dst + first, row, (uint32_t)(second * sizeof(T)), bar);
+    if (first + second < len)  // a strip as wide as the box: its right halo wraps again
+      bulk_g2s(dst + first + second, row, (uint32_t)((len - first - second) * sizeof(T)), bar);
+  }
+}
+
+// One stage of the two-cell march: for output row r = y0 - 1 + k, plane i's
+// source row r - c_iy, columns x0 - PAD .. x0 + width + PAD (wrapped), and the
+// mask row r, columns x0 .. x0 + width. Slots have a fixed stride.
 template <int S, bool MASKED, int NSTAGE>
 __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename Store<S>::T* src,
-                                             unsigned char* stages, uint64_t* bars, int k, int y0, int x0, int lane) {
+                                             unsigned char* stages, uint64_t* bars, unsigned gk, int k, int y0,
+                                             int x0, int width, int lane) {
   using G = TmaGeom2<S>;
   using T = typename G::T;
-  constexpr uint32_t STAGE_BYTES = Q * G::ROW_BYTES + (MASKED ? kBX2 : 0);
-  const int slot = k % NSTAGE;
-  unsigned char* st = stages + (size_t)slot * STAGE_BYTES;
+  constexpr uint32_t SLOT_BYTES = Q * G::ROW_BYTES + (MASKED ? kBX2 : 0);
+  const int len = width + 2 * G::PAD;
+  const uint32_t bytes = (uint32_t)(Q * len * G::E + (MASKED ? width : 0));
+  const int slot = (int)(gk % NSTAGE);
+  unsigned char* st = stages + (size_t)slot * SLOT_BYTES;
   uint64_t* bar = bars + slot;
   const int r = y0 - 1 + k;
   const int ny = p.ny, nx = p.nx;
   if (lane < Q + (MASKED ? 1 : 0)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(bar, STAGE_BYTES);
+  if (lane == 0) mbar_expect_tx(bar, bytes);
   __syncwarp();
   if (lane < Q) {
     const int i = lane;
@@ -557,10 +579,10 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
     g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
     g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
     const T* row = src + (size_t)i * p.N + (size_t)g * nx;
-    copy_row_wrapped<T>(reinterpret_cast<T*>(st + i * G::ROW_BYTES), row, x0 - G::PAD, G::WIN, nx, bar);
+    copy_row_wrapped3<T>(reinterpret_cast<T*>(st + i * G::ROW_BYTES), row, x0 - G::PAD, len, nx, bar);
   } else if (MASKED && lane == Q) {
     const int g = r < 0 ? r + ny : (r >= ny ? r - ny : r);
-    copy_row_wrapped<uint8_t>(st + Q * G::ROW_BYTES, p.mask + (size_t)g * nx, x0, kBX2, nx, bar);
+    copy_row_wrapped3<uint8_t>(st + Q * G::ROW_BYTES, p.mask + (size_t)g * nx, x0, width, nx, bar);
   }
 }
 
@@ -569,58 +591,61 @@ constexpr size_t tma2_smem_bytes_c() {
   return (size_t)NSTAGE * (Q * TmaGeom2<S>::ROW_BYTES + (MASKED ? kBX2 : 0)) + 4 * (kBX2 + 4) * 4 + NSTAGE * 8 + 16;
 }
 
-template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
-__global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParams p) {
+template <int S, bool MASKED, int NSTAGE>
+struct Tma2Smem {
+  static constexpr int SLOT_BYTES = Q * TmaGeom2<S>::ROW_BYTES + (MASKED ? kBX2 : 0);
+  static constexpr int RW = kBX2 + 4;  // ring row: cell column c at index c + 2, halos at 1 and width + 2
+  unsigned char* stages;
+  float (*ring)[RW];
+  uint64_t* bars;
+  int* abort_flag;
+  __device__ __forceinline__ explicit Tma2Smem(unsigned char* smem) {
+    stages = smem;
+    ring = reinterpret_cast<float(*)[RW]>(smem + (size_t)NSTAGE * SLOT_BYTES);
+    bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * SLOT_BYTES + 4 * RW * 4);
+    abort_flag = reinterpret_cast<int*>(bars + NSTAGE);
+  }
+};
+
+// The two-cell march of one work item: columns x0 .. x0 + width (a multiple of
+// 16, at most kBX2) and rows y0 .. y1 of one box. `gstage` counts the stages
+// this CTA consumed before (mbarrier phases continue across items). Returns
+// false if a stage wait timed out (the CTA must then leave).
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE>
+__device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MASKED, NSTAGE>& sm, int x0, int width,
+                                       int y0, int y1, unsigned& gstage, int& bad) {
   using G = TmaGeom2<S>;
   using T = typename G::T;
-  using O = VOps<float2>;
-  constexpr int STAGE_BYTES = Q * G::ROW_BYTES + (MASKED ? kBX2 : 0);
-  constexpr int RW = kBX2 + 4;  // ring row: cell column c at index c + 2, halos at 1 and width + 2
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* stages = smem;
-  float(*ring)[RW] = reinterpret_cast<float(*)[RW]>(smem + (size_t)NSTAGE * STAGE_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE_BYTES + 4 * RW * 4);
-  int* abort_flag = reinterpret_cast<int*>(bars + NSTAGE);
-
+  constexpr int SLOT_BYTES = Tma2Smem<S, MASKED, NSTAGE>::SLOT_BYTES;
   const T* __restrict__ src = static_cast<const T*>(p.src);
   T* __restrict__ dst = static_cast<T*>(p.dst);
-  const int nx = p.nx, ny = p.ny;
+  const int nx = p.nx;
   const int tid = threadIdx.x;
   const bool helper = tid >= kBX;
   const int lane = tid & 31;
-  const int x0 = blockIdx.x * kBX2;
-  const int width = min(kBX2, nx - x0);  // a multiple of 16
   const bool active = !helper && 2 * tid < width;
-  const int y0 = blockIdx.y * p.rows_per_chunk;
-  const int y1 = min(y0 + p.rows_per_chunk, ny);
-  if (y0 >= y1) return;
-  const int nst = (y1 - y0) + 2;
+  const int nst = (y1 - y0) + 2;  // stages = rows y0-1 .. y1
+  const unsigned g0 = gstage;
 
-  if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(bars + s, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
   if (helper)
-    for (int k = 0; k < NSTAGE - 1 && k < nst; ++k) issue_stage2<S, MASKED, NSTAGE>(p, src, stages, bars, k, y0, x0, lane);
+    for (int k = 0; k < NSTAGE - 1 && k < nst; ++k)
+      issue_stage2<S, MASKED, NSTAGE>(p, src, sm.stages, sm.bars, g0 + k, k, y0, x0, width, lane);
 
   const int hplane = lane & 15;
   const bool hlane = helper && hplane < Q;
   const int hcx = (hplane == 1 || hplane == 5 || hplane == 8) ? 1 : ((hplane == 3 || hplane == 6 || hplane == 7) ? -1 : 0);
   const int hpos = (lane < 16 ? G::PAD - 1 : G::PAD + width) - hcx;
 
-  const int jc = 2 * tid + 2;      // ring index of the first cell of the pair
+  const int jc = 2 * tid + 2;        // ring index of the first cell of the pair
   const int pos = G::PAD + 2 * tid;  // window position of the first cell
   float2 fprev[Q];
   float2 rho_prev = make_float2(1.f, 1.f), jx_prev = make_float2(0.f, 0.f), jy_prev = make_float2(0.f, 0.f);
   unsigned m_prev = 0;
-  int bad = 0;
-  int k_abort = 0;
+  int k_abort = -1;
   for (int k = 0; k < nst; ++k) {
-    const int slot = k % NSTAGE;
-    const unsigned char* st = stages + (size_t)slot * STAGE_BYTES;
-    if (!mbar_wait(bars + slot, (uint32_t)((k / NSTAGE) & 1))) *abort_flag = 1;
+    const unsigned gk = g0 + k;
+    const unsigned char* st = sm.stages + (size_t)(gk % NSTAGE) * SLOT_BYTES;
+    if (!mbar_wait(sm.bars + gk % NSTAGE, (gk / NSTAGE) & 1u)) *sm.abort_flag = 1;
     float2 f[Q];
     float2 rho = make_float2(1.f, 1.f), jx = make_float2(0.f, 0.f), jy = make_float2(0.f, 0.f);
     unsigned m = 0;
@@ -628,7 +653,7 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
 #pragma unroll
       for (int i = 0; i < Q; ++i) f[i] = load_pair<S>(st + i * G::ROW_BYTES, pos - cx(i), cx(i));
       moments9(f, rho, jx, jy);
-      *reinterpret_cast<float2*>(&ring[k & 3][jc]) = psi_of(full_rho<S != LBM_F32>(rho, p), p);
+      *reinterpret_cast<float2*>(&sm.ring[k & 3][jc]) = psi_of(full_rho<S != LBM_F32>(rho, p), p);
       if (MASKED) m = *reinterpret_cast<const uint16_t*>(st + Q * G::ROW_BYTES + 2 * tid);
     } else if (helper) {
       const float v = hlane ? Store<S>::raw_smem(reinterpret_cast<const T*>(st + hplane * G::ROW_BYTES), hpos) : 0.f;
@@ -636,23 +661,24 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
       const float t2 = __fadd_rn(t1, __shfl_xor_sync(0xffffffffu, t1, 2));
       const float t3 = __fadd_rn(t2, __shfl_xor_sync(0xffffffffu, t2, 4));
       const float rh = full_rho<S != LBM_F32>(__fadd_rn(t3, __shfl_xor_sync(0xffffffffu, t2, 8)), p);
-      if (lane == 0) ring[k & 3][1] = psi_of(rh, p);
-      if (lane == 16) ring[k & 3][width + 2] = psi_of(rh, p);
+      if (lane == 0) sm.ring[k & 3][1] = psi_of(rh, p);
+      if (lane == 16) sm.ring[k & 3][width + 2] = psi_of(rh, p);
     }
     __syncthreads();
-    if (*abort_flag) {
+    if (*sm.abort_flag) {
       k_abort = k;
       break;
     }
     if (helper) {
-      if (k + NSTAGE - 1 < nst) issue_stage2<S, MASKED, NSTAGE>(p, src, stages, bars, k + NSTAGE - 1, y0, x0, lane);
+      if (k + NSTAGE - 1 < nst)
+        issue_stage2<S, MASKED, NSTAGE>(p, src, sm.stages, sm.bars, gk + NSTAGE - 1, k + NSTAGE - 1, y0, x0, width, lane);
     } else if (k >= 2 && active) {
       const int rc = y0 + k - 2;
       const int srow[3] = {(k - 2) & 3, (k - 1) & 3, k & 3};  // rows rc-1, rc, rc+1
       float2 nb[3][3];  // [row][left, centre, right] for the pair
 #pragma unroll
       for (int r3 = 0; r3 < 3; ++r3) {
-        const float* rr = ring[srow[r3]];
+        const float* rr = sm.ring[srow[r3]];
         const float2 c2 = *reinterpret_cast<const float2*>(rr + jc);
         nb[r3][0] = make_float2(rr[jc - 1], c2.x);
         nb[r3][1] = c2;
@@ -684,16 +710,87 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
     jy_prev = jy;
     m_prev = m;
   }
-  if (*abort_flag) {
+  if (k_abort >= 0) {
+    // a stage never completed: record it, then wait (bounded) for the copies
+    // of every stage issued and not consumed before the CTA leaves
     if (tid == 0) {
       atomicOr(p.flags + FLAG_TIMEOUT, 1);
       const int issued = min(nst, k_abort + NSTAGE - 1);
-      for (int q = k_abort; q < issued; ++q) mbar_wait(bars + q % NSTAGE, (uint32_t)((q / NSTAGE) & 1), 500000000ull);
+      for (int q = k_abort; q < issued; ++q)
+        mbar_wait(sm.bars + (g0 + q) % NSTAGE, ((g0 + q) / NSTAGE) & 1u, 500000000ull);
     }
     __syncthreads();
-    return;
+    return false;
   }
+  gstage = g0 + nst;
+  return true;
+}
+
+template <int S, bool MASKED, int NSTAGE>
+__device__ __forceinline__ void march2_init(const Tma2Smem<S, MASKED, NSTAGE>& sm) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(sm.bars + s, 1);
+    *sm.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// One box, one work item per CTA: strip blockIdx.x (kBX2 columns), row chunk blockIdx.y.
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Tma2Smem<S, MASKED, NSTAGE> sm(smem);
+  const int x0 = blockIdx.x * kBX2;
+  const int y0 = blockIdx.y * p.rows_per_chunk;
+  const int y1 = min(y0 + p.rows_per_chunk, p.ny);
+  if (y0 >= y1) return;
+  march2_init(sm);
+  unsigned gstage = 0;
+  int bad = 0;
+  if (!march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, x0, min(kBX2, p.nx - x0), y0, y1, gstage, bad)) return;
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
+}
+
+// Many boxes in one launch: persistent CTAs take work items (box, strip,
+// row chunk) from a device counter until the list is exhausted. Each box
+// reads buffer `cur ^ parity` and writes the other.
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kTmaThreads, MINB)
+    k_step_batch(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
+                 int* __restrict__ counter, int parity) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int item_sh;
+  const Tma2Smem<S, MASKED, NSTAGE> sm(smem);
+  march2_init(sm);
+  unsigned gstage = 0;
+  for (int guard = 0; guard < nitems + 1; ++guard) {
+    __syncthreads();  // the previous item's ring and item index are no longer read
+    if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = item_sh;
+    if (w >= nitems) break;
+    const BatchItem it = items[w];
+    const BatchInst& in = insts[it.inst];
+    StepParams p{};
+    const int c = in.cur ^ parity;
+    p.src = c ? in.pops1 : in.pops0;
+    p.dst = c ? in.pops0 : in.pops1;
+    p.mask = in.mask;
+    p.flags = in.flags;
+    p.nx = in.nx;
+    p.ny = in.ny;
+    p.N = (long long)in.nx * in.ny;
+    p.tau = in.tau;
+    p.inv_tau = in.inv_tau;
+    p.G = in.G;
+    p.rho0 = in.rho0;
+    p.inv_rho0 = in.inv_rho0;
+    p.rho_ref = in.rho_ref;
+    int bad = 0;
+    if (!march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, it.x0, it.width, it.y0, it.y1, gstage, bad)) return;
+    if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
+  }
 }
 
 // Stage ring depth and CTAs per SM, from measured sweeps at 8192^2: with
@@ -759,7 +856,7 @@ constexpr int kTma2MinBlocks = 4;
 
 template <int S>
 bool tma2_ok(int nx) {
-  return nx % 16 == 0 && nx >= TmaGeom2<S>::WIN;
+  return nx % 16 == 0;
 }
 
 template <int S, bool MASKED, bool TAU_ONE>
@@ -833,6 +930,75 @@ void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk
   *grid_y = gy;
   *rows_per_chunk = rows;
   *block = kBX;
+}
+
+// ---------------------------------------------------------------- batched launch
+namespace {
+
+template <int S, bool MASKED, bool TAU_ONE>
+struct BatchKernel {
+  static constexpr int NS = tma2_stages<S>();
+  static constexpr int MINB = TAU_ONE ? kTma2MinBlocks : 2;
+  static constexpr size_t SMEM = tma2_smem_bytes_c<S, MASKED, NS>();
+  static int resident() {  // CTAs that fit the GPU at once
+    static int r = 0;
+    if (r == 0) {
+      auto kern = k_step_batch<S, MASKED, TAU_ONE, NS, MINB>;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM) != cudaSuccess) return 0;
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTmaThreads, SMEM) != cudaSuccess) return 0;
+      r = (occ > 0 ? occ : 1) * sm_count();
+    }
+    return r;
+  }
+  static cudaError_t launch(const BatchInst* insts, const BatchItem* items, int nitems, int* counter, int parity,
+                            cudaStream_t s) {
+    const int res = resident();
+    if (res == 0) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int grid = nitems < res ? nitems : res;
+    if (grid <= 0) return cudaSuccess;
+    k_step_batch<S, MASKED, TAU_ONE, NS, MINB><<<grid, kTmaThreads, SMEM, s>>>(insts, items, nitems, counter, parity);
+    return cudaGetLastError();
+  }
+};
+
+template <int S>
+cudaError_t launch_batch_s(bool masked, bool tau_one, const BatchInst* insts, const BatchItem* items, int nitems,
+                           int* counter, int parity, cudaStream_t s) {
+  if (masked)
+    return tau_one ? BatchKernel<S, true, true>::launch(insts, items, nitems, counter, parity, s)
+                   : BatchKernel<S, true, false>::launch(insts, items, nitems, counter, parity, s);
+  return tau_one ? BatchKernel<S, false, true>::launch(insts, items, nitems, counter, parity, s)
+                 : BatchKernel<S, false, false>::launch(insts, items, nitems, counter, parity, s);
+}
+
+template <int S>
+int batch_resident_s(bool masked, bool tau_one) {
+  if (masked) return tau_one ? BatchKernel<S, true, true>::resident() : BatchKernel<S, true, false>::resident();
+  return tau_one ? BatchKernel<S, false, true>::resident() : BatchKernel<S, false, false>::resident();
+}
+
+}  // namespace
+
+cudaError_t launch_step_batch(int storage, bool masked, bool tau_one, const BatchInst* insts, const BatchItem* items,
+                              int nitems, int* counter, int parity, cudaStream_t s) {
+  switch (storage) {
+    case LBM_F32: return launch_batch_s<LBM_F32>(masked, tau_one, insts, items, nitems, counter, parity, s);
+    case LBM_F16_DEV: return launch_batch_s<LBM_F16_DEV>(masked, tau_one, insts, items, nitems, counter, parity, s);
+    case LBM_BF16_DEV: return launch_batch_s<LBM_BF16_DEV>(masked, tau_one, insts, items, nitems, counter, parity, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int batch_resident_ctas(int storage, bool masked, bool tau_one) {
+  switch (storage) {
+    case LBM_F32: return batch_resident_s<LBM_F32>(masked, tau_one);
+    case LBM_F16_DEV: return batch_resident_s<LBM_F16_DEV>(masked, tau_one);
+    case LBM_BF16_DEV: return batch_resident_s<LBM_BF16_DEV>(masked, tau_one);
+    default: return 0;
+  }
 }
 
 bool step_tma_allowed(int storage, int nx) {

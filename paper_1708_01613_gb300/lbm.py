@@ -77,6 +77,19 @@ SIGNATURES = {
     "lbm_destroy": (None, [_vp]),
     "lbm_mass_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _vp, _vp,
                                    C.c_char_p, C.c_size_t]),
+    "lbm_batch_workspace_bytes": (C.c_size_t, [_vp, C.c_int32]),
+    "lbm_batch_create": (C.c_int, [_vp, C.c_int32, _vp, C.c_size_t, C.POINTER(_vp)]),
+    "lbm_batch_set_tiles": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "lbm_batch_get_tiles": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_batch_tune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_float)]),
+    "lbm_batch_use_graph": (C.c_int, [_vp, C.c_int]),
+    "lbm_batch_set_active": (C.c_int, [_vp, C.c_int32, C.c_int]),
+    "lbm_batch_step": (C.c_int, [_vp, C.c_int64]),
+    "lbm_batch_sync": (C.c_int, [_vp]),
+    "lbm_batch_steps_done": (C.c_int64, [_vp]),
+    "lbm_batch_kernel_launches": (C.c_int64, [_vp]),
+    "lbm_batch_last_error": (C.c_char_p, [_vp]),
+    "lbm_batch_destroy": (None, [_vp]),
 }
 
 _lib = None
@@ -280,3 +293,86 @@ class Simulation:
 
     def sync(self) -> None:
         self._call("lbm_sync")
+
+
+class Batch:
+    """Several Simulation boxes advanced together (lbm_batch_*).
+
+    Every step is one persistent launch over all active boxes; blocks of a
+    relabel period are replayed as CUDA graphs. Boxes evolve bitwise as they
+    would alone. The workspace is a torch uint8 tensor owned by this object.
+    """
+
+    def __init__(self, sims):
+        import torch
+
+        self.sims = list(sims)
+        lib = load_library()
+        arr = (C.c_void_p * len(self.sims))(*[s.handle.value for s in self.sims])
+        self._arr = arr
+        nbytes = int(lib.lbm_batch_workspace_bytes(arr, len(self.sims)))
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "invalid batch")
+        dev = self.sims[0].device
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = C.c_void_p()
+        with torch.cuda.device(dev):
+            _check(lib.lbm_batch_create(arr, len(self.sims), C.c_void_p(ptr), nbytes, C.byref(h)))
+        self.handle = h
+        self.device = dev
+
+    def _call(self, name, *args):
+        import torch
+
+        lib = load_library()
+        with torch.cuda.device(self.device):
+            code = getattr(lib, name)(self.handle, *args)
+        if code != LBM_OK:
+            m = lib.lbm_batch_last_error(self.handle)
+            raise LbmError(code, m.decode() if m else "")
+
+    def set_tiles(self, strip_width: int, chunk_rows: int) -> None:
+        self._call("lbm_batch_set_tiles", int(strip_width), int(chunk_rows))
+
+    @property
+    def tiles(self):
+        a, b = C.c_int32(), C.c_int32()
+        load_library().lbm_batch_get_tiles(self.handle, C.byref(a), C.byref(b))
+        return int(a.value), int(b.value)
+
+    def tune(self, trial_steps: int = 3) -> float:
+        ms = C.c_float(0.0)
+        self._call("lbm_batch_tune", int(trial_steps), C.byref(ms))
+        return float(ms.value)
+
+    def use_graph(self, enable: bool) -> None:
+        self._call("lbm_batch_use_graph", int(bool(enable)))
+
+    def set_active(self, index: int, active: bool) -> None:
+        self._call("lbm_batch_set_active", int(index), int(bool(active)))
+
+    def step(self, n: int = 1) -> None:
+        self._call("lbm_batch_step", C.c_int64(int(n)))
+
+    def sync(self) -> None:
+        self._call("lbm_batch_sync")
+
+    @property
+    def steps_done(self) -> int:
+        return int(load_library().lbm_batch_steps_done(self.handle))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(load_library().lbm_batch_kernel_launches(self.handle))
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            load_library().lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,91 @@
+"""Batched stepping (lbm_batch_*): many boxes of uneven size in one persistent
+launch per step, relabel periods replayed as CUDA graphs. Each box must end
+bitwise where it ends when stepped alone."""
+import numpy as np
+import pytest
+
+import inputs
+from paper_1708_01613_gb300 import Batch, LbmError, Simulation, make_config
+
+pytestmark = pytest.mark.gpu
+
+RL, RG = inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55
+SIZES = [(256, 256), (320, 192), (528, 64), (1024, 96), (80, 48)]
+
+
+def make_box(nx, ny, storage, barrier, K, seed):
+    bub = inputs.poisson_disk_bubbles(nx, ny, 3, 6.0, min(14.0, 0.2 * min(nx, ny)), 2.0, seed=seed)
+    sim = Simulation(make_config(nx, ny, storage=storage, barrier=barrier, relabel_every=K, rho_ref=RL))
+    sim.init_bubbles(bub, RL, RG, 4.0)
+    return sim
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_matches_boxes_alone_bitwise(storage, graph):
+    K, steps = 3, 11
+    alone = [make_box(nx, ny, storage, True, K, 100 + i) for i, (nx, ny) in enumerate(SIZES)]
+    for s in alone:
+        s.step(steps)
+    boxes = [make_box(nx, ny, storage, True, K, 100 + i) for i, (nx, ny) in enumerate(SIZES)]
+    b = Batch(boxes)
+    b.use_graph(graph)
+    b.step(4)
+    b.step(steps - 4)
+    b.sync()
+    assert b.steps_done == steps and b.kernel_launches > 0
+    b.close()
+    for s, a in zip(boxes, alone):
+        assert s.steps_done == steps
+        got = s.read("pops", "mask")
+        ref = a.read("pops", "mask")
+        assert np.array_equal(got["pops"], ref["pops"]), (s.nx, s.ny)
+        assert np.array_equal(got["mask"], ref["mask"])
+
+
+def test_batch_tiles_tune_and_activity():
+    storage = "f16"
+    boxes = [make_box(nx, ny, storage, True, 2, 200 + i) for i, (nx, ny) in enumerate(SIZES)]
+    ref = [make_box(nx, ny, storage, True, 2, 200 + i) for i, (nx, ny) in enumerate(SIZES)]
+    b = Batch(boxes)
+    ms = b.tune(trial_steps=1)
+    strip, rows = b.tiles
+    assert ms > 0 and strip in (256, 512) and rows % 8 == 0
+    tuned = b.steps_done
+    assert tuned == 20  # ten candidates x (1 + 1) steps
+    for s in ref:
+        s.step(tuned)
+    # box 1 sits out 5 steps; the others advance
+    b.set_active(1, False)
+    b.step(5)
+    b.sync()
+    for i, (s, r) in enumerate(zip(boxes, ref)):
+        if i != 1:
+            r.step(5)
+    for s, r in zip(boxes, ref):
+        assert np.array_equal(s.read("pops")["pops"], r.read("pops")["pops"])
+    with pytest.raises(LbmError):
+        b.set_active(1, True)  # box 1 is 5 steps behind
+    for strip, rows in ((256, 16), (512, 40)):
+        b.set_tiles(strip, rows)
+        b.step(2)
+    with pytest.raises(LbmError):
+        b.set_tiles(384, 16)
+    b.close()
+
+
+def test_batch_rules():
+    a = make_box(256, 64, "f32", True, 1, 1)
+    c = make_box(256, 64, "f16", True, 1, 2)
+    with pytest.raises(LbmError):
+        Batch([a, c])  # mixed storage
+    d = Simulation(make_config(100, 64))
+    d.init_density(np.full((64, 100), 0.7))
+    with pytest.raises(LbmError) as e:
+        Batch([d])  # rows not 16-byte aligned
+    assert e.value.code == 6
+    b = Batch([a])
+    with pytest.raises(LbmError):
+        a.step(1)  # a batched box is stepped through its batch
+    b.close()
+    a.step(1)

@@ -329,8 +329,10 @@ def test_step_variant_selection_errors():
     with pytest.raises(LbmError) as e:
         sim.set_step_variant(2)  # 128 columns is too narrow for the staged kernel
     assert e.value.code == 6
+    sim.set_step_variant(3)  # the two-cell kernel takes any width that is a multiple of 16
+    odd = gpu_sim(100, 64, inputs.noise_density(100, 64, seed=1))
     with pytest.raises(LbmError) as e:
-        sim.set_step_variant(3)
+        odd.set_step_variant(3)
     assert e.value.code == 6
     with pytest.raises(LbmError):
         sim.set_step_variant(4)
