@@ -197,8 +197,8 @@ void lbm_destroy(lbm_handle* h);
  * when stepped alone with lbm_step.
  *
  * Rules: all boxes share storage, barrier setting and relabel period, are
- * on one device, are at the same step count, have nx % 16 == 0, and do not
- * stop on rupture. The batch works on a stream of its own (created by
+ * on one device, have nx % 16 == 0, and do not stop on rupture. Boxes may be
+ * at different step counts (each relabels when its own count is due). The batch works on a stream of its own (created by
  * lbm_batch_create; the legacy default stream cannot be captured into a
  * graph), ordered by events after earlier work on the first box's stream,
  * and later work on that stream is ordered after each lbm_batch_step. A box
@@ -228,8 +228,7 @@ int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, float* best_ms_per_step);
  * step by step. Results are identical. */
 int lbm_batch_use_graph(lbm_batch* b, int enable);
 
-/* Excludes (0) or re-includes (1) box `index`; a box re-included must be at
- * the batch's step count. */
+/* Excludes (0) or re-includes (1) box `index` from the steps that follow. */
 int lbm_batch_set_active(lbm_batch* b, int32_t index, int active);
 
 /* Enqueues nsteps steps of every active box (asynchronous). */

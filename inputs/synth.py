@@ -186,9 +186,13 @@ def serving_requests(count: int = 2000, rate_per_s: float = 10.0, side_lo: int =
 
 
 def request_bubbles(req: dict) -> np.ndarray:
-    """Bubble list of one serving request (Poisson-disk, log-uniform radii)."""
+    """Bubble list of one serving request (Poisson-disk, log-uniform radii).
+
+    The requested count is capped so that bubbles of the smallest radius (4)
+    cover at most a fifth of the box; dart throwing then always succeeds."""
     side = req["nx"]
-    nb = req["n_bubbles"]
+    cap = max(1, int(0.2 * req["nx"] * req["ny"] / (math.pi * 5.0**2)))
+    nb = min(req["n_bubbles"], cap)
     rmax = max(4.0, min(48.0, 0.33 * side / math.sqrt(max(nb, 1))))
     rmin = min(4.0, rmax)
     return poisson_disk_bubbles(req["nx"], req["ny"], nb, rmin, rmax, 2.0, req["seed"])

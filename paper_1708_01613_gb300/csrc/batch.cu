@@ -107,7 +107,8 @@ void build_items(lbm_batch* b) {
   b->nitems = (int)b->items.size();
 }
 
-// Re-uploads descriptors and items (host-synchronous copies).
+// Re-uploads descriptors and items (host-synchronous copies). Boxes may be
+// at different step counts: each relabels on its own phase.
 int upload(lbm_batch* b) {
   if (!b->dirty) return LBM_OK;
   std::vector<BatchInst> insts(b->n);
@@ -154,13 +155,15 @@ void advance(lbm_batch* b, int64_t n) {
     }
 }
 
-// Enqueues one step (relabels when due, then the batched kernel).
-int enqueue_step(lbm_batch* b, int parity, bool relabel_now) {
+// Enqueues one step `j` steps after the boxes' current state (relabel of
+// every box whose own step count is then due, then the batched kernel).
+int enqueue_step(lbm_batch* b, int parity, int64_t j) {
   int rc;
-  if (b->masked && relabel_now)
+  if (b->masked)
     for (int i = 0; i < b->n; ++i) {
       if (!b->active[i]) continue;
       lbm_handle* h = b->h[i];
+      if ((h->t + j) % h->cfg.relabel_every != 0) continue;
       const int saved = h->cur;
       h->cur = b->base_cur[i] ^ parity;
       cudaStream_t hs = h->stream;
@@ -182,7 +185,7 @@ int build_graph(lbm_batch* b, int start_parity) {
   BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   const int64_t saved = b->launches;
   int rc = LBM_OK;
-  for (int j = 0; j < b->K && rc == LBM_OK; ++j) rc = enqueue_step(b, start_parity ^ (j & 1), b->masked && j == 0);
+  for (int j = 0; j < b->K && rc == LBM_OK; ++j) rc = enqueue_step(b, start_parity ^ (j & 1), j);
   const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   b->launches = saved;  // counted again at every replay
   if (rc) {
@@ -243,7 +246,7 @@ int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, s
     if (h->cfg.storage != h0->cfg.storage || h->cfg.barrier != h0->cfg.barrier) return LBM_EINVAL;
     if (h->cfg.barrier && h->cfg.relabel_every != h0->cfg.relabel_every) return LBM_EINVAL;
     if (h->cfg.stop_on_first_rupture) return LBM_ENOTSUP;
-    if (h->t != h0->t || h->device != h0->device || h->halted) return LBM_EINVAL;
+    if (h->device != h0->device || h->halted) return LBM_EINVAL;
     if (h->cfg.nx % 16 != 0) return LBM_ENOTSUP;  // bulk copies need 16-byte rows
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();
@@ -310,9 +313,6 @@ int lbm_batch_set_active(lbm_batch* b, int32_t index, int active) {
   if (!b) return LBM_EINVAL;
   if (index < 0 || index >= b->n) return bfail(b, LBM_EINVAL, "index out of range");
   const int a = active ? 1 : 0;
-  if (a && !b->active[index] && b->h[index]->t != b->t)
-    return bfail(b, LBM_EINVAL, "box %d is at step %lld, the batch at %lld", index, (long long)b->h[index]->t,
-                 (long long)b->t);
   if (b->active[index] != a) {
     b->active[index] = a;
     b->dirty = 1;
@@ -334,22 +334,25 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   if ((rc = enter(b))) return rc;
   if ((rc = upload(b))) return rc;
   int64_t left = nsteps;
-  // single steps until the step counter reaches a relabel boundary
-  while (left > 0 && (!b->use_graph || b->t % b->K != 0 || left < b->K)) {
-    if ((rc = enqueue_step(b, b->par, b->masked && b->t % b->K == 0))) return rc;
+  // blocks start where the batch counter is a multiple of K; each box's
+  // relabel offset to that counter is fixed while the membership is, so a
+  // block's relabel schedule (captured in the graph) repeats; buffer parity
+  // repeats after 2K steps (two graphs)
+  while (left > 0 && b->use_graph && b->t % b->K != 0) {
+    if ((rc = enqueue_step(b, b->par, 0))) return rc;
     advance(b, 1);
     --left;
   }
-  while (left >= b->K) {
+  while (b->use_graph && left >= b->K) {
     const int p = b->par;
     if (!b->graph[p] && (rc = build_graph(b, p))) return rc;
     BCUDA(b, cudaGraphLaunch(b->graph[p], b->stream));
-    b->launches += b->K + (b->masked ? 7LL * active_count(b) : 0);
+    b->launches += b->K + (b->masked ? 7LL * active_count(b) * b->K / b->h[0]->cfg.relabel_every : 0);
     advance(b, b->K);
     left -= b->K;
   }
   while (left > 0) {
-    if ((rc = enqueue_step(b, b->par, b->masked && b->t % b->K == 0))) return rc;
+    if ((rc = enqueue_step(b, b->par, 0))) return rc;
     advance(b, 1);
     --left;
   }

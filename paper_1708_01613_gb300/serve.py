@@ -1,0 +1,202 @@
+"""Continuous-batching server for foam simulations on one GPU.
+
+Requests (box size, bubbles, step count, storage) arrive over time. The
+server keeps every admitted box resident in HBM, admits waiting requests in
+arrival order as long as their workspace (lbm_workspace_bytes) fits the
+memory budget and a box slot is free, and advances all resident boxes
+together: one batch per storage type (each on its own stream, so the two
+overlap on the device), stepped in quanta of at most `quantum_steps` so that
+new arrivals join within a quantum. A box leaves as soon as its step count is
+reached; its result is read and its memory returned. Every box evolves
+bitwise as it would alone (batches keep the single-box arithmetic), so a
+result does not depend on what else was in the mix.
+
+`run_one_at_a_time` processes the same arrival stream with the plain method:
+one request at a time, in arrival order, each stepped alone.
+"""
+from __future__ import annotations
+
+import collections
+import statistics
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .lbm import Batch, Simulation, lbm_workspace_bytes, make_config
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    nx: int
+    ny: int
+    bubbles: np.ndarray          # (n, 3) cx, cy, r
+    steps: int
+    storage: str = "f16"         # "f32" | "f16" | "bf16"
+    rho_l: float = 2.306865
+    rho_g: float = 0.104158
+    barrier: bool = True
+    relabel_every: int = 10
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival_s: float
+    admit_s: float
+    done_s: float
+    steps: int
+    cells: int
+    mass: float
+    n_bubbles: int
+    gas_fraction: float
+    pops: np.ndarray | None = None
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.arrival_s
+
+
+def config_of(req: Request):
+    return make_config(req.nx, req.ny, storage=req.storage, barrier=req.barrier,
+                       relabel_every=req.relabel_every, rho_ref=req.rho_l)
+
+
+def footprint_bytes(req: Request) -> int:
+    """Device bytes a request holds while resident (its workspace)."""
+    return int(lbm_workspace_bytes(config_of(req)))
+
+
+def _make_box(req: Request, device) -> Simulation:
+    sim = Simulation(config_of(req), device=device)
+    sim.init_bubbles(req.bubbles, req.rho_l, req.rho_g, 4.0)
+    return sim
+
+
+def _finish(req: Request, sim: Simulation, t0: float, admit_s: float, keep_pops: bool) -> Result:
+    st = sim.stats()
+    pops = sim.read("pops")["pops"] if keep_pops else None
+    return Result(req.rid, req.arrival_s, admit_s, time.perf_counter() - t0, req.steps, req.nx * req.ny,
+                  st["mass"], st["n_bubbles"], st["gas_fraction"], pops)
+
+
+@dataclass
+class _Job:
+    req: Request
+    sim: Simulation
+    remaining: int
+    admit_s: float
+    nbytes: int
+
+
+@dataclass
+class FoamServer:
+    memory_budget_bytes: int
+    max_boxes: int = 64
+    quantum_steps: int = 200
+    device: str = "cuda"
+    keep_pops: bool = False
+    stats: dict = field(default_factory=dict)
+
+    def run(self, requests: list[Request]) -> list[Result]:
+        import torch
+
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
+        waiting: collections.deque[Request] = collections.deque()
+        active: dict[int, _Job] = {}
+        batches: dict[str, Batch] = {}
+        results: list[Result] = []
+        used = 0
+        peak_used = 0
+        rebuilds = 0
+        quanta = 0
+        t0 = time.perf_counter()
+        changed = False
+        while pending or waiting or active:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival_s <= now:
+                waiting.append(pending.popleft())
+            while waiting and len(active) < self.max_boxes:
+                r = waiting[0]
+                need = footprint_bytes(r)
+                if need > self.memory_budget_bytes:
+                    raise ValueError(f"request {r.rid} needs {need} bytes, more than the whole budget")
+                if used + need > self.memory_budget_bytes:
+                    break
+                waiting.popleft()
+                active[r.rid] = _Job(r, _make_box(r, self.device), r.steps, time.perf_counter() - t0, need)
+                used += need
+                peak_used = max(peak_used, used)
+                changed = True
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, pending[0].arrival_s - (time.perf_counter() - t0)))
+                continue
+            if changed:
+                for b in batches.values():
+                    b.close()
+                batches = {}
+                groups: dict[str, list[_Job]] = collections.defaultdict(list)
+                for j in active.values():
+                    groups[j.req.storage].append(j)
+                for storage, jobs in groups.items():
+                    batches[storage] = Batch([j.sim for j in jobs])
+                rebuilds += 1
+                changed = False
+            q = min(self.quantum_steps, min(j.remaining for j in active.values()))
+            for b in batches.values():
+                b.step(q)  # each batch on its own stream: the storage classes overlap
+            for b in batches.values():
+                b.sync()
+            quanta += 1
+            for j in active.values():
+                j.remaining -= q
+            for rid in [rid for rid, j in active.items() if j.remaining == 0]:
+                j = active.pop(rid)
+                for b in batches.values():
+                    b.close()
+                batches = {}
+                changed = True
+                results.append(_finish(j.req, j.sim, t0, j.admit_s, self.keep_pops))
+                used -= j.nbytes
+                del j
+                torch.cuda.empty_cache()
+        for b in batches.values():
+            b.close()
+        self.stats = {"makespan_s": time.perf_counter() - t0, "peak_bytes": peak_used,
+                      "batch_rebuilds": rebuilds, "quanta": quanta}
+        return results
+
+
+def run_one_at_a_time(requests: list[Request], device: str = "cuda", keep_pops: bool = False):
+    """The plain method: requests in arrival order, each stepped alone."""
+    import torch
+
+    results = []
+    t0 = time.perf_counter()
+    for r in sorted(requests, key=lambda r: r.arrival_s):
+        wait = r.arrival_s - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        admit = time.perf_counter() - t0
+        sim = _make_box(r, device)
+        sim.step(r.steps)
+        results.append(_finish(r, sim, t0, admit, keep_pops))
+        del sim
+        torch.cuda.empty_cache()
+    return results, time.perf_counter() - t0
+
+
+def summarize(results: list[Result], makespan_s: float) -> dict:
+    lat = sorted(r.latency_s for r in results)
+    updates = sum(r.cells * r.steps for r in results)
+
+    def pct(p):
+        k = min(len(lat) - 1, max(0, int(round(p / 100.0 * (len(lat) - 1)))))
+        return lat[k]
+
+    return {"requests": len(results), "p50_s": round(pct(50), 4), "p99_s": round(pct(99), 4),
+            "mean_s": round(statistics.mean(lat), 4), "makespan_s": round(makespan_s, 3),
+            "mlups": round(updates / makespan_s / 1e6, 1), "cell_updates": updates}

@@ -1,0 +1,45 @@
+"""Continuous-batching server: requests of mixed size and storage arrive over
+time, share the GPU in batches, and each result equals (bitwise) the result
+of running that request alone. Admission respects the memory budget."""
+import numpy as np
+import pytest
+
+import inputs
+from paper_1708_01613_gb300.serve import FoamServer, Request, footprint_bytes, run_one_at_a_time, summarize
+
+pytestmark = pytest.mark.gpu
+
+
+def requests():
+    spec = [(256, 256, "f16", 48, 0.000), (192, 128, "f32", 30, 0.002), (320, 64, "f16", 75, 0.004),
+            (512, 512, "f32", 40, 0.010), (128, 128, "f16", 61, 0.015), (256, 192, "f32", 22, 0.020)]
+    out = []
+    for i, (nx, ny, storage, steps, t) in enumerate(spec):
+        bub = inputs.poisson_disk_bubbles(nx, ny, 3, 5.0, 0.15 * min(nx, ny), 2.0, seed=500 + i)
+        out.append(Request(i, t, nx, ny, bub, steps, storage, inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, True, 4))
+    return out
+
+
+def test_served_results_equal_lone_runs_and_budget_holds():
+    reqs = requests()
+    # room for the two largest boxes at most: the rest queue behind them
+    budget = sorted(footprint_bytes(r) for r in reqs)[-1] + sorted(footprint_bytes(r) for r in reqs)[-2]
+    server = FoamServer(memory_budget_bytes=budget, max_boxes=4, quantum_steps=16, keep_pops=True)
+    served = {r.rid: r for r in server.run(reqs)}
+    assert sorted(served) == [r.rid for r in reqs]
+    assert server.stats["peak_bytes"] <= budget
+    assert server.stats["batch_rebuilds"] >= 3
+    alone, _ = run_one_at_a_time(reqs, keep_pops=True)
+    for a in alone:
+        s = served[a.rid]
+        assert np.array_equal(s.pops, a.pops), a.rid
+        assert s.mass == a.mass and s.n_bubbles == a.n_bubbles
+        assert s.latency_s >= 0 and s.done_s >= s.admit_s >= s.arrival_s - 1e-9
+    summ = summarize(list(served.values()), server.stats["makespan_s"])
+    assert summ["requests"] == 6 and summ["p99_s"] >= summ["p50_s"] > 0
+
+
+def test_request_larger_than_budget_is_refused():
+    r = requests()[3]
+    with pytest.raises(ValueError):
+        FoamServer(memory_budget_bytes=footprint_bytes(r) - 1).run([r])
