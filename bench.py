@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-step-scale", type=float, default=0.05)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
+    ap.add_argument("--serve-load", type=float, default=0.9,
+                    help="offered load as a fraction of the one-box-at-a-time throughput")
     ap.add_argument("--batch-step-scale", type=float, default=1.0)
     return ap.parse_args()
 
@@ -290,7 +292,7 @@ def run_gpu(args, world, rank, local):
     if not args.no_batch:
         out["batched"] = run_batched(args, dev, world, rank)
     if not args.no_serve:
-        cap = out.get("batched", {}).get("value", 60000.0) * 1e6
+        cap = out.get("batched", {}).get("sequential", 45000.0) * 1e6
         out["served"] = run_served(args, dev, world, rank, cap)
     return out
 
@@ -298,8 +300,9 @@ def run_gpu(args, world, rank, local):
 def run_served(args, dev, world, rank, capacity_ups):
     """Continuous-batching server on a Poisson request stream (sides 128-4096
     log-uniform, 2-300 bubbles, 1k-20k steps scaled by `serve_step_scale`,
-    half FP32 and half FP16 storage), offered load 0.7 of the batched
-    capacity measured above; against the same stream run one at a time."""
+    half FP32 and half FP16 storage), offered load `serve_load` of the
+    one-box-at-a-time throughput measured above; against the same stream run
+    one at a time."""
     import math
 
     import torch
@@ -311,7 +314,7 @@ def run_served(args, dev, world, rank, capacity_ups):
     scale = args.serve_step_scale
     raw = inputs.serving_requests(count=n, rate_per_s=1.0, seed=41 + 1000 * rank)
     work = [r["nx"] * r["ny"] * max(20, int(round(r["steps"] * scale))) for r in raw]
-    rate = 0.7 * capacity_ups / (sum(work) / len(work))
+    rate = args.serve_load * capacity_ups / (sum(work) / len(work))
     reqs = []
     for r in raw:
         bub = inputs.request_bubbles(r)
@@ -324,12 +327,14 @@ def run_served(args, dev, world, rank, capacity_ups):
     served = summarize(server.run(reqs), server.stats["makespan_s"])
     alone_res, alone_span = run_one_at_a_time(reqs, device=str(dev))
     alone = summarize(alone_res, alone_span)
-    return {"workload": f"{n} requests, Poisson arrivals at offered load 0.7 of the batched capacity, sides "
+    return {"workload": f"{n} requests, Poisson arrivals at offered load {args.serve_load} of the one-at-a-time "
+                        "throughput, sides "
                         "128-4096 log-uniform, 2-300 bubbles, 1k-20k steps x step_scale, FP32/FP16 50/50, "
                         "barrier on (K=10)",
             "step_scale": scale, "rate_per_s": round(rate, 3), "memory_budget_gb": args.serve_budget_gb,
             "p50_s": served["p50_s"], "p99_s": served["p99_s"], "mlups": served["mlups"],
             "makespan_s": served["makespan_s"], "batch_rebuilds": server.stats["batch_rebuilds"],
+            "server_s": {k: server.stats[k] for k in ("admit_s", "step_s", "finish_s")},
             "peak_resident_gb": round(server.stats["peak_bytes"] / 2**30, 2),
             "one_at_a_time": {"p50_s": alone["p50_s"], "p99_s": alone["p99_s"], "mlups": alone["mlups"],
                               "makespan_s": alone["makespan_s"]}}

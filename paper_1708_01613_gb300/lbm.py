@@ -332,6 +332,13 @@ class Batch:
             m = lib.lbm_batch_last_error(self.handle)
             raise LbmError(code, m.decode() if m else "")
 
+    @property
+    def period(self) -> int:
+        """Steps covered by one captured graph: the relabel period with the
+        barrier on, else 16."""
+        c = self.sims[0].cfg
+        return int(c.relabel_every) if c.barrier else 16
+
     def set_tiles(self, strip_width: int, chunk_rows: int) -> None:
         self._call("lbm_batch_set_tiles", int(strip_width), int(chunk_rows))
 

@@ -101,72 +101,92 @@ class FoamServer:
     stats: dict = field(default_factory=dict)
 
     def run(self, requests: list[Request]) -> list[Result]:
+        """Serves `requests` (arrival times relative to the call) to completion.
+
+        Membership changes cost a batch rebuild (descriptor upload and, for
+        long quanta, a graph capture), so they are batched too: a box that
+        finishes is only switched off in its batch and its memory is given
+        back at the next admission, which rebuilds the batches once for
+        every request admitted at that point."""
         import torch
 
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
         waiting: collections.deque[Request] = collections.deque()
         active: dict[int, _Job] = {}
-        batches: dict[str, Batch] = {}
+        parked: list[_Job] = []            # finished, still held by a batch
+        batches: dict[str, tuple[Batch, list[_Job]]] = {}
         results: list[Result] = []
-        used = 0
-        peak_used = 0
-        rebuilds = 0
-        quanta = 0
+        used = 0                           # bytes of boxes still stepping
+        peak_held = 0
+        rebuilds = quanta = 0
+        t_admit = t_step = t_finish = 0.0
         t0 = time.perf_counter()
-        changed = False
         while pending or waiting or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival_s <= now:
                 waiting.append(pending.popleft())
-            while waiting and len(active) < self.max_boxes:
-                r = waiting[0]
-                need = footprint_bytes(r)
+            admit: list[Request] = []
+            want = used
+            while waiting and len(active) + len(admit) < self.max_boxes:
+                need = footprint_bytes(waiting[0])
                 if need > self.memory_budget_bytes:
-                    raise ValueError(f"request {r.rid} needs {need} bytes, more than the whole budget")
-                if used + need > self.memory_budget_bytes:
+                    raise ValueError(f"request {waiting[0].rid} needs {need} bytes, more than the whole budget")
+                if want + need > self.memory_budget_bytes:
                     break
-                waiting.popleft()
-                active[r.rid] = _Job(r, _make_box(r, self.device), r.steps, time.perf_counter() - t0, need)
-                used += need
-                peak_used = max(peak_used, used)
-                changed = True
-            if not active:
-                if pending:
-                    time.sleep(max(0.0, pending[0].arrival_s - (time.perf_counter() - t0)))
-                continue
-            if changed:
-                for b in batches.values():
+                admit.append(waiting.popleft())
+                want += need
+            if admit:
+                ta = time.perf_counter()
+                for b, _ in batches.values():
                     b.close()
                 batches = {}
+                if parked:
+                    parked.clear()
+                    torch.cuda.empty_cache()
+                for r in admit:
+                    active[r.rid] = _Job(r, _make_box(r, self.device), r.steps, time.perf_counter() - t0,
+                                         footprint_bytes(r))
+                used = want
+                peak_held = max(peak_held, used)
                 groups: dict[str, list[_Job]] = collections.defaultdict(list)
                 for j in active.values():
                     groups[j.req.storage].append(j)
                 for storage, jobs in groups.items():
-                    batches[storage] = Batch([j.sim for j in jobs])
+                    batches[storage] = (Batch([j.sim for j in jobs]), jobs)
                 rebuilds += 1
-                changed = False
+                t_admit += time.perf_counter() - ta
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, pending[0].arrival_s - (time.perf_counter() - t0)))
+                continue
             q = min(self.quantum_steps, min(j.remaining for j in active.values()))
-            for b in batches.values():
+            ts = time.perf_counter()
+            live = [(b, jobs) for b, jobs in batches.values() if any(j.remaining > 0 for j in jobs)]
+            for b, _ in live:
+                b.use_graph(q >= 2 * b.period)
                 b.step(q)  # each batch on its own stream: the storage classes overlap
-            for b in batches.values():
+            for b, _ in live:
                 b.sync()
+            t_step += time.perf_counter() - ts
             quanta += 1
-            for j in active.values():
-                j.remaining -= q
-            for rid in [rid for rid, j in active.items() if j.remaining == 0]:
-                j = active.pop(rid)
-                for b in batches.values():
-                    b.close()
-                batches = {}
-                changed = True
-                results.append(_finish(j.req, j.sim, t0, j.admit_s, self.keep_pops))
-                used -= j.nbytes
-                del j
-                torch.cuda.empty_cache()
-        for b in batches.values():
+            tf = time.perf_counter()
+            for b, jobs in live:
+                for i, j in enumerate(jobs):
+                    if j.remaining <= 0:
+                        continue
+                    j.remaining -= q
+                    if j.remaining == 0:
+                        b.set_active(i, False)
+                        active.pop(j.req.rid)
+                        results.append(_finish(j.req, j.sim, t0, j.admit_s, self.keep_pops))
+                        used -= j.nbytes
+                        parked.append(j)
+            t_finish += time.perf_counter() - tf
+        for b, _ in batches.values():
             b.close()
-        self.stats = {"makespan_s": time.perf_counter() - t0, "peak_bytes": peak_used,
-                      "batch_rebuilds": rebuilds, "quanta": quanta}
+        self.stats = {"makespan_s": time.perf_counter() - t0, "peak_bytes": peak_held,
+                      "batch_rebuilds": rebuilds, "quanta": quanta, "admit_s": round(t_admit, 4),
+                      "step_s": round(t_step, 4), "finish_s": round(t_finish, 4)}
         return results
 
 

@@ -378,3 +378,25 @@ def test_barrier_state_clears_when_a_bubble_dissolves():
         assert np.array_equal(got["mask"], ref.mask), t
         assert rel_inf(got["pops"], ref.f) < 1e-4
     assert np.all(ref.owner == -1)  # everything dissolved by step 900
+
+
+@pytest.mark.parametrize("nx,ny,n", [(37, 5, 3), (300, 70, 40), (256, 256, 700), (1024, 64, 0)])
+def test_init_bubbles_matches_oracle(nx, ny, n):
+    """Initial density of a bubble set (each CTA takes the minimum only over
+    bubbles that come near its tile; more bubbles than one staged chunk;
+    centres outside the box; no bubbles) against the oracle's minimum over
+    all bubbles: FP32 populations within one rounding, exact where the tanh
+    profile saturates."""
+    u = inputs.splitmix64_uniform(7000 + n, np.arange(3 * n)).reshape(n, 3)
+    b = np.stack([u[:, 0] * (nx + 20) - 10, u[:, 1] * (ny + 20) - 10, 1.0 + 0.1 * min(nx, ny) * u[:, 2]], 1)
+    rho = O.init_bubbles(O.make_params(nx, ny), b, RL, RG, 4.0)
+    sim = gpu_sim(nx, ny, bubbles=b)
+    got = sim.read("pops")["pops"]
+    _, _, w = O.lattice()
+    want = (w[:, None, None] * rho[None]).astype(np.float32)
+    assert np.all(np.abs(got - want) <= np.spacing(want))
+    assert np.mean(got == want) > 0.999
+    sat = rho == 0.5 * (RL + RG) + 0.5 * (RL - RG)
+    assert np.array_equal(got[:, sat], want[:, sat])
+    if n == 0:
+        assert sat.all()
