@@ -61,8 +61,8 @@ def parse():
     ap.add_argument("--no-k1", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-step-scale", type=float, default=0.05)
+    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-step-scale", type=float, default=0.1)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     ap.add_argument("--serve-load", type=float, default=0.9,
                     help="offered load as a fraction of the one-box-at-a-time throughput")
@@ -322,8 +322,7 @@ def run_served(args, dev, world, rank, capacity_ups):
                             max(20, int(round(r["steps"] * scale))), r["storage"],
                             inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, True, 10))
     torch.cuda.synchronize(dev)
-    server = FoamServer(memory_budget_bytes=int(args.serve_budget_gb * 2**30), max_boxes=32,
-                        quantum_steps=max(10, int(200 * scale)), device=str(dev))
+    server = FoamServer(memory_budget_bytes=int(args.serve_budget_gb * 2**30), max_boxes=32, device=str(dev))
     served = summarize(server.run(reqs), server.stats["makespan_s"])
     alone_res, alone_span = run_one_at_a_time(reqs, device=str(dev))
     alone = summarize(alone_res, alone_span)
@@ -334,7 +333,7 @@ def run_served(args, dev, world, rank, capacity_ups):
             "step_scale": scale, "rate_per_s": round(rate, 3), "memory_budget_gb": args.serve_budget_gb,
             "p50_s": served["p50_s"], "p99_s": served["p99_s"], "mlups": served["mlups"],
             "makespan_s": served["makespan_s"], "batch_rebuilds": server.stats["batch_rebuilds"],
-            "server_s": {k: server.stats[k] for k in ("admit_s", "step_s", "finish_s")},
+            "server": {k: server.stats[k] for k in ("quanta", "admit_s", "step_s", "finish_s", "rate_mlups")},
             "peak_resident_gb": round(server.stats["peak_bytes"] / 2**30, 2),
             "one_at_a_time": {"p50_s": alone["p50_s"], "p99_s": alone["p99_s"], "mlups": alone["mlups"],
                               "makespan_s": alone["makespan_s"]}}

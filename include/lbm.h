@@ -234,6 +234,15 @@ int lbm_batch_set_active(lbm_batch* b, int32_t index, int active);
 /* Enqueues nsteps steps of every active box (asynchronous). */
 int lbm_batch_step(lbm_batch* b, int64_t nsteps);
 
+/* Multi-rate steps: box i advances nsteps[i] steps (n = the batch's box
+ * count; 0 = sits out; a switched-off box must get 0). Step j of the call is
+ * one persistent launch over the boxes with nsteps[i] > j, so small boxes
+ * can take many steps while large ones take few, as a server sharing the
+ * GPU between requests wants. Relabels follow each box's own count. No
+ * graphs are used; asynchronous, like lbm_batch_step. The batch's step
+ * counter advances by the largest nsteps[i]. */
+int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n);
+
 /* Synchronises the batch stream and reports device faults of any box. */
 int lbm_batch_sync(lbm_batch* b);
 

@@ -359,6 +359,74 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   return leave(b);
 }
 
+// Multi-rate steps: box i advances nsteps[i]. Boxes are laid out in the item
+// list in descending order of their step counts, so the boxes still stepping
+// at step j own a prefix of the items and step j is one launch over that
+// prefix. Every box stepping at j has done exactly j steps of the call, so
+// the common buffer parity j & 1 holds for all of them.
+int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n) {
+  if (!b) return LBM_EINVAL;
+  if (!nsteps || n != b->n) return bfail(b, LBM_EINVAL, "need one step count per box (%d)", b->n);
+  int64_t most = 0;
+  for (int i = 0; i < n; ++i) {
+    if (nsteps[i] < 0) return bfail(b, LBM_EINVAL, "box %d: nsteps < 0", i);
+    if (nsteps[i] > 0 && !b->active[i]) return bfail(b, LBM_EINVAL, "box %d is switched off", i);
+    most = std::max(most, nsteps[i]);
+  }
+  if (most == 0) return LBM_OK;
+  int rc;
+  if ((rc = enter(b))) return rc;
+  std::vector<int> order;
+  for (int i = 0; i < n; ++i)
+    if (nsteps[i] > 0) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return nsteps[a] > nsteps[c]; });
+  // item list in that order; prefix[k] = items of the first k boxes
+  std::vector<int> keep = b->active;
+  for (int i = 0; i < n; ++i) b->active[i] = nsteps[i] > 0;
+  b->dirty = 1;
+  rc = upload(b);  // items of the stepping boxes, current buffers
+  b->active = keep;
+  if (rc) return rc;
+  std::vector<BatchItem> sorted;
+  std::vector<int> prefix(order.size() + 1, 0);
+  for (size_t k = 0; k < order.size(); ++k) {
+    for (const BatchItem& it : b->items)
+      if (it.inst == order[k]) sorted.push_back(it);
+    prefix[k + 1] = (int)sorted.size();
+  }
+  BCUDA(b, cudaMemcpyAsync(b->d_items, sorted.data(), sizeof(BatchItem) * sorted.size(), cudaMemcpyHostToDevice,
+                           b->stream));
+  size_t live = order.size();
+  for (int64_t j = 0; j < most; ++j) {
+    while (live > 0 && nsteps[order[live - 1]] <= j) --live;
+    const int parity = (int)(j & 1);
+    if (b->masked)
+      for (size_t k = 0; k < live; ++k) {
+        lbm_handle* h = b->h[order[k]];
+        if ((h->t + j) % h->cfg.relabel_every != 0) continue;
+        const int saved = h->cur;
+        h->cur = b->base_cur[order[k]] ^ parity;
+        cudaStream_t hs = h->stream;
+        h->stream = b->stream;
+        rc = handle_relabel(h);
+        h->stream = hs;
+        h->cur = saved;
+        if (rc) return bfail(b, rc, "relabel of box %d: %s", order[k], h->err);
+        b->launches += 7;
+      }
+    BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items,
+                               prefix[live], b->d_counter, parity, b->stream));
+    b->launches += 1;
+  }
+  for (int i = 0; i < n; ++i) {
+    b->h[i]->t += nsteps[i];
+    b->h[i]->cur ^= (int)(nsteps[i] & 1);
+  }
+  b->t += most;
+  b->dirty = 1;  // the next lbm_batch_step re-uploads its own item list
+  return leave(b);
+}
+
 int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, float* best_ms_per_step) {
   if (!b) return LBM_EINVAL;
   if (trial_steps < 1) return bfail(b, LBM_EINVAL, "trial_steps must be >= 1");

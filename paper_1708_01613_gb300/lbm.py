@@ -85,6 +85,7 @@ SIGNATURES = {
     "lbm_batch_use_graph": (C.c_int, [_vp, C.c_int]),
     "lbm_batch_set_active": (C.c_int, [_vp, C.c_int32, C.c_int]),
     "lbm_batch_step": (C.c_int, [_vp, C.c_int64]),
+    "lbm_batch_step_each": (C.c_int, [_vp, _vp, C.c_int32]),
     "lbm_batch_sync": (C.c_int, [_vp]),
     "lbm_batch_steps_done": (C.c_int64, [_vp]),
     "lbm_batch_kernel_launches": (C.c_int64, [_vp]),
@@ -361,6 +362,13 @@ class Batch:
 
     def step(self, n: int = 1) -> None:
         self._call("lbm_batch_step", C.c_int64(int(n)))
+
+    def step_each(self, nsteps) -> None:
+        """Box i advances nsteps[i] steps (0 = sits out), asynchronously."""
+        a = np.ascontiguousarray(np.asarray(nsteps, dtype=np.int64))
+        if a.shape != (len(self.sims),):
+            raise LbmError(LBM_EINVAL, f"need {len(self.sims)} step counts")
+        self._call("lbm_batch_step_each", C.c_void_p(a.ctypes.data), len(self.sims))
 
     def sync(self) -> None:
         self._call("lbm_batch_sync")

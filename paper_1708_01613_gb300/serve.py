@@ -5,9 +5,10 @@ server keeps every admitted box resident in HBM, admits waiting requests in
 arrival order as long as their workspace (lbm_workspace_bytes) fits the
 memory budget and a box slot is free, and advances all resident boxes
 together: one batch per storage type (each on its own stream, so the two
-overlap on the device), stepped in quanta of at most `quantum_steps` so that
-new arrivals join within a quantum. A box leaves as soon as its step count is
-reached; its result is read and its memory returned. Every box evolves
+overlap on the device), in short quanta shared fairly by work, so that new
+arrivals join within a quantum and small requests overtake large ones. A box
+leaves at the end of the quantum in which its step count is reached; its
+result is read then and its memory returned at the next admission. Every box evolves
 bitwise as it would alone (batches keep the single-box arithmetic), so a
 result does not depend on what else was in the mix.
 
@@ -90,12 +91,40 @@ class _Job:
     admit_s: float
     nbytes: int
 
+    @property
+    def cells(self) -> int:
+        return self.req.nx * self.req.ny
+
+
+def fair_steps(jobs: list[_Job], budget_updates: float) -> dict[int, int]:
+    """Steps per job for one quantum: the cell-update budget is shared equally
+    among the jobs (processor sharing by work), a job needing less than its
+    share takes all its remaining steps and leaves the rest to the others
+    (water-filling), and every job advances at least one step."""
+    out: dict[int, int] = {}
+    left = float(budget_updates)
+    order = sorted(jobs, key=lambda j: j.remaining * j.cells)
+    for k, j in enumerate(order):
+        share = max(0.0, left) / (len(order) - k)
+        s = j.remaining if j.remaining * j.cells <= share else max(1, int(share // j.cells))
+        s = min(s, j.remaining)
+        out[j.req.rid] = s
+        left -= s * j.cells
+    return out
+
 
 @dataclass
 class FoamServer:
+    """Continuous batching: each quantum (about `quantum_s` of GPU time, from
+    a running estimate of the update rate, or exactly `quantum_updates` cell
+    updates when given) is split fairly between the resident boxes with
+    `fair_steps`, and every batch runs its share as multi-rate steps
+    (lbm_batch_step_each): small boxes take many cheap steps while large ones
+    take few, so a small request is not held to the pace of the largest box."""
     memory_budget_bytes: int
     max_boxes: int = 64
-    quantum_steps: int = 200
+    quantum_s: float = 0.02
+    quantum_updates: float | None = None
     device: str = "cuda"
     keep_pops: bool = False
     stats: dict = field(default_factory=dict)
@@ -103,11 +132,10 @@ class FoamServer:
     def run(self, requests: list[Request]) -> list[Result]:
         """Serves `requests` (arrival times relative to the call) to completion.
 
-        Membership changes cost a batch rebuild (descriptor upload and, for
-        long quanta, a graph capture), so they are batched too: a box that
-        finishes is only switched off in its batch and its memory is given
-        back at the next admission, which rebuilds the batches once for
-        every request admitted at that point."""
+        Membership changes cost a batch rebuild (descriptor upload), so they
+        are batched too: a box that finishes is only switched off in its
+        batch and its memory is given back at the next admission, which
+        rebuilds the batches once for every request admitted at that point."""
         import torch
 
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
@@ -119,6 +147,7 @@ class FoamServer:
         used = 0                           # bytes of boxes still stepping
         peak_held = 0
         rebuilds = quanta = 0
+        rate = 3e10                        # cell updates per second, refined as we go
         t_admit = t_step = t_finish = 0.0
         t0 = time.perf_counter()
         while pending or waiting or active:
@@ -159,22 +188,28 @@ class FoamServer:
                 if pending:
                     time.sleep(max(0.0, pending[0].arrival_s - (time.perf_counter() - t0)))
                 continue
-            q = min(self.quantum_steps, min(j.remaining for j in active.values()))
+            budget = self.quantum_updates if self.quantum_updates else rate * self.quantum_s
+            share = fair_steps(list(active.values()), budget)
             ts = time.perf_counter()
-            live = [(b, jobs) for b, jobs in batches.values() if any(j.remaining > 0 for j in jobs)]
-            for b, _ in live:
-                b.use_graph(q >= 2 * b.period)
-                b.step(q)  # each batch on its own stream: the storage classes overlap
-            for b, _ in live:
+            live = []
+            for b, jobs in batches.values():
+                plan = [share.get(j.req.rid, 0) if j.remaining > 0 else 0 for j in jobs]
+                if any(plan):
+                    b.step_each(plan)  # each batch on its own stream: the storage classes overlap
+                    live.append((b, jobs, plan))
+            for b, _, _ in live:
                 b.sync()
-            t_step += time.perf_counter() - ts
+            dt = time.perf_counter() - ts
+            t_step += dt
+            done = sum(share[r] * active[r].cells for r in share)
+            rate = 0.7 * rate + 0.3 * done / max(dt, 1e-6)
             quanta += 1
             tf = time.perf_counter()
-            for b, jobs in live:
-                for i, j in enumerate(jobs):
-                    if j.remaining <= 0:
+            for b, jobs, plan in live:
+                for i, (j, s) in enumerate(zip(jobs, plan)):
+                    if s == 0:
                         continue
-                    j.remaining -= q
+                    j.remaining -= s
                     if j.remaining == 0:
                         b.set_active(i, False)
                         active.pop(j.req.rid)
@@ -186,7 +221,8 @@ class FoamServer:
             b.close()
         self.stats = {"makespan_s": time.perf_counter() - t0, "peak_bytes": peak_held,
                       "batch_rebuilds": rebuilds, "quanta": quanta, "admit_s": round(t_admit, 4),
-                      "step_s": round(t_step, 4), "finish_s": round(t_finish, 4)}
+                      "step_s": round(t_step, 4), "finish_s": round(t_finish, 4),
+                      "rate_mlups": round(rate / 1e6, 1)}
         return results
 
 

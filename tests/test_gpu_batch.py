@@ -95,3 +95,30 @@ def test_batch_rules():
         a.step(1)  # a batched box is stepped through its batch
     b.close()
     a.step(1)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_step_each_multi_rate_bitwise(storage):
+    """Boxes advancing different step counts in one call (prefix launches,
+    per-box relabel phases), mixed with common steps and a switched-off box,
+    end bitwise where the lone runs end."""
+    K = 3
+    boxes = [make_box(nx, ny, storage, True, K, 300 + i) for i, (nx, ny) in enumerate(SIZES)]
+    ref = [make_box(nx, ny, storage, True, K, 300 + i) for i, (nx, ny) in enumerate(SIZES)]
+    b = Batch(boxes)
+    plan = [[7, 0, 3, 12, 1], [2, 5, 5, 0, 9]]
+    b.step_each(plan[0])
+    b.step(4)
+    b.set_active(3, False)
+    b.step_each(plan[1])
+    with pytest.raises(LbmError):
+        b.step_each([1, 1, 1, 1, 1])  # box 3 is switched off
+    b.sync()
+    total = [p0 + 4 + p1 for p0, p1 in zip(*plan)]
+    assert b.steps_done == 12 + 4 + 9
+    for s, r, n in zip(boxes, ref, total):
+        r.step(n)
+        assert s.steps_done == n
+        assert np.array_equal(s.read("pops")["pops"], r.read("pops")["pops"]), (s.nx, s.ny)
+        assert np.array_equal(s.read("mask")["mask"], r.read("mask")["mask"])
+    b.close()

@@ -7,7 +7,6 @@ import pytest
 import inputs
 from paper_1708_01613_gb300.serve import FoamServer, Request, footprint_bytes, run_one_at_a_time, summarize
 
-pytestmark = pytest.mark.gpu
 
 
 def requests():
@@ -20,11 +19,12 @@ def requests():
     return out
 
 
+@pytest.mark.gpu
 def test_served_results_equal_lone_runs_and_budget_holds():
     reqs = requests()
     # room for the two largest boxes at most: the rest queue behind them
     budget = sorted(footprint_bytes(r) for r in reqs)[-1] + sorted(footprint_bytes(r) for r in reqs)[-2]
-    server = FoamServer(memory_budget_bytes=budget, max_boxes=4, quantum_steps=16, keep_pops=True)
+    server = FoamServer(memory_budget_bytes=budget, max_boxes=4, quantum_updates=2e6, keep_pops=True)
     served = {r.rid: r for r in server.run(reqs)}
     assert sorted(served) == [r.rid for r in reqs]
     assert server.stats["peak_bytes"] <= budget
@@ -39,6 +39,25 @@ def test_served_results_equal_lone_runs_and_budget_holds():
     assert summ["requests"] == 6 and summ["p99_s"] >= summ["p50_s"] > 0
 
 
+def test_fair_steps_water_filling():
+    """Pure host logic: equal shares of the update budget, small jobs finish
+    inside their share and hand the rest on, everybody moves."""
+    from paper_1708_01613_gb300.serve import _Job, fair_steps
+
+    def job(rid, nx, ny, rem):
+        return _Job(Request(rid, 0.0, nx, ny, np.zeros((0, 3)), rem), None, rem, 0.0, 0)
+
+    jobs = [job(0, 100, 100, 50), job(1, 1000, 1000, 1000), job(2, 1000, 100, 1000), job(3, 10, 10, 10**6)]
+    s = fair_steps(jobs, 4e6)
+    # by remaining work: job 0 (5e5 updates) fits its 1e6 share; jobs 2 and 3
+    # (1e8 each) split 3.5e6 three ways, then 2.4e6 two ways; job 1 gets the rest
+    assert s == {0: 50, 2: 11, 3: 12000, 1: 1}
+    assert sum(s[j.req.rid] * j.cells for j in jobs) <= 4e6 + 1e6
+    assert all(v >= 1 for v in fair_steps(jobs, 1.0).values())
+    assert fair_steps(jobs, 1e12) == {0: 50, 1: 1000, 2: 1000, 3: 10**6}
+
+
+@pytest.mark.gpu
 def test_request_larger_than_budget_is_refused():
     r = requests()[3]
     with pytest.raises(ValueError):
