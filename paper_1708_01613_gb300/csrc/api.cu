@@ -69,6 +69,7 @@ Layout layout_for(const lbm_config& c) {
     L.ntiles = relabel_tile_count(c.nx, c.ny);
     L.tiles = take(3 * (size_t)L.ntiles);  // gas, active, previous active
     L.tile_list = take(4 * (size_t)L.ntiles);
+    L.rbox = take(sizeof(RelabelBox) + 2 * sizeof(RelabelEntry));
   }
   L.flags = take(sizeof(int) * FLAG_COUNT);
   L.nparts = mass_partials_needed();
@@ -144,15 +145,27 @@ int reset_state(lbm_handle* h) {
   return LBM_OK;
 }
 
+// Descriptor and one-box entry list of the tiled barrier pipeline, written
+// into the workspace once (pointers into the workspace do not move).
+int upload_relabel_box(lbm_handle* h) {
+  if (!handle_relabel_tiled(h)) return LBM_OK;
+  const RelabelBox b = handle_relabel_box(h);
+  RelabelEntry e[2] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  relabel_entry_sizes(h->cfg.nx, h->cfg.ny, &e[1].off_tiles, &e[1].off_scan, &e[1].off_list);
+  CUDA_TRY(h, cudaMemcpyAsync(h->rbox(), &b, sizeof(b), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->rentries(), e, sizeof(e), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // the sources live on this stack frame
+  return LBM_OK;
+}
+
 // Barrier pipeline on the current populations (Sec. 2.1.5).
 int relabel(lbm_handle* h) {
   const FieldParams fp = field_params(h);
   const lbm_config& c = h->cfg;
-  if (relabel_tiled_ok(c.nx, c.ny, c.zone_radius)) {
-    CUDA_TRY(h, launch_relabel_tiled(fp, (float)c.gas_threshold, c.zone_radius, (float)c.G, (float)c.rho0,
-                                     (float)c.rupture_eps, h->rho(), h->label(), h->owner(), h->sgn(), h->open(),
-                                     h->mask(), h->tiles(0), h->tiles(1), h->tiles(2),
-                                     reinterpret_cast<int*>(h->ws + h->L.tile_list), h->flags(), h->stream));
+  if (handle_relabel_tiled(h)) {
+    int totals[3];
+    relabel_entry_sizes(c.nx, c.ny, &totals[0], &totals[1], &totals[2]);
+    CUDA_TRY(h, launch_relabel_boxes(c.storage, h->rbox(), h->rentries(), 1, totals, h->cur, h->stream));
     h->launches += 7;
     return LBM_OK;
   }
@@ -206,6 +219,41 @@ int handle_fail(lbm_handle* h, int code, const char* fmt, ...) {
 }
 
 int handle_relabel(lbm_handle* h) { return relabel(h); }
+
+bool handle_relabel_tiled(const lbm_handle* h) {
+  return h->cfg.barrier && relabel_tiled_ok(h->cfg.nx, h->cfg.ny, h->cfg.zone_radius);
+}
+
+RelabelBox handle_relabel_box(lbm_handle* h) {
+  const lbm_config& c = h->cfg;
+  RelabelBox b;
+  memset(&b, 0, sizeof(b));
+  b.pops[0] = h->pops(0);
+  b.pops[1] = h->pops(1);
+  b.rho = h->rho();
+  b.label = h->label();
+  b.owner = h->owner();
+  b.sgn = h->sgn();
+  b.open = h->open();
+  b.mask = h->mask();
+  b.tile_gas = h->tiles(0);
+  b.tile_active = h->tiles(1);
+  b.tile_prev = h->tiles(2);
+  b.tile_list = reinterpret_cast<int*>(h->ws + h->L.tile_list);
+  b.flags = h->flags();
+  b.nx = c.nx;
+  b.ny = c.ny;
+  b.ntx = c.nx / kRelabelTileX;
+  b.nty = c.ny / kRelabelTileY;
+  b.R = c.zone_radius;
+  b.cur = 0;
+  b.threshold = (float)c.gas_threshold;
+  b.G = (float)c.G;
+  b.rho0 = (float)c.rho0;
+  b.eps = (float)c.rupture_eps;
+  for (int i = 0; i < Q; ++i) b.wref[i] = h->wref[i];
+  return b;
+}
 
 int handle_check_flags(lbm_handle* h) { return check_flags(h); }
 
@@ -284,7 +332,7 @@ int lbm_create(const lbm_config* cfg, void* d_workspace, size_t bytes, void* cud
     delete h;
     return LBM_EINVAL;
   }
-  if (reset_state(h) != LBM_OK) {
+  if (reset_state(h) != LBM_OK || upload_relabel_box(h) != LBM_OK) {
     delete h;
     return LBM_ECUDA;
   }

@@ -506,17 +506,45 @@ __global__ void __launch_bounds__(kThreads) k_stats_partial(long long N, const i
 // later kernels skip every tile that is inactive now and was inactive at the
 // previous relabel: its owner/sign/mask are already -1/0/0. A tile that just
 // became inactive is reset to those values. Results equal the untiled kernels.
-constexpr int kTX = 32, kTY = 8;
+//
+// Every phase is one launch over any number of boxes (a lone box is a list
+// of one): each box's CTAs follow those of the boxes before it in the entry
+// list (RelabelEntry prefix sums), and a CTA finds its box by binary search.
+constexpr int kTX = kRelabelTileX, kTY = kRelabelTileY;
+constexpr int kListCtas = 152 * 8;  // CTAs per box for the tile-list phases, at most
 
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+enum { kOffTiles = 0, kOffScan = 1, kOffList = 2 };
+
+template <int F>
+__device__ __forceinline__ int entry_off(const RelabelEntry& e) {
+  return F == kOffTiles ? e.off_tiles : (F == kOffScan ? e.off_scan : e.off_list);
+}
+
+// Entry k owning CTA `b`: the last k < m with off(k) <= b.
+template <int F>
+__device__ __forceinline__ int find_entry(const RelabelEntry* __restrict__ e, int m, int b) {
+  int lo = 0, hi = m - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (entry_off<F>(e[mid]) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int S>
-__global__ void __launch_bounds__(kTX * kTY) kt_density_label(const FieldParams fp, float th, float* __restrict__ rho,
-                                                              int32_t* __restrict__ L, uint8_t* __restrict__ tile_gas) {
+__global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* __restrict__ boxes,
+                                                              const RelabelEntry* __restrict__ e, int m, int parity) {
   using T = typename Store<S>::T;
-  const T* p = static_cast<const T*>(fp.pops);
-  const int nx = fp.nx, ny = fp.ny;
-  const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
+  const int k = find_entry<kOffTiles>(e, m, blockIdx.x);
+  const RelabelBox& B = boxes[e[k].box];
+  const int t = blockIdx.x - e[k].off_tiles;
+  const T* p = static_cast<const T*>(B.pops[B.cur ^ parity]);
+  const int nx = B.nx, ny = B.ny;
+  const size_t N = (size_t)nx * ny;
+  const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
   const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
   const size_t r0 = (size_t)y * nx, rm = (size_t)wrap1(y - 1, ny) * nx, rp = (size_t)wrap1(y + 1, ny) * nx;
   float f[Q];
@@ -524,44 +552,68 @@ __global__ void __launch_bounds__(kTX * kTY) kt_density_label(const FieldParams 
   for (int i = 0; i < Q; ++i) {
     const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
     const int xs = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : x);
-    f[i] = Store<S>::load(p, (size_t)i * fp.N + row + xs, fp.wref[i]);
+    f[i] = Store<S>::load(p, (size_t)i * N + row + xs, B.wref[i]);
   }
   const float r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   const size_t c = r0 + x;
-  rho[c] = r;
-  const bool gas = r < th;
-  L[c] = gas ? (int32_t)c : -1;
+  B.rho[c] = r;
+  const bool gas = r < B.threshold;
+  B.label[c] = gas ? (int32_t)c : -1;
   const int any = __syncthreads_or(gas);
-  if (threadIdx.x == 0 && threadIdx.y == 0) tile_gas[blockIdx.y * gridDim.x + blockIdx.x] = (uint8_t)(any != 0);
-}
-
-// Also appends every tile that needs a visit (active now or at the previous
-// relabel) to `list`; the order of the list does not affect any result.
-__global__ void kt_active(const uint8_t* __restrict__ gas, uint8_t* __restrict__ active,
-                          const uint8_t* __restrict__ prev, int* __restrict__ list, int* __restrict__ count, int ntx,
-                          int nty, int spx, int spy) {
-  const int ntiles = ntx * nty;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
-    const int ty = t / ntx, tx = t - ty * ntx;
-    int a = 0;
-    for (int dy = -spy; dy <= spy && !a; ++dy) {
-      const int yy = wrapi(ty + dy, nty);
-      for (int dx = -spx; dx <= spx; ++dx) a |= gas[yy * ntx + wrapi(tx + dx, ntx)];
-    }
-    active[t] = (uint8_t)(a != 0);
-    if (a || prev[t]) list[atomicAdd(count, 1)] = t;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    B.tile_gas[t] = (uint8_t)(any != 0);
+    if (t == 0) B.flags[FLAG_TILES] = 0;  // the tile list is rebuilt by the next phase
   }
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_union(int nx, int ny, int ntx, int32_t* L,
-                                                      const uint8_t* __restrict__ tile_gas, const int* __restrict__ list,
-                                                      const int* __restrict__ count, int* flags) {
-  const int n = *count;
+// Also appends every tile that needs a visit (active now or at the previous
+// relabel) to the box's list; the order of the list does not affect any
+// result.
+__global__ void kb_active(const RelabelBox* __restrict__ boxes, const RelabelEntry* __restrict__ e, int m) {
+  const int k = find_entry<kOffScan>(e, m, blockIdx.x);
+  const RelabelBox& B = boxes[e[k].box];
+  const int t = (blockIdx.x - e[k].off_scan) * blockDim.x + threadIdx.x;
+  const int ntx = B.ntx, nty = B.nty;
+  if (t >= ntx * nty) return;
+  const int spx = (B.R + kTX - 1) / kTX, spy = (B.R + kTY - 1) / kTY;
+  const int ty = t / ntx, tx = t - ty * ntx;
+  int a = 0;
+  for (int dy = -spy; dy <= spy && !a; ++dy) {
+    const int yy = wrapi(ty + dy, nty);
+    for (int dx = -spx; dx <= spx; ++dx) a |= B.tile_gas[yy * ntx + wrapi(tx + dx, ntx)];
+  }
+  B.tile_active[t] = (uint8_t)(a != 0);
+  if (a || B.tile_prev[t]) B.tile_list[atomicAdd(B.flags + FLAG_TILES, 1)] = t;
+}
+
+// CTA `first` of `stride` CTAs that walk box k's tile list.
+struct ListWalk {
+  const RelabelBox* B;
+  int first, stride, n;
+};
+
+__device__ __forceinline__ ListWalk list_walk(const RelabelBox* __restrict__ boxes, const RelabelEntry* __restrict__ e,
+                                              int m) {
+  const int k = find_entry<kOffList>(e, m, blockIdx.x);
+  ListWalk w;
+  w.B = &boxes[e[k].box];
+  w.first = blockIdx.x - e[k].off_list;
+  w.stride = e[k + 1].off_list - e[k].off_list;
+  w.n = w.B->flags[FLAG_TILES];
+  return w;
+}
+
+__global__ void __launch_bounds__(kTX * kTY) kb_union(const RelabelBox* __restrict__ boxes,
+                                                      const RelabelEntry* __restrict__ e, int m) {
+  const ListWalk lw = list_walk(boxes, e, m);
+  const RelabelBox& B = *lw.B;
+  const int nx = B.nx, ny = B.ny;
+  int32_t* L = B.label;
   int fail = 0;
-  for (int w = blockIdx.x; w < n; w += gridDim.x) {
-    const int t = list[w];
-    if (!tile_gas[t]) continue;
-    const int x = (t % ntx) * kTX + threadIdx.x, y = (t / ntx) * kTY + threadIdx.y;
+  for (int w = lw.first; w < lw.n; w += lw.stride) {
+    const int t = B.tile_list[w];
+    if (!B.tile_gas[t]) continue;
+    const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
     const int c = y * nx + x;
     if (L[c] < 0) continue;
     const int right = y * nx + (x + 1 == nx ? 0 : x + 1);
@@ -569,137 +621,142 @@ __global__ void __launch_bounds__(kTX * kTY) kt_union(int nx, int ny, int ntx, i
     if (L[right] >= 0) unite(L, c, right, &fail);
     if (L[down] >= 0) unite(L, c, down, &fail);
   }
-  if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
+  if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_flatten(int nx, int ntx, int32_t* L, const uint8_t* __restrict__ tile_gas,
-                                                        const int* __restrict__ list, const int* __restrict__ count,
-                                                        int* flags) {
-  const int n = *count;
+__global__ void __launch_bounds__(kTX * kTY) kb_flatten(const RelabelBox* __restrict__ boxes,
+                                                        const RelabelEntry* __restrict__ e, int m) {
+  const ListWalk lw = list_walk(boxes, e, m);
+  const RelabelBox& B = *lw.B;
+  int32_t* L = B.label;
   int fail = 0;
-  for (int w = blockIdx.x; w < n; w += gridDim.x) {
-    const int t = list[w];
-    if (!tile_gas[t]) continue;
-    const int c = ((t / ntx) * kTY + threadIdx.y) * nx + (t % ntx) * kTX + threadIdx.x;
+  for (int w = lw.first; w < lw.n; w += lw.stride) {
+    const int t = B.tile_list[w];
+    if (!B.tile_gas[t]) continue;
+    const int c = ((t / B.ntx) * kTY + threadIdx.y) * B.nx + (t % B.ntx) * kTX + threadIdx.x;
     if (L[c] >= 0) L[c] = find_root(L, c, &fail);
   }
-  if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
+  if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_owner(int nx, int ny, int ntx, int R, const int32_t* __restrict__ L,
-                                                      int32_t* __restrict__ own, const uint8_t* __restrict__ active,
-                                                      const int* __restrict__ list, const int* __restrict__ count) {
+__global__ void __launch_bounds__(kTX * kTY) kb_owner(const RelabelBox* __restrict__ boxes,
+                                                      const RelabelEntry* __restrict__ e, int m) {
   __shared__ int32_t sl[(kTY + 2 * kOMaxR) * (kTX + 2 * kOMaxR)];
-  const int n = *count;
-  for (int w = blockIdx.x; w < n; w += gridDim.x) {
-  const int t = list[w];
-  const int tx = t % ntx, ty = t / ntx;
-  const int x = tx * kTX + threadIdx.x, y = ty * kTY + threadIdx.y;
-  const size_t c = (size_t)y * nx + x;
-  if (!active[t]) {  // went quiet since the previous relabel
-    own[c] = -1;
-    continue;
-  }
-  const int W = kTX + 2 * R, H = kTY + 2 * R;
-  const int bx0 = tx * kTX - R, by0 = ty * kTY - R;
-  __syncthreads();  // the previous tile's window is no longer read
-  for (int yy = threadIdx.y; yy < H; yy += kTY) {
-    const size_t row = (size_t)wrap1(by0 + yy, ny) * nx;
-    for (int xx = threadIdx.x; xx < W; xx += kTX) sl[yy * W + xx] = L[row + wrap1(bx0 + xx, nx)];
-  }
-  __syncthreads();
-  const int* row0 = sl + (threadIdx.y + R) * W + threadIdx.x + R;
-  int result = row0[0];
-  if (result < 0) {
-    int bd = 0x7fffffff;
-    for (int dy = -R; dy <= R; ++dy) {
-      const int* rowp = row0 + dy * W;
-      for (int dx = -R; dx <= R; ++dx) {
-        const int d2 = dx * dx + dy * dy;
-        if (d2 > R * R || d2 > bd) continue;
-        const int l = rowp[dx];
-        if (l < 0) continue;
-        if (d2 < bd || l < result) {
-          bd = d2;
-          result = l;
+  const ListWalk lw = list_walk(boxes, e, m);
+  const RelabelBox& B = *lw.B;
+  const int nx = B.nx, ny = B.ny, R = B.R;
+  const int32_t* L = B.label;
+  for (int w = lw.first; w < lw.n; w += lw.stride) {
+    const int t = B.tile_list[w];
+    const int tx = t % B.ntx, ty = t / B.ntx;
+    const int x = tx * kTX + threadIdx.x, y = ty * kTY + threadIdx.y;
+    const size_t c = (size_t)y * nx + x;
+    if (!B.tile_active[t]) {  // went quiet since the previous relabel
+      B.owner[c] = -1;
+      continue;
+    }
+    const int W = kTX + 2 * R, H = kTY + 2 * R;
+    const int bx0 = tx * kTX - R, by0 = ty * kTY - R;
+    __syncthreads();  // the previous tile's window is no longer read
+    for (int yy = threadIdx.y; yy < H; yy += kTY) {
+      const size_t row = (size_t)wrap1(by0 + yy, ny) * nx;
+      for (int xx = threadIdx.x; xx < W; xx += kTX) sl[yy * W + xx] = L[row + wrap1(bx0 + xx, nx)];
+    }
+    __syncthreads();
+    const int* row0 = sl + (threadIdx.y + R) * W + threadIdx.x + R;
+    int result = row0[0];
+    if (result < 0) {
+      int bd = 0x7fffffff;
+      for (int dy = -R; dy <= R; ++dy) {
+        const int* rowp = row0 + dy * W;
+        for (int dx = -R; dx <= R; ++dx) {
+          const int d2 = dx * dx + dy * dy;
+          if (d2 > R * R || d2 > bd) continue;
+          const int l = rowp[dx];
+          if (l < 0) continue;
+          if (d2 < bd || l < result) {
+            bd = d2;
+            result = l;
+          }
         }
       }
     }
-  }
-  own[c] = result;
+    B.owner[c] = result;
   }
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_rupture(int nx, int ny, int ntx, float G, float rho0, float eps,
-                                                        const float* __restrict__ rho, const int32_t* __restrict__ own,
-                                                        int8_t* __restrict__ sgn, uint8_t* __restrict__ open,
-                                                        const uint8_t* __restrict__ active,
-                                                        const int* __restrict__ list, const int* __restrict__ count,
-                                                        int* flags) {
-  const int nw = *count;
-  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-  const int t = list[w];
-  const int act = active[t];
-  const int x = (t % ntx) * kTX + threadIdx.x, y = (t / ntx) * kTY + threadIdx.y;
-  const size_t c = (size_t)y * nx + x;
-  const int o = act ? own[c] : -1;
-  int dir = 0;
-  if (o >= 0) {
+__global__ void __launch_bounds__(kTX * kTY) kb_rupture(const RelabelBox* __restrict__ boxes,
+                                                        const RelabelEntry* __restrict__ e, int m) {
+  const ListWalk lw = list_walk(boxes, e, m);
+  const RelabelBox& B = *lw.B;
+  const int nx = B.nx, ny = B.ny;
+  const int32_t* own = B.owner;
+  for (int w = lw.first; w < lw.n; w += lw.stride) {
+    const int t = B.tile_list[w];
+    const int act = B.tile_active[t];
+    const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    const size_t c = (size_t)y * nx + x;
+    const int o = act ? own[c] : -1;
+    int dir = 0;
+    if (o >= 0) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int on = own[(size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx)];
-      if (dir == 0 && on >= 0 && on != o) dir = i;
-    }
-  }
-  int opened = 0;
-  if (dir == 0) {
-    sgn[c] = 0;
-  } else {
-    int ex = 0, ey = 0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i)
-      if (i == dir) {
-        ex = cx(i);
-        ey = cy(i);
+      for (int i = 1; i < Q; ++i) {
+        const int on = own[(size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx)];
+        if (dir == 0 && on >= 0 && on != o) dir = i;
       }
-    const float pp = pressure_of(rho[(size_t)wrap1(y + ey, ny) * nx + wrap1(x + ex, nx)], G, rho0);
-    const float p0 = pressure_of(rho[c], G, rho0);
-    const float pm = pressure_of(rho[(size_t)wrap1(y - ey, ny) * nx + wrap1(x - ex, nx)], G, rho0);
-    const float d2 = pp - 2.0f * p0 + pm;
-    const int sg = (d2 > 0.f) - (d2 < 0.f);
-    const int prevs = sgn[c];
-    if (eps >= 0.f && !open[c] && (fabsf(d2) <= eps || (prevs != 0 && sg != prevs))) {
-      open[c] = 1;
-      opened = 1;
     }
-    sgn[c] = (int8_t)sg;
-  }
-  const int n = __syncthreads_count(opened);
-  if (n && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(flags + FLAG_OPENED, n);
+    int opened = 0;
+    if (dir == 0) {
+      B.sgn[c] = 0;
+    } else {
+      int ex = 0, ey = 0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if (i == dir) {
+          ex = cx(i);
+          ey = cy(i);
+        }
+      const float pp = pressure_of(B.rho[(size_t)wrap1(y + ey, ny) * nx + wrap1(x + ex, nx)], B.G, B.rho0);
+      const float p0 = pressure_of(B.rho[c], B.G, B.rho0);
+      const float pm = pressure_of(B.rho[(size_t)wrap1(y - ey, ny) * nx + wrap1(x - ex, nx)], B.G, B.rho0);
+      const float d2 = pp - 2.0f * p0 + pm;
+      const int sg = (d2 > 0.f) - (d2 < 0.f);
+      const int prevs = B.sgn[c];
+      if (B.eps >= 0.f && !B.open[c] && (fabsf(d2) <= B.eps || (prevs != 0 && sg != prevs))) {
+        B.open[c] = 1;
+        opened = 1;
+      }
+      B.sgn[c] = (int8_t)sg;
+    }
+    const int n = __syncthreads_count(opened);
+    if (n && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(B.flags + FLAG_OPENED, n);
   }
 }
 
-__global__ void __launch_bounds__(kTX * kTY) kt_mask(int nx, int ny, int ntx, const int32_t* __restrict__ own,
-                                                     const uint8_t* __restrict__ open, uint8_t* __restrict__ mask,
-                                                     const uint8_t* __restrict__ active,
-                                                     const int* __restrict__ list, const int* __restrict__ count) {
-  const int nw = *count;
-  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-  const int t = list[w];
-  const int act = active[t];
-  const int x = (t % ntx) * kTX + threadIdx.x, y = (t / ntx) * kTY + threadIdx.y;
-  const size_t c = (size_t)y * nx + x;
-  unsigned m = 0;
-  const int o = act ? own[c] : -1;
-  if (o >= 0 && !open[c]) {
+// Also records this relabel's activity as the "previous" one of the next:
+// tiles outside the list are inactive in both, so only listed tiles change.
+__global__ void __launch_bounds__(kTX * kTY) kb_mask(const RelabelBox* __restrict__ boxes,
+                                                     const RelabelEntry* __restrict__ e, int m) {
+  const ListWalk lw = list_walk(boxes, e, m);
+  const RelabelBox& B = *lw.B;
+  const int nx = B.nx, ny = B.ny;
+  for (int w = lw.first; w < lw.n; w += lw.stride) {
+    const int t = B.tile_list[w];
+    const int act = B.tile_active[t];
+    const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    const size_t c = (size_t)y * nx + x;
+    unsigned msk = 0;
+    const int o = act ? B.owner[c] : -1;
+    if (o >= 0 && !B.open[c]) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const size_t nb = (size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx);
-      const int on = own[nb];
-      if (on >= 0 && on != o && !open[nb]) m |= 1u << (i - 1);
+      for (int i = 1; i < Q; ++i) {
+        const size_t nb = (size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx);
+        const int on = B.owner[nb];
+        if (on >= 0 && on != o && !B.open[nb]) msk |= 1u << (i - 1);
+      }
     }
-  }
-  mask[c] = (uint8_t)m;
+    B.mask[c] = (uint8_t)msk;
+    if (threadIdx.x == 0 && threadIdx.y == 0) B.tile_prev[t] = (uint8_t)act;
   }
 }
 
@@ -863,35 +920,30 @@ bool relabel_tiled_ok(int nx, int ny, int R) { return nx % kTX == 0 && ny % kTY 
 
 int relabel_tile_count(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY); }
 
-cudaError_t launch_relabel_tiled(const FieldParams& fp, float threshold, int R, float G, float rho0, float eps,
-                                 float* rho, int32_t* label, int32_t* owner, int8_t* sgn, uint8_t* open,
-                                 uint8_t* mask, uint8_t* tile_gas, uint8_t* tile_active, uint8_t* tile_prev,
-                                 int* tile_list, int* flags, cudaStream_t s) {
-  const int nx = fp.nx, ny = fp.ny;
-  const int ntx = nx / kTX, nty = ny / kTY;
-  const dim3 grid(ntx, nty), block(kTX, kTY);
-  switch (fp.storage) {
-    case LBM_F32: kt_density_label<LBM_F32><<<grid, block, 0, s>>>(fp, threshold, rho, label, tile_gas); break;
-    case LBM_F16_DEV: kt_density_label<LBM_F16_DEV><<<grid, block, 0, s>>>(fp, threshold, rho, label, tile_gas); break;
-    case LBM_BF16_DEV: kt_density_label<LBM_BF16_DEV><<<grid, block, 0, s>>>(fp, threshold, rho, label, tile_gas); break;
+void relabel_entry_sizes(int nx, int ny, int* tiles, int* scan, int* list) {
+  const int t = relabel_tile_count(nx, ny);
+  *tiles = t;
+  *scan = (t + kThreads - 1) / kThreads;
+  *list = t < kListCtas ? t : kListCtas;
+}
+
+cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const RelabelEntry* entries, int m,
+                                 const int totals[3], int parity, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  const dim3 block(kTX, kTY);
+  switch (storage) {
+    case LBM_F32: kb_density_label<LBM_F32><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
+    case LBM_F16_DEV: kb_density_label<LBM_F16_DEV><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
+    case LBM_BF16_DEV: kb_density_label<LBM_BF16_DEV><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
     default: return cudaErrorInvalidValue;
   }
-  const int spx = (R + kTX - 1) / kTX, spy = (R + kTY - 1) / kTY;
-  int* count = flags + FLAG_TILES;
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  kt_active<<<blocks_for((long long)ntx * nty), kThreads, 0, s>>>(tile_gas, tile_active, tile_prev, tile_list, count,
-                                                                 ntx, nty, spx, spy);
-  const int wgrid = 152 * 8;  // tiles are taken from the list in a grid-stride loop
-  kt_union<<<wgrid, block, 0, s>>>(nx, ny, ntx, label, tile_gas, tile_list, count, flags);
-  kt_flatten<<<wgrid, block, 0, s>>>(nx, ntx, label, tile_gas, tile_list, count, flags);
-  kt_owner<<<wgrid, block, 0, s>>>(nx, ny, ntx, R, label, owner, tile_active, tile_list, count);
-  kt_rupture<<<wgrid, block, 0, s>>>(nx, ny, ntx, G, rho0, eps, rho, owner, sgn, open, tile_active, tile_list, count,
-                                     flags);
-  kt_mask<<<wgrid, block, 0, s>>>(nx, ny, ntx, owner, open, mask, tile_active, tile_list, count);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyAsync(tile_prev, tile_active, (size_t)ntx * nty, cudaMemcpyDeviceToDevice, s);
+  kb_active<<<totals[1], kThreads, 0, s>>>(boxes, entries, m);
+  kb_union<<<totals[2], block, 0, s>>>(boxes, entries, m);
+  kb_flatten<<<totals[2], block, 0, s>>>(boxes, entries, m);
+  kb_owner<<<totals[2], block, 0, s>>>(boxes, entries, m);
+  kb_rupture<<<totals[2], block, 0, s>>>(boxes, entries, m);
+  kb_mask<<<totals[2], block, 0, s>>>(boxes, entries, m);
+  return cudaGetLastError();
 }
 
 }  // namespace lbm

@@ -14,6 +14,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -40,6 +42,19 @@ struct lbm_batch {
   int max_items = 0;
   int nitems = 0;
   std::vector<BatchItem> items;
+  // barrier pipeline: tiled boxes relabel together, one launch per phase for
+  // all boxes due at the same step; boxes are grouped by the residue of their
+  // step count modulo the relabel period (relative to the batch counter)
+  RelabelBox* d_rboxes = nullptr;
+  RelabelEntry* d_rent = nullptr;
+  struct Group {
+    int start = 0;                        // first entry in d_rent
+    std::vector<int> members;             // box indices, upload order
+    std::vector<std::array<int, 3>> tot;  // CTA totals of the first k members
+  };
+  std::map<int, Group> groups;            // by residue of the step count
+  std::vector<int> untiled;               // boxes relabelled one by one
+  int64_t relabel_launches = 0;           // per relabel period
   int strip = 512, rows = 0;
   int use_graph = 1;
   int dirty = 1;               // descriptors/items must be re-uploaded
@@ -51,6 +66,7 @@ struct lbm_batch {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kMinItems = 64;  // work items per box, where its height allows
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 int bfail(lbm_batch* b, int code, const char* fmt, ...) {
@@ -72,7 +88,7 @@ int bfail(lbm_batch* b, int code, const char* fmt, ...) {
 // Upper bound of work items for any tile choice the batch accepts.
 int max_items_for(lbm_handle* const* hs, int n) {
   long long m = 0;
-  for (int i = 0; i < n; ++i) m += (long long)((hs[i]->cfg.nx + 255) / 256) * ((hs[i]->cfg.ny + 7) / 8);
+  for (int i = 0; i < n; ++i) m += (long long)((hs[i]->cfg.nx + 255) / 256) * hs[i]->cfg.ny;
   return m > 0x7fffffff ? 0x7fffffff : (int)m;
 }
 
@@ -84,19 +100,32 @@ void drop_graphs(lbm_batch* b) {
     }
 }
 
+// Work items. A CTA walks its item row by row, each row a dependent
+// load-compute-store round of a few microseconds, so a launch lasts about
+// (rows per item) x (items per CTA) such rounds. Chunks are therefore no
+// taller than needed to give every resident CTA one item (and at most the
+// tuned height), and a box gets at least kMinItems items, so that a launch
+// over a few small boxes (the end of a multi-rate call) stays short too.
 void build_items(lbm_batch* b) {
   b->items.clear();
+  long long total_rows = 0;
+  for (int i = 0; i < b->n; ++i)
+    if (b->active[i]) total_rows += (long long)((b->h[i]->cfg.nx + b->strip - 1) / b->strip) * b->h[i]->cfg.ny;
+  const int res = std::max(1, batch_resident_ctas(b->storage, b->masked != 0, b->tau_one != 0));
+  const int rows_all = (int)std::max(1LL, std::min<long long>(b->rows, (total_rows + res - 1) / res));
   for (int i = 0; i < b->n; ++i) {
     if (!b->active[i]) continue;
     const int nx = b->h[i]->cfg.nx, ny = b->h[i]->cfg.ny;
+    const int strips = (nx + b->strip - 1) / b->strip;
+    const int rows = std::max(1, std::min(rows_all, (strips * ny + kMinItems - 1) / kMinItems));
     for (int x0 = 0; x0 < nx; x0 += b->strip)
-      for (int y0 = 0; y0 < ny; y0 += b->rows) {
+      for (int y0 = 0; y0 < ny; y0 += rows) {
         BatchItem it;
         it.inst = i;
         it.x0 = x0;
         it.width = std::min(b->strip, nx - x0);
         it.y0 = y0;
-        it.y1 = std::min(y0 + b->rows, ny);
+        it.y1 = std::min(y0 + rows, ny);
         b->items.push_back(it);
       }
   }
@@ -108,10 +137,13 @@ void build_items(lbm_batch* b) {
 }
 
 // Re-uploads descriptors and items (host-synchronous copies). Boxes may be
-// at different step counts: each relabels on its own phase.
-int upload(lbm_batch* b) {
+// at different step counts: each relabels on its own phase. `order` lists
+// the boxes to step, in the order their barrier entries take (empty = all
+// active boxes, by index).
+int upload(lbm_batch* b, const std::vector<int>& order = {}) {
   if (!b->dirty) return LBM_OK;
   std::vector<BatchInst> insts(b->n);
+  std::vector<RelabelBox> rboxes(b->masked ? b->n : 0);
   for (int i = 0; i < b->n; ++i) {
     lbm_handle* h = b->h[i];
     BatchInst& d = insts[i];
@@ -130,6 +162,10 @@ int upload(lbm_batch* b) {
     d.rho_ref = (float)h->cfg.rho_ref;
     d.cur = h->cur;
     b->base_cur[i] = h->cur;
+    if (b->masked && handle_relabel_tiled(h)) {
+      rboxes[i] = handle_relabel_box(h);
+      rboxes[i].cur = h->cur;
+    }
   }
   build_items(b);
   if (b->nitems > b->max_items) return bfail(b, LBM_EINVAL, "too many work items (%d > %d)", b->nitems, b->max_items);
@@ -137,10 +173,86 @@ int upload(lbm_batch* b) {
   if (b->nitems)
     BCUDA(b, cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(BatchItem) * b->nitems, cudaMemcpyHostToDevice,
                              b->stream));
+  BCUDA(b, cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), b->stream));  // item counters (step parity)
+  b->groups.clear();
+  b->untiled.clear();
+  b->relabel_launches = 0;
+  std::vector<RelabelEntry> ents;
+  if (b->masked) {
+    std::vector<int> ord = order;
+    if (ord.empty())
+      for (int i = 0; i < b->n; ++i)
+        if (b->active[i]) ord.push_back(i);
+    const int r = b->h[0]->cfg.relabel_every;
+    for (int i : ord) {
+      lbm_handle* h = b->h[i];
+      if (!handle_relabel_tiled(h)) {
+        b->untiled.push_back(i);
+        b->relabel_launches += 7;
+        continue;
+      }
+      // due at batch count T when T + (t_i - t_batch) is a multiple of r
+      const int64_t o = ((h->t - b->t) % r + r) % r;
+      b->groups[(int)((r - o) % r)].members.push_back(i);
+    }
+    for (auto& kv : b->groups) {
+      lbm_batch::Group& g = kv.second;
+      g.start = (int)ents.size();
+      std::array<int, 3> acc = {0, 0, 0};
+      g.tot.push_back(acc);
+      for (int i : g.members) {
+        ents.push_back({i, acc[0], acc[1], acc[2]});
+        int t0, t1, t2;
+        relabel_entry_sizes(b->h[i]->cfg.nx, b->h[i]->cfg.ny, &t0, &t1, &t2);
+        acc = {acc[0] + t0, acc[1] + t1, acc[2] + t2};
+        g.tot.push_back(acc);
+      }
+      ents.push_back({-1, acc[0], acc[1], acc[2]});
+      b->relabel_launches += 7;
+    }
+    BCUDA(b, cudaMemcpyAsync(b->d_rboxes, rboxes.data(), sizeof(RelabelBox) * b->n, cudaMemcpyHostToDevice,
+                             b->stream));
+    if (!ents.empty())
+      BCUDA(b, cudaMemcpyAsync(b->d_rent, ents.data(), sizeof(RelabelEntry) * ents.size(), cudaMemcpyHostToDevice,
+                               b->stream));
+  }
   BCUDA(b, cudaStreamSynchronize(b->stream));
   b->par = 0;
   b->dirty = 0;
   drop_graphs(b);
+  return LBM_OK;
+}
+
+// Barrier pipeline of the boxes due at batch count b->t + j: the first
+// `live` members of their residue group (all of them when live < 0) in one
+// launch per phase, and the untiled boxes one by one (those for which
+// `stepping` says yes). Buffers: parity `parity` since the upload.
+template <class Stepping>
+int enqueue_relabel(lbm_batch* b, int parity, int64_t j, int live, Stepping stepping) {
+  const int r = b->h[0]->cfg.relabel_every;
+  const auto it = b->groups.find((int)((b->t + j) % r));
+  if (it != b->groups.end()) {
+    const lbm_batch::Group& g = it->second;
+    const int m = live < 0 ? (int)g.members.size() : std::min(live, (int)g.members.size());
+    if (m > 0) {
+      BCUDA(b, launch_relabel_boxes(b->storage, b->d_rboxes, b->d_rent + g.start, m, g.tot[m].data(), parity,
+                                    b->stream));
+      b->launches += 7;
+    }
+  }
+  for (int i : b->untiled) {
+    lbm_handle* h = b->h[i];
+    if (!stepping(i) || (h->t + j) % r != 0) continue;
+    const int saved = h->cur;
+    h->cur = b->base_cur[i] ^ parity;
+    cudaStream_t hs = h->stream;
+    h->stream = b->stream;
+    const int rc = handle_relabel(h);
+    h->stream = hs;
+    h->cur = saved;
+    if (rc) return bfail(b, rc, "relabel of box %d: %s", i, h->err);
+    b->launches += 7;
+  }
   return LBM_OK;
 }
 
@@ -159,21 +271,8 @@ void advance(lbm_batch* b, int64_t n) {
 // every box whose own step count is then due, then the batched kernel).
 int enqueue_step(lbm_batch* b, int parity, int64_t j) {
   int rc;
-  if (b->masked)
-    for (int i = 0; i < b->n; ++i) {
-      if (!b->active[i]) continue;
-      lbm_handle* h = b->h[i];
-      if ((h->t + j) % h->cfg.relabel_every != 0) continue;
-      const int saved = h->cur;
-      h->cur = b->base_cur[i] ^ parity;
-      cudaStream_t hs = h->stream;
-      h->stream = b->stream;
-      rc = handle_relabel(h);
-      h->stream = hs;
-      h->cur = saved;
-      if (rc) return bfail(b, rc, "relabel of box %d: %s", i, h->err);
-      b->launches += 7;
-    }
+  if (b->masked && (rc = enqueue_relabel(b, parity, j, -1, [&](int i) { return b->active[i] != 0; })))
+    return rc;
   BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items, b->nitems,
                              b->d_counter, parity, b->stream));
   b->launches += 1;
@@ -229,7 +328,8 @@ size_t lbm_batch_workspace_bytes(lbm_handle* const* handles, int32_t n) {
   for (int i = 0; i < n; ++i)
     if (!handles[i]) return 0;
   const int mi = max_items_for(handles, n);
-  return align_up(sizeof(BatchInst) * (size_t)n) + align_up(sizeof(BatchItem) * (size_t)mi) + kAlign;
+  return align_up(sizeof(BatchInst) * (size_t)n) + align_up(sizeof(BatchItem) * (size_t)mi) + kAlign +
+         align_up(sizeof(RelabelBox) * (size_t)n) + align_up(sizeof(RelabelEntry) * (2 * (size_t)n + 1));
 }
 
 int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, size_t bytes, lbm_batch** out) {
@@ -278,6 +378,9 @@ int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, s
   b->d_items = reinterpret_cast<BatchItem*>(b->ws + align_up(sizeof(BatchInst) * (size_t)n));
   b->d_counter = reinterpret_cast<int*>(b->ws + align_up(sizeof(BatchInst) * (size_t)n) +
                                         align_up(sizeof(BatchItem) * (size_t)b->max_items));
+  b->d_rboxes = reinterpret_cast<RelabelBox*>(reinterpret_cast<char*>(b->d_counter) + kAlign);
+  b->d_rent = reinterpret_cast<RelabelEntry*>(reinterpret_cast<char*>(b->d_rboxes) +
+                                              align_up(sizeof(RelabelBox) * (size_t)n));
   // default tiles: full-width strips, chunks giving ~4 items per resident CTA
   long long cells = 0;
   for (int i = 0; i < n; ++i) cells += (long long)handles[i]->cfg.nx * handles[i]->cfg.ny;
@@ -347,7 +450,7 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     const int p = b->par;
     if (!b->graph[p] && (rc = build_graph(b, p))) return rc;
     BCUDA(b, cudaGraphLaunch(b->graph[p], b->stream));
-    b->launches += b->K + (b->masked ? 7LL * active_count(b) * b->K / b->h[0]->cfg.relabel_every : 0);
+    b->launches += b->K + b->relabel_launches;  // every group relabels once per period
     advance(b, b->K);
     left -= b->K;
   }
@@ -380,15 +483,15 @@ int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n) {
   for (int i = 0; i < n; ++i)
     if (nsteps[i] > 0) order.push_back(i);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return nsteps[a] > nsteps[c]; });
-  // item list in that order; prefix[k] = items of the first k boxes
+  // item list and barrier groups in that order
   std::vector<int> keep = b->active;
   for (int i = 0; i < n; ++i) b->active[i] = nsteps[i] > 0;
   b->dirty = 1;
-  rc = upload(b);  // items of the stepping boxes, current buffers
+  rc = upload(b, order);
   b->active = keep;
   if (rc) return rc;
   std::vector<BatchItem> sorted;
-  std::vector<int> prefix(order.size() + 1, 0);
+  std::vector<int> prefix(order.size() + 1, 0);  // items of the first k boxes
   for (size_t k = 0; k < order.size(); ++k) {
     for (const BatchItem& it : b->items)
       if (it.inst == order[k]) sorted.push_back(it);
@@ -396,24 +499,24 @@ int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n) {
   }
   BCUDA(b, cudaMemcpyAsync(b->d_items, sorted.data(), sizeof(BatchItem) * sorted.size(), cudaMemcpyHostToDevice,
                            b->stream));
+  std::map<int, int> glive;  // members of each barrier group still stepping
+  for (const auto& kv : b->groups) glive[kv.first] = (int)kv.second.members.size();
   size_t live = order.size();
   for (int64_t j = 0; j < most; ++j) {
     while (live > 0 && nsteps[order[live - 1]] <= j) --live;
     const int parity = (int)(j & 1);
-    if (b->masked)
-      for (size_t k = 0; k < live; ++k) {
-        lbm_handle* h = b->h[order[k]];
-        if ((h->t + j) % h->cfg.relabel_every != 0) continue;
-        const int saved = h->cur;
-        h->cur = b->base_cur[order[k]] ^ parity;
-        cudaStream_t hs = h->stream;
-        h->stream = b->stream;
-        rc = handle_relabel(h);
-        h->stream = hs;
-        h->cur = saved;
-        if (rc) return bfail(b, rc, "relabel of box %d: %s", order[k], h->err);
-        b->launches += 7;
+    if (b->masked) {
+      const int key = (int)((b->t + j) % b->h[0]->cfg.relabel_every);
+      int gl = 0;
+      const auto it = b->groups.find(key);
+      if (it != b->groups.end()) {
+        const std::vector<int>& mem = it->second.members;
+        int& c = glive[key];
+        while (c > 0 && nsteps[mem[c - 1]] <= j) --c;
+        gl = c;
       }
+      if ((rc = enqueue_relabel(b, parity, j, gl, [&](int i) { return nsteps[i] > j; }))) return rc;
+    }
     BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items,
                                prefix[live], b->d_counter, parity, b->stream));
     b->launches += 1;

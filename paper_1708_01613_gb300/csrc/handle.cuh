@@ -11,7 +11,7 @@ namespace lbm {
 
 // Offsets of the slices of the caller's workspace.
 struct Layout {
-  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, tile_list, flags, partials, scalars, total;
+  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, tile_list, rbox, flags, partials, scalars, total;
   int nparts, ntiles;
 };
 
@@ -41,6 +41,9 @@ struct lbm_handle {
   int8_t* sgn() { return cfg.barrier ? reinterpret_cast<int8_t*>(ws + L.sgn) : nullptr; }
   uint8_t* tiles(int k) { return reinterpret_cast<uint8_t*>(ws + L.tiles) + (size_t)k * L.ntiles; }
   int* flags() { return reinterpret_cast<int*>(ws + L.flags); }
+  // the box's own barrier-pipeline descriptor and its one-box entry list
+  lbm::RelabelBox* rbox() { return reinterpret_cast<lbm::RelabelBox*>(ws + L.rbox); }
+  lbm::RelabelEntry* rentries() { return reinterpret_cast<lbm::RelabelEntry*>(rbox() + 1); }
   double* partials() { return reinterpret_cast<double*>(ws + L.partials); }
   double* scalars() { return reinterpret_cast<double*>(ws + L.scalars); }
   size_t N() const { return (size_t)cfg.nx * cfg.ny; }
@@ -57,5 +60,9 @@ int handle_relabel(lbm_handle* h);
 int handle_check_flags(lbm_handle* h);
 // Step parameters of the handle (buffers chosen by the caller).
 StepParams handle_step_params(lbm_handle* h);
+// True when the handle's barrier pipeline runs tiled (RelabelBox form).
+bool handle_relabel_tiled(const lbm_handle* h);
+// The handle's barrier-pipeline descriptor (host copy, cur = 0).
+RelabelBox handle_relabel_box(lbm_handle* h);
 
 }  // namespace lbm

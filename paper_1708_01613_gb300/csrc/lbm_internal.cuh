@@ -134,9 +134,11 @@ void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk
 // Whether the TMA-staged step kernel can run on a box of width nx.
 bool step_tma_allowed(int storage, int nx);
 // Batched fused step (two-cell staged march over a list of work items of
-// many boxes); resets *counter and launches one persistent grid.
+// many boxes); one persistent grid drawing items from counters[parity] and
+// zeroing counters[parity ^ 1]. Both counters must be zero before the
+// first launch and consecutive launches must alternate parity.
 cudaError_t launch_step_batch(int storage, bool masked, bool tau_one, const BatchInst* insts, const BatchItem* items,
-                              int nitems, int* counter, int parity, cudaStream_t s);
+                              int nitems, int* counters, int parity, cudaStream_t s);
 // CTAs of the batched kernel that fit the GPU at once.
 int batch_resident_ctas(int storage, bool masked, bool tau_one);
 // Whether the two-cell staged step kernel can run on a box of width nx.
@@ -191,12 +193,43 @@ cudaError_t launch_stats(int nx, int ny, const int32_t* label, int32_t* area, do
 constexpr int kMaxHistBins = 64;
 // Tiled barrier pipeline (barrier.cu): density + labels + tile flags, then
 // union, flatten, owner, rupture and mask restricted to tiles near gas.
+// One launch per phase serves any number of boxes.
 bool relabel_tiled_ok(int nx, int ny, int R);
 int relabel_tile_count(int nx, int ny);
-cudaError_t launch_relabel_tiled(const FieldParams& fp, float threshold, int R, float G, float rho0, float eps,
-                                 float* rho, int32_t* label, int32_t* owner, int8_t* sgn, uint8_t* open,
-                                 uint8_t* mask, uint8_t* tile_gas, uint8_t* tile_active, uint8_t* tile_prev,
-                                 int* tile_list, int* flags, cudaStream_t s);
+constexpr int kRelabelTileX = 32, kRelabelTileY = 8;  // tile of the pipeline
+
+// A box as the pipeline sees it (device memory). Populations are read from
+// pops[cur ^ parity], parity being the launch argument.
+struct RelabelBox {
+  const void* pops[2];
+  float* rho;
+  int32_t* label;
+  int32_t* owner;
+  int8_t* sgn;
+  uint8_t* open;
+  uint8_t* mask;
+  uint8_t* tile_gas;
+  uint8_t* tile_active;
+  uint8_t* tile_prev;
+  int* tile_list;
+  int* flags;
+  int nx, ny, ntx, nty, R, cur;
+  float threshold, G, rho0, eps;
+  float wref[Q];
+};
+
+// Box `box` in a launch's entry list, with the CTAs of the entries before it
+// in each kind of phase (per-tile, tile-scan, tile-list). An entry list of m
+// boxes has m + 1 entries: the last holds the totals.
+struct RelabelEntry {
+  int box, off_tiles, off_scan, off_list;
+};
+
+// CTAs a box takes in each kind of phase.
+void relabel_entry_sizes(int nx, int ny, int* tiles, int* scan, int* list);
+// The seven phases over the first m entries; totals = entries[m]'s offsets.
+cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const RelabelEntry* entries, int m,
+                                 const int totals[3], int parity, cudaStream_t s);
 int mass_partials_needed();
 
 }  // namespace lbm

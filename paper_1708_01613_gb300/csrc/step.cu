@@ -754,15 +754,20 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
 
 // Many boxes in one launch: persistent CTAs take work items (box, strip,
 // row chunk) from a device counter until the list is exhausted. Each box
-// reads buffer `cur ^ parity` and writes the other.
+// reads buffer `cur ^ parity` and writes the other. Launches alternate
+// parity, so two counters take turns: this launch draws from
+// counters[parity] and zeroes counters[parity ^ 1] for the next one (which
+// starts only after this one has finished), so no reset is launched.
 template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(kTmaThreads, MINB)
     k_step_batch(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
-                 int* __restrict__ counter, int parity) {
+                 int* __restrict__ counters, int parity) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int item_sh;
   const Tma2Smem<S, MASKED, NSTAGE> sm(smem);
   march2_init(sm);
+  int* counter = counters + parity;
+  if (blockIdx.x == 0 && threadIdx.x == 0) counters[parity ^ 1] = 0;
   unsigned gstage = 0;
   for (int guard = 0; guard < nitems + 1; ++guard) {
     __syncthreads();  // the previous item's ring and item index are no longer read
@@ -951,15 +956,13 @@ struct BatchKernel {
     }
     return r;
   }
-  static cudaError_t launch(const BatchInst* insts, const BatchItem* items, int nitems, int* counter, int parity,
+  static cudaError_t launch(const BatchInst* insts, const BatchItem* items, int nitems, int* counters, int parity,
                             cudaStream_t s) {
     const int res = resident();
     if (res == 0) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
     const int grid = nitems < res ? nitems : res;
-    if (grid <= 0) return cudaSuccess;
-    k_step_batch<S, MASKED, TAU_ONE, NS, MINB><<<grid, kTmaThreads, SMEM, s>>>(insts, items, nitems, counter, parity);
+    if (grid <= 0) return cudaMemsetAsync(counters, 0, 2 * sizeof(int), s);  // no launch resets them
+    k_step_batch<S, MASKED, TAU_ONE, NS, MINB><<<grid, kTmaThreads, SMEM, s>>>(insts, items, nitems, counters, parity);
     return cudaGetLastError();
   }
 };

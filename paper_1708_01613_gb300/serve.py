@@ -101,30 +101,88 @@ def fair_steps(jobs: list[_Job], budget_updates: float) -> dict[int, int]:
     among the jobs (processor sharing by work), a job needing less than its
     share takes all its remaining steps and leaves the rest to the others
     (water-filling), and every job advances at least one step."""
+    return _water_fill(jobs, budget_updates, lambda j: float(j.cells))
+
+
+def fair_time_steps(jobs: list[_Job], budget_s: float, launch_s: float, s_per_update: float) -> dict[int, int]:
+    """Like `fair_steps`, but the shares are GPU time: a step of job j is
+    taken to cost launch_s + s_per_update * cells (a small box's step is
+    bound by the launch, not by its cells)."""
+    return _water_fill(jobs, budget_s, lambda j: launch_s + s_per_update * j.cells)
+
+
+def lockstep_steps(jobs: list[_Job], budget_s: float, launch_s: float, s_per_update: float) -> dict[int, int]:
+    """Every job steps in every launch (until its count is reached); the
+    number of launches L is the largest whose predicted time, the sum over
+    launches of launch_s + s_per_update * (cells still stepping), fits the
+    budget (at least one launch)."""
+    by_rem = sorted((j.remaining, j.cells) for j in jobs)
+    live = float(sum(c for _, c in by_rem))
+    t, L, k = 0.0, 0, 0
+    while k < len(by_rem):
+        nxt = by_rem[k][0]  # launches L .. nxt-1 step the same set of jobs
+        per = launch_s + s_per_update * live
+        fit = int((budget_s - t) // per)
+        if L + fit < nxt:
+            L += max(0, fit)
+            break
+        t += per * (nxt - L)
+        L = nxt
+        while k < len(by_rem) and by_rem[k][0] == nxt:
+            live -= by_rem[k][1]
+            k += 1
+    L = max(1, L)
+    return {j.req.rid: min(j.remaining, L) for j in jobs}
+
+
+def _water_fill(jobs: list[_Job], budget: float, cost) -> dict[int, int]:
     out: dict[int, int] = {}
-    left = float(budget_updates)
-    order = sorted(jobs, key=lambda j: j.remaining * j.cells)
+    left = float(budget)
+    order = sorted(jobs, key=lambda j: j.remaining * cost(j))
     for k, j in enumerate(order):
         share = max(0.0, left) / (len(order) - k)
-        s = j.remaining if j.remaining * j.cells <= share else max(1, int(share // j.cells))
+        c = cost(j)
+        s = j.remaining if j.remaining * c <= share else max(1, int(share // c))
         s = min(s, j.remaining)
         out[j.req.rid] = s
-        left -= s * j.cells
+        left -= s * c
     return out
+
+
+class _CostModel:
+    """Quantum time ~ launch_s * launches + s_per_update * updates, fitted
+    by least squares over the recent quanta."""
+
+    def __init__(self, launch_s=1e-5, s_per_update=1.0 / 5e10, keep=64):
+        self.launch_s, self.s_per_update, self.keep = launch_s, s_per_update, keep
+        self.obs: list[tuple[float, float, float]] = []
+
+    def add(self, launches: int, updates: float, seconds: float) -> None:
+        self.obs = (self.obs + [(float(launches), float(updates), float(seconds))])[-self.keep:]
+        if len(self.obs) < 4:
+            return
+        A = np.array([[o[0], o[1]] for o in self.obs])
+        y = np.array([o[2] for o in self.obs])
+        sol, *_ = np.linalg.lstsq(A, y, rcond=None)
+        if sol[0] > 0 and sol[1] > 0:
+            self.launch_s, self.s_per_update = float(sol[0]), float(sol[1])
 
 
 @dataclass
 class FoamServer:
-    """Continuous batching: each quantum (about `quantum_s` of GPU time, from
-    a running estimate of the update rate, or exactly `quantum_updates` cell
-    updates when given) is split fairly between the resident boxes with
-    `fair_steps`, and every batch runs its share as multi-rate steps
-    (lbm_batch_step_each): small boxes take many cheap steps while large ones
-    take few, so a small request is not held to the pace of the largest box."""
+    """Continuous batching in quanta of about `quantum_s` of GPU time (from a
+    cost model fitted to the quanta so far). Each quantum's steps per box
+    follow `policy`: "work" shares the cell updates equally (`fair_steps`;
+    `quantum_updates` fixes the budget), "time" shares GPU time counting a
+    launch cost per step (`fair_time_steps`), "lockstep" steps every box in
+    every launch (`lockstep_steps`). Every batch runs its plan as multi-rate
+    steps (lbm_batch_step_each), so small boxes can take many cheap steps
+    while large ones take few."""
     memory_budget_bytes: int
     max_boxes: int = 64
-    quantum_s: float = 0.02
+    quantum_s: float = 0.01
     quantum_updates: float | None = None
+    policy: str = "work"            # "work" | "time" | "lockstep"
     device: str = "cuda"
     keep_pops: bool = False
     stats: dict = field(default_factory=dict)
@@ -147,7 +205,7 @@ class FoamServer:
         used = 0                           # bytes of boxes still stepping
         peak_held = 0
         rebuilds = quanta = 0
-        rate = 3e10                        # cell updates per second, refined as we go
+        model = _CostModel()               # quantum time vs launches and updates
         t_admit = t_step = t_finish = 0.0
         t0 = time.perf_counter()
         while pending or waiting or active:
@@ -188,8 +246,16 @@ class FoamServer:
                 if pending:
                     time.sleep(max(0.0, pending[0].arrival_s - (time.perf_counter() - t0)))
                 continue
-            budget = self.quantum_updates if self.quantum_updates else rate * self.quantum_s
-            share = fair_steps(list(active.values()), budget)
+            jobs_now = list(active.values())
+            if self.policy == "work":
+                budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
+                share = fair_steps(jobs_now, budget)
+            elif self.policy == "time":
+                share = fair_time_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
+            elif self.policy == "lockstep":
+                share = lockstep_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
+            else:
+                raise ValueError(f"unknown policy {self.policy!r}")
             ts = time.perf_counter()
             live = []
             for b, jobs in batches.values():
@@ -202,7 +268,7 @@ class FoamServer:
             dt = time.perf_counter() - ts
             t_step += dt
             done = sum(share[r] * active[r].cells for r in share)
-            rate = 0.7 * rate + 0.3 * done / max(dt, 1e-6)
+            model.add(max(share.values()), done, dt)
             quanta += 1
             tf = time.perf_counter()
             for b, jobs, plan in live:
@@ -222,7 +288,8 @@ class FoamServer:
         self.stats = {"makespan_s": time.perf_counter() - t0, "peak_bytes": peak_held,
                       "batch_rebuilds": rebuilds, "quanta": quanta, "admit_s": round(t_admit, 4),
                       "step_s": round(t_step, 4), "finish_s": round(t_finish, 4),
-                      "rate_mlups": round(rate / 1e6, 1)}
+                      "policy": self.policy, "launch_us": round(model.launch_s * 1e6, 2),
+                      "rate_mlups": round(1e-6 / model.s_per_update, 1)}
         return results
 
 

@@ -57,6 +57,27 @@ def test_fair_steps_water_filling():
     assert fair_steps(jobs, 1e12) == {0: 50, 1: 1000, 2: 1000, 3: 10**6}
 
 
+def test_time_share_and_lockstep_plans():
+    from paper_1708_01613_gb300.serve import _Job, fair_time_steps, lockstep_steps
+
+    def job(rid, cells, rem):
+        return _Job(Request(rid, 0.0, cells, 1, np.zeros((0, 3)), rem), None, rem, 0.0, 0)
+
+    jobs = [job(0, 100, 1000), job(1, 10**6, 1000)]
+    # step costs 1e-5 + 1e-9 * cells: 1.01e-5 s and 1.01e-3 s; budget 0.02 s
+    # -> job 0 wants 1000 * 1.01e-5 = 0.0101 s > 0.01 s share: 990 steps,
+    #    job 1 gets the rest: (0.02 - 990 * 1.01e-5) / 1.01e-3 -> 9 steps
+    assert fair_time_steps(jobs, 0.02, 1e-5, 1e-9) == {0: 990, 1: 9}
+    # lockstep: each launch costs 1e-5 + 1e-9 * 1000100 = 1.0101e-3 s -> 19 launches
+    assert lockstep_steps(jobs, 0.02, 1e-5, 1e-9) == {0: 19, 1: 19}
+    # short job ends after 5 launches, the rest are cheaper
+    jobs = [job(0, 10**6, 5), job(1, 100, 10**5)]
+    t5 = 5 * (1e-5 + 1e-9 * 1000100)
+    more = int((0.02 - t5) // (1e-5 + 1e-7))
+    assert lockstep_steps(jobs, 0.02, 1e-5, 1e-9) == {0: 5, 1: 5 + more}
+    assert lockstep_steps(jobs, 0.0, 1e-5, 1e-9) == {0: 1, 1: 1}
+
+
 @pytest.mark.gpu
 def test_request_larger_than_budget_is_refused():
     r = requests()[3]
