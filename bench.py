@@ -331,11 +331,14 @@ def run_served(args, dev, world, rank, capacity_ups):
                         "128-4096 log-uniform, 2-300 bubbles, 1k-20k steps x step_scale, FP32/FP16 50/50, "
                         "barrier on (K=10)",
             "step_scale": scale, "rate_per_s": round(rate, 3), "memory_budget_gb": args.serve_budget_gb,
-            "p50_s": served["p50_s"], "p99_s": served["p99_s"], "mlups": served["mlups"],
+            "policy": server.policy, "quantum_s": server.quantum_s,
+            "p50_s": served["p50_s"], "p99_s": served["p99_s"], "mean_s": served["mean_s"],
+            "p50_by_size_s": served["p50_by_size_s"], "mlups": served["mlups"],
             "makespan_s": served["makespan_s"], "batch_rebuilds": server.stats["batch_rebuilds"],
             "server": {k: server.stats[k] for k in ("quanta", "admit_s", "step_s", "finish_s", "rate_mlups")},
             "peak_resident_gb": round(server.stats["peak_bytes"] / 2**30, 2),
-            "one_at_a_time": {"p50_s": alone["p50_s"], "p99_s": alone["p99_s"], "mlups": alone["mlups"],
+            "one_at_a_time": {"p50_s": alone["p50_s"], "p99_s": alone["p99_s"], "mean_s": alone["mean_s"],
+                              "p50_by_size_s": alone["p50_by_size_s"], "mlups": alone["mlups"],
                               "makespan_s": alone["makespan_s"]}}
 
 

@@ -104,9 +104,10 @@ void drop_graphs(lbm_batch* b) {
 // load-compute-store round of a few microseconds, so a launch lasts about
 // (rows per item) x (items per CTA) such rounds. Chunks are therefore no
 // taller than needed to give every resident CTA one item (and at most the
-// tuned height), and a box gets at least kMinItems items, so that a launch
-// over a few small boxes (the end of a multi-rate call) stays short too.
-void build_items(lbm_batch* b) {
+// tuned height). For multi-rate steps (`spread`) a box also gets at least
+// kMinItems items, so that the launches over a few small boxes at the end
+// of a call stay short too.
+void build_items(lbm_batch* b, bool spread) {
   b->items.clear();
   long long total_rows = 0;
   for (int i = 0; i < b->n; ++i)
@@ -117,7 +118,7 @@ void build_items(lbm_batch* b) {
     if (!b->active[i]) continue;
     const int nx = b->h[i]->cfg.nx, ny = b->h[i]->cfg.ny;
     const int strips = (nx + b->strip - 1) / b->strip;
-    const int rows = std::max(1, std::min(rows_all, (strips * ny + kMinItems - 1) / kMinItems));
+    const int rows = spread ? std::max(1, std::min(rows_all, (strips * ny + kMinItems - 1) / kMinItems)) : rows_all;
     for (int x0 = 0; x0 < nx; x0 += b->strip)
       for (int y0 = 0; y0 < ny; y0 += rows) {
         BatchItem it;
@@ -139,7 +140,7 @@ void build_items(lbm_batch* b) {
 // Re-uploads descriptors and items (host-synchronous copies). Boxes may be
 // at different step counts: each relabels on its own phase. `order` lists
 // the boxes to step, in the order their barrier entries take (empty = all
-// active boxes, by index).
+// active boxes, by index; a non-empty order means multi-rate steps).
 int upload(lbm_batch* b, const std::vector<int>& order = {}) {
   if (!b->dirty) return LBM_OK;
   std::vector<BatchInst> insts(b->n);
@@ -167,7 +168,7 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
       rboxes[i].cur = h->cur;
     }
   }
-  build_items(b);
+  build_items(b, !order.empty());
   if (b->nitems > b->max_items) return bfail(b, LBM_EINVAL, "too many work items (%d > %d)", b->nitems, b->max_items);
   BCUDA(b, cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice, b->stream));
   if (b->nitems)

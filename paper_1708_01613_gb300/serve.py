@@ -312,14 +312,21 @@ def run_one_at_a_time(requests: list[Request], device: str = "cuda", keep_pops: 
     return results, time.perf_counter() - t0
 
 
+def _pct(vals: list[float], p: float) -> float:
+    v = sorted(vals)
+    return v[min(len(v) - 1, max(0, int(round(p / 100.0 * (len(v) - 1)))))]
+
+
 def summarize(results: list[Result], makespan_s: float) -> dict:
-    lat = sorted(r.latency_s for r in results)
+    """Latency percentiles (nearest rank), mean, throughput, and the median
+    latency of the smallest, middle and largest third of the requests by
+    work (cells x steps)."""
+    lat = [r.latency_s for r in results]
     updates = sum(r.cells * r.steps for r in results)
-
-    def pct(p):
-        k = min(len(lat) - 1, max(0, int(round(p / 100.0 * (len(lat) - 1)))))
-        return lat[k]
-
-    return {"requests": len(results), "p50_s": round(pct(50), 4), "p99_s": round(pct(99), 4),
-            "mean_s": round(statistics.mean(lat), 4), "makespan_s": round(makespan_s, 3),
-            "mlups": round(updates / makespan_s / 1e6, 1), "cell_updates": updates}
+    by_work = sorted(results, key=lambda r: r.cells * r.steps)
+    k = len(by_work)
+    thirds = [by_work[: k // 3], by_work[k // 3: 2 * k // 3], by_work[2 * k // 3:]]
+    return {"requests": len(results), "p50_s": round(float(_pct(lat, 50)), 4), "p99_s": round(float(_pct(lat, 99)), 4),
+            "mean_s": round(float(statistics.mean(lat)), 4), "makespan_s": round(makespan_s, 3),
+            "mlups": round(updates / makespan_s / 1e6, 1), "cell_updates": updates,
+            "p50_by_size_s": [round(float(_pct([r.latency_s for r in t], 50)), 4) if t else None for t in thirds]}
