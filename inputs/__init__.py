@@ -12,6 +12,7 @@ from .synth import (  # noqa: F401
     clustered_bubbles,
     log_uniform_sides,
     batch_instances,
+    nucleation_schedule,
     serving_requests,
     RHO_GAS_G55,
     RHO_LIQ_G55,

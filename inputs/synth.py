@@ -161,6 +161,20 @@ def batch_instances(count: int = 64, side_lo: int = 256, side_hi: int = 2048,
     return out
 
 
+def nucleation_schedule(nx: int, ny: int, count: int, t_max: int, r_lo: float = 3.0, r_hi: float = 8.0,
+                        seed: int = 61) -> np.ndarray:
+    """Random nucleation events (the paper's "time random subroutine"): rows
+    (step, cx, cy, r), steps uniform in [0, t_max), sites uniform over the
+    box, radii log-uniform in [r_lo, r_hi], sorted by step (stable)."""
+    s = _Stream(seed)
+    rows = []
+    for _ in range(count):
+        t = min(t_max - 1, int(s.uniform() * t_max))
+        rows.append((float(t), s.uniform() * nx, s.uniform() * ny, s.log_uniform(r_lo, r_hi)))
+    rows.sort(key=lambda r: r[0])
+    return np.array(rows, dtype=np.float64).reshape(-1, 4)
+
+
 def serving_requests(count: int = 2000, rate_per_s: float = 10.0, side_lo: int = 128,
                      side_hi: int = 4096, bub_lo: int = 2, bub_hi: int = 300,
                      steps_lo: int = 1000, steps_hi: int = 20000, seed: int = 41,

@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("relabel_every", C.c_int32), ("zone_radius", C.c_int32),
                 ("stop_on_first_rupture", C.c_int32), ("tau", C.c_double),
                 ("G", C.c_double), ("rho0", C.c_double), ("gas_threshold", C.c_double),
-                ("rupture_eps", C.c_double)]
+                ("rupture_eps", C.c_double), ("growth_rate", C.c_double),
+                ("growth_budget", C.c_double)]
 
 
 class _State(C.Structure):
@@ -57,7 +58,8 @@ class _State(C.Structure):
                 ("Fx", C.c_void_p), ("Fy", C.c_void_p), ("label", C.c_void_p),
                 ("owner", C.c_void_p), ("sgn", C.c_void_p), ("open", C.c_void_p),
                 ("mask", C.c_void_p), ("t", C.c_int64), ("opened_total", C.c_int64),
-                ("opened_last", C.c_int32), ("halted", C.c_int32)]
+                ("opened_last", C.c_int32), ("halted", C.c_int32), ("gas", C.c_void_p),
+                ("n_gas", C.c_int64), ("injected", C.c_double)]
 
 
 def lib():
@@ -82,6 +84,8 @@ def lib():
             "orc_rupture": (None, [P, vp, vp, vp, vp, vp]),
             "orc_mask": (None, [P, vp, vp, vp]),
             "orc_relabel": (None, [P, S]),
+            "orc_gas_census": (None, [P, S]),
+            "orc_nucleate": (None, [P, S, vp, C.c_int32, C.c_double]),
             "orc_init_state": (None, [P, S, vp]),
             "orc_step": (C.c_int, [P, S]),
             "orc_run": (C.c_int64, [P, S, C.c_int64]),
@@ -109,12 +113,13 @@ def _p(a: np.ndarray | None):
 
 def make_params(nx, ny, *, tau=1.0, G=-5.5, rho0=1.0, barrier=False, relabel_every=1,
                 zone_radius=4, stop_on_first_rupture=False, gas_threshold=None,
-                rupture_eps=1e-6) -> Params:
+                rupture_eps=1e-6, growth_rate=0.0, growth_budget=0.0) -> Params:
     if gas_threshold is None:
         gas_threshold = RHO_CRITICAL
     return Params(nx=nx, ny=ny, barrier=int(bool(barrier)), relabel_every=relabel_every,
                   zone_radius=zone_radius, stop_on_first_rupture=int(bool(stop_on_first_rupture)),
-                  tau=tau, G=G, rho0=rho0, gas_threshold=gas_threshold, rupture_eps=rupture_eps)
+                  tau=tau, G=G, rho0=rho0, gas_threshold=gas_threshold, rupture_eps=rupture_eps,
+                  growth_rate=growth_rate, growth_budget=growth_budget)
 
 
 def set_threads(n: int) -> None:
@@ -239,11 +244,12 @@ class OracleSim:
         self.sgn = np.zeros((ny, nx), np.int8)
         self.open = np.zeros((ny, nx), np.uint8)
         self.mask = np.zeros((ny, nx), np.uint8)
+        self.gas = np.zeros((ny, nx), np.uint8)
         self._s = _State(f=_p(self.f), f_next=_p(self.f_next), rho=_p(self.rho), jx=_p(self.jx),
                          jy=_p(self.jy), psi=_p(self.psi), Fx=_p(self.Fx), Fy=_p(self.Fy),
                          label=_p(self.label), owner=_p(self.owner), sgn=_p(self.sgn),
                          open=_p(self.open), mask=_p(self.mask), t=0, opened_total=0,
-                         opened_last=0, halted=0)
+                         opened_last=0, halted=0, gas=_p(self.gas), n_gas=0, injected=0.0)
 
     def init_density(self, rho: np.ndarray) -> None:
         rho = np.ascontiguousarray(rho, dtype=np.float64)
@@ -255,6 +261,19 @@ class OracleSim:
 
     def relabel(self) -> None:
         lib().orc_relabel(C.byref(self.params), C.byref(self._s))
+
+    def nucleate(self, nuclei, rho_g: float) -> None:
+        """Cells within r of a nucleus (cx, cy, r) become gas at rest (rho_g)."""
+        b = np.ascontiguousarray(np.asarray(nuclei, dtype=np.float64).reshape(-1, 3))
+        lib().orc_nucleate(C.byref(self.params), C.byref(self._s), _p(b), int(b.shape[0]), float(rho_g))
+
+    @property
+    def injected(self) -> float:
+        return float(self._s.injected)
+
+    @property
+    def n_gas(self) -> int:
+        return int(self._s.n_gas)
 
     def step(self, n: int = 1) -> int:
         return int(lib().orc_run(C.byref(self.params), C.byref(self._s), int(n)))

@@ -32,6 +32,11 @@
  *   rupture criterion       Sec. 2.1.5, Eq. 41 (eta_m = 0 when d2p/dn2 = 0)
  *   run termination         Sec. 2.1.4 main flowchart and Sec. 5 (the foam
  *                           run ends when the first cell reaches rupture)
+ *   nucleation and growth   Sec. 2.1.3 (gas nuclei at random sites; every
+ *                           step the released gas is added to the gas
+ *                           points, dp/dt = A (dn/dt) / N, Eq. 34) and the
+ *                           main flowchart's "Random Nucleation" and
+ *                           "Bubble growth" boxes
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   - direction order 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1)
@@ -52,7 +57,19 @@
  *     sign stored at the previous relabel; eps < 0 disables rupture;
  *   - the barrier pipeline runs on the pre-collision density at the start of
  *     every step t with t % K == 0 and the mask is held for K steps;
- *   - reported velocity u = (j + F/2) / rho; reported pressure p of Eq. 29.
+ *   - reported velocity u = (j + F/2) / rho; reported pressure p of Eq. 29;
+ *   - growth: the pressure increment of a gas point is taken on the ideal-gas
+ *     part of the equation of state, dp = c_s^2 drho with c_s^2 = 1/3, so the
+ *     released gas is a density source. Each step releases growth_rate
+ *     (= 3 A dn/dt in lattice units) until growth_budget is used up (the
+ *     last release is the remainder); it is split equally over the N gas
+ *     points (rho < gas_threshold) of the latest census, which is taken with
+ *     the barrier pipeline, every K steps, on the pre-collision density, and
+ *     added at rest after the collision: f_i^out(x) += w_i drho (no momentum);
+ *   - nucleation: a nucleus (cx, cy, r) turns the cells within torus distance
+ *     r of its centre into gas at rest: incoming f_i = w_i rho_g. When and
+ *     where nuclei appear is an input (the paper's random subroutine draws
+ *     them; here the seeded input generator does).
  */
 #include <math.h>
 #include <stdint.h>
@@ -79,6 +96,8 @@ typedef struct {
   double tau, G, rho0;
   double gas_threshold;     /* rho below this is gas */
   double rupture_eps;       /* eps for |D2| <= eps; < 0 disables rupture */
+  double growth_rate;       /* gas mass released per step (0: no growth) */
+  double growth_budget;     /* total gas mass of the blowing agent */
 } orc_params;
 
 typedef struct {
@@ -94,6 +113,9 @@ typedef struct {
   int64_t opened_total;    /* cells opened so far */
   int32_t opened_last;     /* cells opened at the latest relabel */
   int32_t halted;          /* 1 after the first rupture if stopping on it */
+  uint8_t *gas;            /* [ny][nx] gas points of the latest census */
+  int64_t n_gas;           /* their number */
+  double injected;         /* gas mass released so far */
 } orc_state;
 
 static inline int wrap(int a, int n) {
@@ -319,6 +341,41 @@ void orc_relabel(const orc_params *p, orc_state *s) {
   s->opened_total += opened;
 }
 
+/* Gas points of the current populations: gas[c] = rho < gas_threshold, and
+ * their number (the N of dp/dt = A (dn/dt) / N). */
+void orc_gas_census(const orc_params *p, orc_state *s) {
+  const size_t N = (size_t)p->nx * p->ny;
+  orc_moments(p, s->f, s->rho, NULL, NULL);
+  int64_t n = 0;
+  for (size_t c = 0; c < N; ++c) {
+    s->gas[c] = s->rho[c] < p->gas_threshold;
+    n += s->gas[c];
+  }
+  s->n_gas = n;
+}
+
+/* Nucleation: every cell within torus distance r of a nucleus centre becomes
+ * gas at rest, incoming f_i = w_i rho_g. nuclei: n triples (cx, cy, r). */
+void orc_nucleate(const orc_params *p, orc_state *s, const double *nuclei, int32_t n, double rho_g) {
+  const int nx = p->nx, ny = p->ny;
+  const size_t N = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      int inside = 0;
+      for (int32_t k = 0; k < n && !inside; ++k) {
+        double dx = fabs((double)x - nuclei[3 * k + 0]);
+        double dy = fabs((double)y - nuclei[3 * k + 1]);
+        dx = fmin(dx, nx - dx);
+        dy = fmin(dy, ny - dy);
+        const double r = nuclei[3 * k + 2];
+        inside = dx * dx + dy * dy <= r * r;
+      }
+      if (inside)
+        for (int i = 0; i < Q; ++i) s->f[i * N + (size_t)y * nx + x] = WT[i] * rho_g;
+    }
+}
+
 /* f_i = f_i^eq(rho, 0) = w_i rho, open/sign state cleared, t = 0. */
 void orc_init_state(const orc_params *p, orc_state *s, const double *rho_init) {
   const size_t N = (size_t)p->nx * p->ny;
@@ -332,6 +389,9 @@ void orc_init_state(const orc_params *p, orc_state *s, const double *rho_init) {
   s->opened_total = 0;
   s->opened_last = 0;
   s->halted = 0;
+  if (s->gas) memset(s->gas, 0, N);
+  s->n_gas = 0;
+  s->injected = 0.0;
 }
 
 /* One time step: barrier pipeline when due, then moments (Eq. 11),
@@ -343,7 +403,22 @@ int orc_step(const orc_params *p, orc_state *s) {
   const size_t N = (size_t)nx * ny;
   if (s->halted) return 1;
   int barrier = p->barrier != 0;
-  if (barrier && s->t % p->relabel_every == 0) orc_relabel(p, s);
+  const int growth = p->growth_rate > 0.0;
+  if (s->t % p->relabel_every == 0) {
+    if (barrier) orc_relabel(p, s);
+    if (growth) orc_gas_census(p, s);
+  }
+  /* gas released this step, split over the gas points of the census */
+  double drho = 0.0;
+  if (growth && s->n_gas > 0) {
+    double release = p->growth_rate;
+    const double left = p->growth_budget - s->injected;
+    if (release > left) release = left;
+    if (release > 0.0) {
+      drho = release / (double)s->n_gas;
+      s->injected += release;
+    }
+  }
   orc_moments(p, s->f, s->rho, s->jx, s->jy);
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y)
@@ -361,9 +436,11 @@ int orc_step(const orc_params *p, orc_state *s) {
       double uy = (s->jy[c] + p->tau * s->Fy[c]) / r;
       double feq[Q];
       orc_equilibrium(r, ux, uy, feq);
+      const int source = drho > 0.0 && s->gas[c];
       for (int i = 0; i < Q; ++i) {
         double fi = s->f[i * N + c];
         double fout = fi - (fi - feq[i]) / p->tau;
+        if (source) fout += WT[i] * drho;
         size_t dst = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
         s->f_next[i * N + dst] = fout;
       }

@@ -508,3 +508,145 @@ def test_inputs_are_seeded_and_independent_of_order():
             dx = abs(bub[i, 0] - bub[j, 0]); dx = min(dx, 512 - dx)
             dy = abs(bub[i, 1] - bub[j, 1]); dy = min(dy, 512 - dy)
             assert math.hypot(dx, dy) - bub[i, 2] - bub[j, 2] >= 2.0
+
+
+# ------------------------------------------------ nucleation and growth (Sec. 2.1.3)
+def test_growth_uniform_gas_box_closed_form():
+    """All cells are gas points and the box stays uniform (no gradient, no
+    force), so each step adds exactly release / N to every cell; the release
+    stops when the budget is spent (the last release is the remainder)."""
+    nx, ny, rho0 = 24, 10, 0.3
+    rate, budget = 0.75, 5.0
+    P = O.make_params(nx, ny, growth_rate=rate, growth_budget=budget, relabel_every=3)
+    s = O.OracleSim(P)
+    s.init_density(np.full((ny, nx), rho0))
+    for t in range(1, 10):
+        s.step(1)
+        released = min(t * rate, budget)
+        fl = s.fields()
+        assert np.allclose(fl["rho"], rho0 + released / (nx * ny), rtol=0, atol=1e-14)
+        assert np.abs(fl["ux"]).max() < 1e-15 and np.abs(fl["uy"]).max() < 1e-15
+        assert s.injected == pytest.approx(released, abs=1e-13)
+        assert s.n_gas == nx * ny
+
+
+@pytest.mark.parametrize("barrier", [False, True])
+def test_growth_mass_accounting_and_momentum(barrier):
+    """Mass grows by exactly the released gas (collision and streaming keep
+    sum f; the source adds w_i drho per gas point); the source is at rest,
+    so with the barrier off the momentum sum(j + F/2) stays conserved."""
+    nx, ny = 96, 64
+    b = inputs.poisson_disk_bubbles(nx, ny, 4, 6.0, 10.0, 3.0, seed=5)
+    P = O.make_params(nx, ny, barrier=barrier, relabel_every=4, growth_rate=0.02, growth_budget=1.5)
+    s = O.OracleSim(P)
+    s.init_density(O.init_bubbles(P, b, inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, 4.0))
+    m0, p0 = s.mass(), s.momentum()
+    s.step(100)
+    assert s.injected == pytest.approx(1.5, abs=1e-12)  # 75 releases of 0.02 use the budget
+    assert abs(s.mass() - (m0 + s.injected)) / m0 < 1e-13
+    if not barrier:
+        p1 = s.momentum()
+        assert abs(p1[0] - p0[0]) < 1e-12 * m0 and abs(p1[1] - p0[1]) < 1e-12 * m0
+
+
+def test_growth_source_goes_to_census_gas_points_only():
+    """One step from a state with known gas points: the incoming populations
+    of the next step differ from the source-free step by w_i drho exactly at
+    the streaming targets of the gas points, drho = release / N."""
+    nx, ny = 40, 24
+    b = [[12.0, 12.0, 5.0], [30.0, 10.0, 4.0]]
+    rho = O.init_bubbles(O.make_params(nx, ny), b, inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, 4.0)
+    plain = O.OracleSim(O.make_params(nx, ny))
+    plain.init_density(rho)
+    grow = O.OracleSim(O.make_params(nx, ny, growth_rate=0.3, growth_budget=10.0))
+    grow.init_density(rho)
+    plain.step(1)
+    grow.step(1)
+    gas = rho < O.RHO_CRITICAL
+    N = int(gas.sum())
+    assert grow.n_gas == N and np.array_equal(grow.gas.astype(bool), gas)
+    ex, ey, w = O.lattice()
+    want = plain.f.copy()
+    for i in range(9):
+        want[i] += np.roll(np.roll(gas * (w[i] * 0.3 / N), ey[i], axis=0), ex[i], axis=1)
+    assert np.allclose(grow.f, want, rtol=0, atol=1e-15)
+    assert not np.array_equal(grow.f, plain.f)
+
+
+def test_growth_off_is_the_plain_step():
+    """A zero rate, or a spent budget, reduces to the plain method bitwise."""
+    nx, ny = 48, 32
+    rho = inputs.noise_density(nx, ny, seed=2)
+    runs = []
+    for rate, budget in ((0.0, 5.0), (0.5, 0.0), (0.0, 0.0)):
+        s = O.OracleSim(O.make_params(nx, ny, growth_rate=rate, growth_budget=budget))
+        s.init_density(rho)
+        s.step(20)
+        runs.append(s.f.copy())
+    ref = O.OracleSim(O.make_params(nx, ny))
+    ref.init_density(rho)
+    ref.step(20)
+    for f in runs:
+        assert np.array_equal(f, ref.f)
+
+
+def test_nucleation_disks_brute_force():
+    """Nuclei turn exactly the lattice points within torus distance r of
+    their centres (counted by brute force, wrapping included) into gas at
+    rest; every other population is untouched."""
+    nx, ny = 37, 23
+    rho = np.full((ny, nx), inputs.RHO_LIQ_G55)
+    s = O.OracleSim(O.make_params(nx, ny))
+    s.init_density(rho)
+    before = s.f.copy()
+    nuclei = [[1.0, 2.0, 3.0], [20.5, 11.0, 2.5], [36.0, 22.0, 1.0]]
+    s.nucleate(nuclei, inputs.RHO_GAS_G55)
+    inside = np.zeros((ny, nx), bool)
+    for cx, cy, r in nuclei:
+        for y in range(ny):
+            for x in range(nx):
+                dx = min(abs(x - cx), nx - abs(x - cx))
+                dy = min(abs(y - cy), ny - abs(y - cy))
+                inside[y, x] |= dx * dx + dy * dy <= r * r
+    assert inside[0, 0] and inside[22, 0] and inside[0, 36]  # wrapped corners
+    _, _, w = O.lattice()
+    for i in range(9):
+        assert np.array_equal(s.f[i][inside], np.full(inside.sum(), w[i] * inputs.RHO_GAS_G55))
+        assert np.array_equal(s.f[i][~inside], before[i][~inside])
+
+
+def test_growth_raises_the_bubble_pressure():
+    """The released gas raises the pressure of the gas points (the paper's
+    pressure increment): in a bubble of radius 20 fed at 0.5 per step, the
+    mean pressure (Eq. 29) and density in the bubble's core stay above those
+    of the same bubble without release. (In a closed periodic box the added
+    mass also condenses into the liquid, so the bubble does not expand; an
+    expanding bubble needs the liquid to leave the box.)"""
+    n = 96
+    yy, xx = np.mgrid[0:n, 0:n]
+    core = (xx - 48) ** 2 + (yy - 48) ** 2 <= 12 ** 2
+    p_core, rho_core = {}, {}
+    for rate in (0.0, 0.5):
+        P = O.make_params(n, n, growth_rate=rate, growth_budget=300.0, relabel_every=5)
+        s = O.OracleSim(P)
+        s.init_density(O.init_bubbles(P, [[48.0, 48.0, 20.0]], inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, 4.0))
+        p_core[rate], rho_core[rate] = [], []
+        for _ in range(3):
+            s.step(50)
+            f = s.fields()
+            p_core[rate].append(f["p"][core].mean())
+            rho_core[rate].append(f["rho"][core].mean())
+    for k in range(3):
+        assert p_core[0.5][k] > p_core[0.0][k] + 5e-4
+        assert rho_core[0.5][k] > rho_core[0.0][k] + 4e-3
+
+
+def test_nucleation_schedule_is_seeded_and_in_range():
+    a = inputs.nucleation_schedule(200, 100, 30, 500, seed=7)
+    b = inputs.nucleation_schedule(200, 100, 30, 500, seed=7)
+    c = inputs.nucleation_schedule(200, 100, 30, 500, seed=8)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    assert a.shape == (30, 4) and np.all(np.diff(a[:, 0]) >= 0)
+    assert a[:, 0].min() >= 0 and a[:, 0].max() < 500 and np.all(a[:, 0] == np.floor(a[:, 0]))
+    assert np.all((a[:, 1] >= 0) & (a[:, 1] < 200) & (a[:, 2] >= 0) & (a[:, 2] < 100))
+    assert np.all((a[:, 3] >= 3.0) & (a[:, 3] <= 8.0))
