@@ -80,7 +80,8 @@ typedef struct {
   int32_t stop_on_first_rupture; /* 1: lbm_step stops after the step whose
                                     relabel first opened a cell (Sec. 2.1.4
                                     flowchart; Sec. 5 "best foaming time") */
-  int32_t reserved;              /* must be 0 */
+  int32_t growth;                /* 1: reserve room (4 bytes per cell) for the
+                                    growth source of lbm_set_growth; 0: none */
   double tau;                    /* BGK relaxation time > 0.5 */
   double G;                      /* Shan-Chen coupling (Eq. 22) */
   double rho0;                   /* psi scale, psi = rho0 (1 - exp(-rho/rho0)) */
@@ -172,6 +173,36 @@ int lbm_read_fields(lbm_handle* h, uint32_t fields, void* dst, size_t dst_bytes,
 /* FP64 sum of rho over the box, reduced in a fixed order. Synchronises. */
 int lbm_mass(lbm_handle* h, double* out);
 
+/* Nucleation (Sec. 2.1.3, "Random Nucleation" of the main flowchart):
+ * every cell within torus distance r of a nucleus centre (cx, cy) becomes
+ * gas at rest, its incoming populations set to w_i rho_g. The decision
+ * dx^2 + dy^2 <= r^2 is taken in FP64 (dx, dy: torus distances along x and
+ * y), like the oracle's. When and where nuclei appear is the caller's
+ * choice (the paper draws them at random). nuclei: n host triples, read
+ * before the call returns; n = 0 does nothing. LBM_EINVAL on non-finite
+ * input or r < 0. Enqueued on the handle's stream. */
+int lbm_nucleate(lbm_handle* h, const lbm_bubble* nuclei, int32_t n, double rho_g);
+
+/* Bubble growth (Sec. 2.1.3, Eq. 34, dp/dt = A (dn/dt) / N): from the next
+ * step on, every step releases `rate` of gas mass (lattice units; the
+ * pressure increment taken on the ideal-gas part of the EOS, so rate =
+ * 3 A dn/dt) until `budget` has been released (the last release is the
+ * remainder). A release is split equally over the N gas points (rho <
+ * gas_threshold) of the latest gas census, taken with the barrier pipeline
+ * every K steps on the pre-collision density, and added at rest to the
+ * post-collision populations: f_i^out(x) += w_i rate / N. No census exists
+ * until the next step t with t % K == 0, so nothing is released before it.
+ * Needs a handle created with config.growth = 1 (else LBM_EINVAL) and FP32
+ * storage (LBM_ENOTSUP otherwise: a release split over many gas points adds
+ * far less than half a unit in the last place of a 16-bit deviation, so it
+ * would round away), rate and budget >= 0 and finite. Resets the released
+ * total to 0; rate = 0 turns the source off. Not available to boxes in a
+ * batch. */
+int lbm_set_growth(lbm_handle* h, double rate, double budget);
+
+/* Gas mass released so far by the growth source (FP64). Synchronises. */
+int lbm_growth_released(lbm_handle* h, double* out);
+
 /* Bubble statistics of the current density (labels recomputed) and, if
  * hist != NULL, a histogram of equivalent diameters on nbins logarithmic
  * bins over [dmin, dmax) (outliers clamped to the end bins). Synchronises. */
@@ -205,7 +236,9 @@ void lbm_destroy(lbm_handle* h);
  * in a batch may not be stepped with lbm_step. */
 typedef struct lbm_batch lbm_batch;
 
-/* Device bytes lbm_batch_create needs for these boxes (0 if invalid). */
+/* Device bytes lbm_batch_create needs for these boxes (0 if invalid).
+ * Boxes created with config.growth = 1 or stop_on_first_rupture = 1 cannot
+ * join a batch (LBM_ENOTSUP). */
 size_t lbm_batch_workspace_bytes(lbm_handle* const* handles, int32_t n);
 
 /* Creates a batch over n handles with a caller-owned device workspace

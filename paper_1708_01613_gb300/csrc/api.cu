@@ -38,7 +38,7 @@ bool valid_config(const lbm_config* c, char* why, size_t n) {
     return snprintf(why, n, "with the barrier on, 2 zone_radius + 1 < nx, ny"), false;
   if (c->stop_on_first_rupture != 0 && c->stop_on_first_rupture != 1)
     return snprintf(why, n, "stop_on_first_rupture must be 0 or 1"), false;
-  if (c->reserved != 0) return snprintf(why, n, "reserved must be 0"), false;
+  if (c->growth != 0 && c->growth != 1) return snprintf(why, n, "growth must be 0 or 1"), false;
   if (!(c->tau > 0.5) || !isfinite(c->tau)) return snprintf(why, n, "tau must be > 0.5"), false;
   if (!isfinite(c->G)) return snprintf(why, n, "G must be finite"), false;
   if (!(c->rho0 > 0.0) || !isfinite(c->rho0)) return snprintf(why, n, "rho0 must be > 0"), false;
@@ -71,6 +71,7 @@ Layout layout_for(const lbm_config& c) {
     L.tile_list = take(4 * (size_t)L.ntiles);
     L.rbox = take(sizeof(RelabelBox) + 2 * sizeof(RelabelEntry));
   }
+  if (c.growth) L.gas_list = take(4 * N);
   L.flags = take(sizeof(int) * FLAG_COUNT);
   L.nparts = mass_partials_needed();
   L.partials = take(sizeof(double) * L.nparts);
@@ -140,6 +141,7 @@ int reset_state(lbm_handle* h) {
     CUDA_TRY(h, cudaMemsetAsync(h->owner(), 0xff, 4 * h->N(), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->tiles(0), 0, 3 * (size_t)h->L.ntiles, h->stream));
   }
+  CUDA_TRY(h, cudaMemsetAsync(h->released(), 0, 2 * sizeof(double), h->stream));
   h->t = 0;
   h->halted = 0;
   return LBM_OK;
@@ -424,10 +426,22 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
         stop_after = after > before;
       }
     }
+    const bool growing = h->growth_rate > 0.0;
+    if (growing && h->t % c.relabel_every == 0) {  // gas census with the barrier pipeline
+      if (!c.barrier) CUDA_TRY(h, launch_density(field_params(h), h->rho(), h->stream));
+      CUDA_TRY(h, launch_gas_census(h->rho(), (long long)h->N(), (float)c.gas_threshold, h->gas_list(),
+                                    h->flags() + FLAG_GAS, h->stream));
+      h->launches += c.barrier ? 1 : 2;
+    }
     p.src = h->pops(h->cur);
     p.dst = h->pops(1 - h->cur);
     CUDA_TRY(h, launch_step(c.storage, p, h->stream));
     h->launches += 1;
+    if (growing) {
+      CUDA_TRY(h, launch_growth(c.storage, p.dst, h->gas_list(), h->flags() + FLAG_GAS, (long long)h->N(),
+                                h->growth_rate, h->growth_budget, h->released(), (int)(h->t & 1), h->stream));
+      h->launches += 1;
+    }
     h->cur ^= 1;
     h->t += 1;
     if (stop_after) h->halted = 1;
@@ -519,6 +533,58 @@ int lbm_read_fields(lbm_handle* h, uint32_t fields, void* dst, size_t dst_bytes,
     out += nb;
   }
   return check_flags(h);
+}
+
+int lbm_nucleate(lbm_handle* h, const lbm_bubble* nuclei, int32_t n, double rho_g) {
+  if (!h) return LBM_EINVAL;
+  if (n < 0 || (n > 0 && !nuclei)) return fail(h, LBM_EINVAL, "bad nucleus list");
+  if (!isfinite(rho_g)) return fail(h, LBM_EINVAL, "rho_g must be finite");
+  for (int k = 0; k < n; ++k)
+    if (!isfinite(nuclei[k].cx) || !isfinite(nuclei[k].cy) || !(nuclei[k].r >= 0.0) || !isfinite(nuclei[k].r))
+      return fail(h, LBM_EINVAL, "nucleus %d: centre must be finite and 0 <= r finite", k);
+  if (n == 0) return LBM_OK;
+  if (sizeof(lbm_bubble) * (size_t)n > h->pops_bytes())
+    return fail(h, LBM_EINVAL, "too many nuclei for the staging area (%d)", n);
+  int rc = select_device(h);
+  if (rc) return rc;
+  lbm_bubble* d_n = static_cast<lbm_bubble*>(h->pops(1 - h->cur));  // the idle buffer stages the list
+  CUDA_TRY(h, cudaMemcpyAsync(d_n, nuclei, sizeof(lbm_bubble) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, launch_nucleate(h->cfg.storage, h->pops(h->cur), d_n, n, rho_g, h->cfg.nx, h->cfg.ny, h->wref,
+                              h->stream));
+  h->launches += 1;
+  // the list is read from pageable memory by an async copy: keep it valid
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_set_growth(lbm_handle* h, double rate, double budget) {
+  if (!h) return LBM_EINVAL;
+  if (!h->cfg.growth) return fail(h, LBM_EINVAL, "the handle was created without config.growth");
+  if (h->cfg.storage != LBM_F32)
+    return fail(h, LBM_ENOTSUP, "the growth source needs FP32 storage (per-step increments fall below "
+                                "the resolution of 16-bit deviations and would be lost)");
+  if (!(rate >= 0.0) || !isfinite(rate) || !(budget >= 0.0) || !isfinite(budget))
+    return fail(h, LBM_EINVAL, "rate and budget must be finite and >= 0");
+  int rc = select_device(h);
+  if (rc) return rc;
+  // no census yet: nothing is released before the next one
+  CUDA_TRY(h, cudaMemsetAsync(h->flags() + FLAG_GAS, 0, sizeof(int), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->released(), 0, 2 * sizeof(double), h->stream));
+  h->growth_rate = rate;
+  h->growth_budget = budget;
+  return LBM_OK;
+}
+
+int lbm_growth_released(lbm_handle* h, double* out) {
+  if (!h) return LBM_EINVAL;
+  if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+  int rc = select_device(h);
+  if (rc) return rc;
+  // the slot written by the latest step (or zeroed by lbm_set_growth)
+  CUDA_TRY(h, cudaMemcpyAsync(out, h->released() + (h->t & 1), sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
 }
 
 int lbm_mass(lbm_handle* h, double* out) {

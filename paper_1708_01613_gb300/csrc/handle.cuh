@@ -11,7 +11,8 @@ namespace lbm {
 
 // Offsets of the slices of the caller's workspace.
 struct Layout {
-  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, tile_list, rbox, flags, partials, scalars, total;
+  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, tile_list, rbox, gas_list, flags, partials, scalars,
+      total;
   int nparts, ntiles;
 };
 
@@ -29,6 +30,7 @@ struct lbm_handle {
   int variant;
   int halted;
   int in_batch;  // 1 while a batch drives this handle
+  double growth_rate, growth_budget;  // growth source (rate 0: off)
   float wref[lbm::Q];
   char err[320];
 
@@ -41,6 +43,9 @@ struct lbm_handle {
   int8_t* sgn() { return cfg.barrier ? reinterpret_cast<int8_t*>(ws + L.sgn) : nullptr; }
   uint8_t* tiles(int k) { return reinterpret_cast<uint8_t*>(ws + L.tiles) + (size_t)k * L.ntiles; }
   int* flags() { return reinterpret_cast<int*>(ws + L.flags); }
+  int32_t* gas_list() { return cfg.growth ? reinterpret_cast<int32_t*>(ws + L.gas_list) : nullptr; }
+  // released growth total, two slots taking turns with the step parity
+  double* released() { return reinterpret_cast<double*>(ws + L.scalars) + 14; }
   // the box's own barrier-pipeline descriptor and its one-box entry list
   lbm::RelabelBox* rbox() { return reinterpret_cast<lbm::RelabelBox*>(ws + L.rbox); }
   lbm::RelabelEntry* rentries() { return reinterpret_cast<lbm::RelabelEntry*>(rbox() + 1); }

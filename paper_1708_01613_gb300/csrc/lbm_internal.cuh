@@ -33,6 +33,7 @@ enum Flag : int {
   FLAG_TIMEOUT = 1,   // a bounded device loop gave up
   FLAG_OPENED = 2,    // cells opened by the latest rupture test
   FLAG_TILES = 3,     // tiles in the relabel work list
+  FLAG_GAS = 4,       // gas points in the growth list
   FLAG_HIST = 64,     // 64 histogram counters
   FLAG_COUNT = 128
 };
@@ -231,5 +232,18 @@ void relabel_entry_sizes(int nx, int ny, int* tiles, int* scan, int* list);
 cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const RelabelEntry* entries, int m,
                                  const int totals[3], int parity, cudaStream_t s);
 int mass_partials_needed();
+
+// Nucleation and growth (growth.cu). The gas census appends every cell with
+// rho < threshold to `list` (order irrelevant) and sets *count. The growth
+// kernel adds w_i drho to the post-collision populations of the listed
+// cells, drho = min(rate, budget - released) / count, reading the released
+// total from released[parity] and writing the new total to
+// released[parity ^ 1] (consecutive steps alternate parity).
+cudaError_t launch_gas_census(const float* rho, long long N, float threshold, int32_t* list, int* count,
+                              cudaStream_t s);
+cudaError_t launch_growth(int storage, void* pops, const int32_t* list, const int* count, long long N,
+                          double rate, double budget, double* released, int parity, cudaStream_t s);
+cudaError_t launch_nucleate(int storage, void* pops, const lbm_bubble* nuclei, int n, double rho_g, int nx,
+                            int ny, const float* wref, cudaStream_t s);
 
 }  // namespace lbm

@@ -611,9 +611,10 @@ struct Tma2Smem {
 // 16, at most kBX2) and rows y0 .. y1 of one box. `gstage` counts the stages
 // this CTA consumed before (mbarrier phases continue across items). Returns
 // false if a stage wait timed out (the CTA must then leave).
-template <int S, bool MASKED, bool TAU_ONE, int NSTAGE>
-__device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MASKED, NSTAGE>& sm, int x0, int width,
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, bool FULL = false>
+__device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MASKED, NSTAGE>& sm, int x0, int width_,
                                        int y0, int y1, unsigned& gstage, int& bad) {
+  const int width = FULL ? kBX2 : width_;  // FULL: a whole strip (known at compile time)
   using G = TmaGeom2<S>;
   using T = typename G::T;
   constexpr int SLOT_BYTES = Tma2Smem<S, MASKED, NSTAGE>::SLOT_BYTES;
@@ -748,7 +749,10 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
   march2_init(sm);
   unsigned gstage = 0;
   int bad = 0;
-  if (!march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, x0, min(kBX2, p.nx - x0), y0, y1, gstage, bad)) return;
+  const int width = min(kBX2, p.nx - x0);
+  const bool ok = width == kBX2 ? march2<S, MASKED, TAU_ONE, NSTAGE, true>(p, sm, x0, width, y0, y1, gstage, bad)
+                                : march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, x0, width, y0, y1, gstage, bad);
+  if (!ok) return;
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
 }
 
@@ -793,7 +797,12 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
     p.inv_rho0 = in.inv_rho0;
     p.rho_ref = in.rho_ref;
     int bad = 0;
-    if (!march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, it.x0, it.width, it.y0, it.y1, gstage, bad)) return;
+    // full strips take the compile-time-width march (with tau != 1 the two
+    // inlined copies would spill at this kernel's register budget)
+    const bool ok = TAU_ONE && it.width == kBX2
+                        ? march2<S, MASKED, TAU_ONE, NSTAGE, TAU_ONE>(p, sm, it.x0, it.width, it.y0, it.y1, gstage, bad)
+                        : march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, it.x0, it.width, it.y0, it.y1, gstage, bad);
+    if (!ok) return;
     if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
   }
 }

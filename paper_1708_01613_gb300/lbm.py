@@ -37,7 +37,7 @@ class LbmError(RuntimeError):
 class lbm_config(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("storage", C.c_int32),
                 ("barrier", C.c_int32), ("relabel_every", C.c_int32), ("zone_radius", C.c_int32),
-                ("stop_on_first_rupture", C.c_int32), ("reserved", C.c_int32),
+                ("stop_on_first_rupture", C.c_int32), ("growth", C.c_int32),
                 ("tau", C.c_double), ("G", C.c_double), ("rho0", C.c_double),
                 ("rho_ref", C.c_double), ("gas_threshold", C.c_double),
                 ("rupture_eps", C.c_double)]
@@ -70,6 +70,9 @@ SIGNATURES = {
     "lbm_fields_bytes": (C.c_size_t, [_vp, C.c_uint32]),
     "lbm_read_fields": (C.c_int, [_vp, C.c_uint32, _vp, C.c_size_t, C.c_int]),
     "lbm_mass": (C.c_int, [_vp, C.POINTER(C.c_double)]),
+    "lbm_nucleate": (C.c_int, [_vp, _vp, C.c_int32, C.c_double]),
+    "lbm_set_growth": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "lbm_growth_released": (C.c_int, [_vp, C.POINTER(C.c_double)]),
     "lbm_bubble_stats": (C.c_int, [_vp, C.POINTER(lbm_stats), _vp, C.c_int32, C.c_double,
                                    C.c_double]),
     "lbm_sync": (C.c_int, [_vp]),
@@ -135,7 +138,8 @@ def lbm_config_default() -> lbm_config:
 def make_config(nx: int, ny: int, *, storage: str = "f32", barrier: bool = False, relabel_every: int = 1,
                 zone_radius: int = 4, stop_on_first_rupture: bool = False, tau: float = 1.0,
                 G: float = -5.5, rho0: float = 1.0, rho_ref: float = 1.0,
-                gas_threshold: float = math.log(2.0), rupture_eps: float = 1e-6) -> lbm_config:
+                gas_threshold: float = math.log(2.0), rupture_eps: float = 1e-6,
+                growth: bool = False) -> lbm_config:
     c = lbm_config_default()
     c.nx, c.ny = int(nx), int(ny)
     c.storage = STORAGE[storage]
@@ -145,6 +149,7 @@ def make_config(nx: int, ny: int, *, storage: str = "f32", barrier: bool = False
     c.stop_on_first_rupture = int(bool(stop_on_first_rupture))
     c.tau, c.G, c.rho0, c.rho_ref = float(tau), float(G), float(rho0), float(rho_ref)
     c.gas_threshold, c.rupture_eps = float(gas_threshold), float(rupture_eps)
+    c.growth = int(bool(growth))
     return c
 
 
@@ -281,6 +286,21 @@ class Simulation:
     def mass(self) -> float:
         v = C.c_double(0.0)
         self._call("lbm_mass", C.byref(v))
+        return float(v.value)
+
+    def nucleate(self, nuclei, rho_g: float) -> None:
+        """Cells within r of a nucleus (cx, cy, r) become gas at rest (rho_g)."""
+        b = np.ascontiguousarray(np.asarray(nuclei, dtype=np.float64).reshape(-1, 3))
+        self._call("lbm_nucleate", C.c_void_p(b.ctypes.data) if len(b) else None, int(len(b)), float(rho_g))
+
+    def set_growth(self, rate: float, budget: float) -> None:
+        """Release `rate` of gas mass per step until `budget` is released."""
+        self._call("lbm_set_growth", float(rate), float(budget))
+
+    @property
+    def growth_released(self) -> float:
+        v = C.c_double(0.0)
+        self._call("lbm_growth_released", C.byref(v))
         return float(v.value)
 
     def stats(self, nbins: int = 0, dmin: float = 1.0, dmax: float = 256.0) -> dict:
