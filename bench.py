@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-k1", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-growth", action="store_true", help="skip the nucleation/growth leg")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-step-scale", type=float, default=0.1)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
@@ -195,10 +196,12 @@ def run_gpu(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     K = args.relabel_every
 
-    def timed(storage: str, relabel_every: int, steps: int, warmup: int, sample_clocks: bool):
+    def timed(storage: str, relabel_every: int, steps: int, warmup: int, sample_clocks: bool, growth=None):
         sim = Simulation(make_config(n, n, storage=storage, barrier=True, relabel_every=relabel_every,
-                                     rho_ref=RL), device=dev)
+                                     rho_ref=RL, growth=growth is not None), device=dev)
         sim.init_bubbles(bub, RL, RG, 4.0)
+        if growth is not None:
+            sim.set_growth(*growth)
         sim.step(warmup)
         sim.sync()
         stream = sim.stream
@@ -229,10 +232,11 @@ def run_gpu(args, world, rank, local):
         plain = [d for k, d in enumerate(per) if (t_first + k) % relabel_every != 0]
         relab = [d for k, d in enumerate(per) if (t_first + k) % relabel_every == 0]
         st = sim.stats()
+        released = sim.growth_released if growth is not None else 0.0
         del sim
         torch.cuda.empty_cache()
         return dict(total_ms=total_ms, per=per, plain=plain, relab=relab, launches=launches,
-                    clocks=clocks, stats=st)
+                    clocks=clocks, stats=st, released=released)
 
     def roofline(storage, r):
         eb = 4 if storage == "f32" else 2
@@ -287,6 +291,21 @@ def run_gpu(args, world, rank, local):
         out["barrier_every_step"] = {"value": round(world * N * ksteps / (t * 1e-3) / 1e6, 1),
                                      "ms_per_step": round(t / ksteps, 5), "steps": ksteps,
                                      "relabel_every": 1}
+    if not args.no_growth and "f32" in results:
+        # nucleation/growth source (Sec. 2.1.3) on the same FP32 box: census with
+        # every relabel, one growth launch after every step
+        rate, budget = 100.0, 1e9
+        r = timed("f32", K, args.steps, min(args.warmup, 3), sample_clocks=False, growth=(rate, budget))
+        t = max_over_ranks(world, r["total_ms"], dev)
+        base = results["f32"]
+        out["growth"] = {"value": round(world * N * args.steps / (t * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                         "ms_per_step": round(t / args.steps, 5),
+                         "release_per_step": rate, "released": r["released"],
+                         "extra_ms_per_plain_step": round(statistics.mean(r["plain"]) - statistics.mean(base["plain"]), 5)
+                         if r["plain"] and base["plain"] else None,
+                         "extra_ms_per_relabel_step": round(statistics.mean(r["relab"]) - statistics.mean(base["relab"]), 5)
+                         if r["relab"] and base["relab"] else None,
+                         "storage": "f32", "gpu_launches": int(r["launches"])}
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, dev, n, bub, RL, RG, world)
     if not args.no_batch:
