@@ -62,6 +62,22 @@ class _State(C.Structure):
                 ("n_gas", C.c_int64), ("injected", C.c_double)]
 
 
+class Params2(C.Structure):
+    """Two-component (melt / gas lattices) parameters; see ``orc2_params``."""
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("barrier", C.c_int32),
+                ("relabel_every", C.c_int32), ("zone_radius", C.c_int32), ("reserved", C.c_int32),
+                ("tau_m", C.c_double), ("tau_g", C.c_double), ("G_mm", C.c_double),
+                ("G_mg", C.c_double), ("G_gg", C.c_double), ("rho0", C.c_double),
+                ("gas_threshold", C.c_double), ("rupture_eps", C.c_double)]
+
+
+class _State2(C.Structure):
+    _fields_ = [("fm", C.c_void_p), ("fg", C.c_void_p), ("fm_next", C.c_void_p), ("fg_next", C.c_void_p),
+                ("rm", C.c_void_p), ("rg", C.c_void_p), ("psim", C.c_void_p), ("psig", C.c_void_p),
+                ("pr", C.c_void_p), ("label", C.c_void_p), ("owner", C.c_void_p), ("sgn", C.c_void_p),
+                ("open", C.c_void_p), ("mask", C.c_void_p), ("t", C.c_int64), ("opened_total", C.c_int64)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -96,6 +112,16 @@ def lib():
             "orc_stats": (C.c_int32, [P, vp, vp, vp, vp, vp, vp, C.c_int32, C.c_double,
                                       C.c_double]),
         }
+        P2 = C.POINTER(Params2)
+        S2 = C.POINTER(_State2)
+        sig.update({
+            "orc2_pressure": (C.c_double, [P2, C.c_double, C.c_double]),
+            "orc2_init_state": (None, [P2, S2, vp, vp]),
+            "orc2_relabel": (None, [P2, S2]),
+            "orc2_step": (None, [P2, S2]),
+            "orc2_run": (None, [P2, S2, C.c_int64]),
+            "orc2_fields": (None, [P2, S2, vp, vp, vp, vp, vp]),
+        })
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
             fn.restype = res
@@ -315,3 +341,74 @@ class OracleSim:
         """Labels of the current density (the same threshold as the barrier)."""
         lib().orc_moments(C.byref(self.params), _p(self.f), _p(self.rho), None, None)
         return label(self.params, self.rho)
+
+
+def make_params2(nx, ny, *, tau_m=1.0, tau_g=1.0, G_mm=-5.5, G_mg=0.0, G_gg=0.0, rho0=1.0, barrier=False,
+                 relabel_every=1, zone_radius=4, gas_threshold=None, rupture_eps=1e-6) -> Params2:
+    if gas_threshold is None:
+        gas_threshold = RHO_CRITICAL
+    return Params2(nx=nx, ny=ny, barrier=int(bool(barrier)), relabel_every=relabel_every,
+                   zone_radius=zone_radius, reserved=0, tau_m=tau_m, tau_g=tau_g, G_mm=G_mm, G_mg=G_mg,
+                   G_gg=G_gg, rho0=rho0, gas_threshold=gas_threshold, rupture_eps=rupture_eps)
+
+
+class OracleSim2:
+    """Two-component box (melt and gas lattices) advanced by the FP64 oracle."""
+
+    def __init__(self, params: Params2):
+        self.params = params
+        nx, ny = params.nx, params.ny
+        self.fm = np.zeros((9, ny, nx), np.float64)
+        self.fg = np.zeros_like(self.fm)
+        self.fm_next = np.zeros_like(self.fm)
+        self.fg_next = np.zeros_like(self.fm)
+        self.rm = np.zeros((ny, nx), np.float64)
+        self.rg = np.zeros_like(self.rm)
+        self.psim = np.zeros_like(self.rm)
+        self.psig = np.zeros_like(self.rm)
+        self.pr = np.zeros_like(self.rm)
+        self.label = np.full((ny, nx), -1, np.int32)
+        self.owner = np.full((ny, nx), -1, np.int32)
+        self.sgn = np.zeros((ny, nx), np.int8)
+        self.open = np.zeros((ny, nx), np.uint8)
+        self.mask = np.zeros((ny, nx), np.uint8)
+        self._s = _State2(fm=_p(self.fm), fg=_p(self.fg), fm_next=_p(self.fm_next), fg_next=_p(self.fg_next),
+                          rm=_p(self.rm), rg=_p(self.rg), psim=_p(self.psim), psig=_p(self.psig), pr=_p(self.pr),
+                          label=_p(self.label), owner=_p(self.owner), sgn=_p(self.sgn), open=_p(self.open),
+                          mask=_p(self.mask), t=0, opened_total=0)
+
+    def init_density(self, rho_m: np.ndarray, rho_g: np.ndarray) -> None:
+        rho_m = np.ascontiguousarray(rho_m, dtype=np.float64)
+        rho_g = np.ascontiguousarray(rho_g, dtype=np.float64)
+        assert rho_m.shape == rho_g.shape == (self.params.ny, self.params.nx)
+        lib().orc2_init_state(C.byref(self.params), C.byref(self._s), _p(rho_m), _p(rho_g))
+
+    def step(self, n: int = 1) -> None:
+        lib().orc2_run(C.byref(self.params), C.byref(self._s), int(n))
+
+    @property
+    def t(self) -> int:
+        return int(self._s.t)
+
+    @property
+    def opened_total(self) -> int:
+        return int(self._s.opened_total)
+
+    def fields(self) -> dict:
+        ny, nx = self.params.ny, self.params.nx
+        out = {k: np.empty((ny, nx)) for k in ("rho_m", "rho_g", "ux", "uy", "p")}
+        lib().orc2_fields(C.byref(self.params), C.byref(self._s), _p(out["rho_m"]), _p(out["rho_g"]),
+                          _p(out["ux"]), _p(out["uy"]), _p(out["p"]))
+        return out
+
+    def masses(self):
+        return float(np.sum(self.fm)), float(np.sum(self.fg))
+
+    def momentum(self):
+        fl = self.fields()
+        r = fl["rho_m"] + fl["rho_g"]
+        return float(np.sum(r * fl["ux"])), float(np.sum(r * fl["uy"]))
+
+
+def pressure2(params: Params2, rho_m: float, rho_g: float) -> float:
+    return lib().orc2_pressure(C.byref(params), float(rho_m), float(rho_g))

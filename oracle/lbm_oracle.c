@@ -281,9 +281,10 @@ static int barrier_direction(const orc_params *p, const int32_t *owner, int x, i
   return 0;
 }
 
-/* Rupture test of Eq. 41 under the reading given in the header. */
-void orc_rupture(const orc_params *p, const double *rho, const int32_t *owner, int8_t *sgn,
-                 uint8_t *open, int32_t *n_opened) {
+/* Rupture test of Eq. 41 under the reading given in the header, on a
+ * pressure field pr. */
+static void rupture_on_pressure(const orc_params *p, const double *pr, const int32_t *owner, int8_t *sgn,
+                                uint8_t *open, int32_t *n_opened) {
   const int nx = p->nx, ny = p->ny;
   int32_t opened = 0;
 #pragma omp parallel for schedule(static) reduction(+ : opened)
@@ -297,8 +298,7 @@ void orc_rupture(const orc_params *p, const double *rho, const int32_t *owner, i
       }
       size_t cp = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
       size_t cm = (size_t)wrap(y - EY[i], ny) * nx + wrap(x - EX[i], nx);
-      double d2 = orc_pressure(rho[cp], p->G, p->rho0) - 2.0 * orc_pressure(rho[c], p->G, p->rho0) +
-                  orc_pressure(rho[cm], p->G, p->rho0);
+      double d2 = pr[cp] - 2.0 * pr[c] + pr[cm];
       int s = (d2 > 0.0) - (d2 < 0.0);
       if (p->rupture_eps >= 0.0 && !open[c]) {
         if (fabs(d2) <= p->rupture_eps || (sgn[c] != 0 && s != sgn[c])) {
@@ -309,6 +309,16 @@ void orc_rupture(const orc_params *p, const double *rho, const int32_t *owner, i
       sgn[c] = (int8_t)s;
     }
   *n_opened = opened;
+}
+
+/* Rupture test with the pressure of Eq. 29 from the density rho. */
+void orc_rupture(const orc_params *p, const double *rho, const int32_t *owner, int8_t *sgn,
+                 uint8_t *open, int32_t *n_opened) {
+  const size_t N = (size_t)p->nx * p->ny;
+  double *pr = (double *)malloc(N * sizeof(double));
+  for (size_t c = 0; c < N; ++c) pr[c] = orc_pressure(rho[c], p->G, p->rho0);
+  rupture_on_pressure(p, pr, owner, sgn, open, n_opened);
+  free(pr);
 }
 
 /* Blocked-edge mask: bit i-1 of mask(x) is set when owner(x) and owner(x+e_i)
@@ -589,4 +599,218 @@ int32_t orc_stats(const orc_params *p, const int32_t *label, double *gas_fractio
   *mean_diameter = nb > 0 ? sum_d / nb : 0.0;
   free(count);
   return nb;
+}
+
+/* ------------------------------------------------------------------------
+ * Two-component variant (melt m and gas g lattices; Sec. 2.1.5, the
+ * two-lattice description and the coupled velocities of Eqs. 36-40).
+ *
+ * Readings (the paper's formulas there are garbled; each is listed in the
+ * design notes):
+ *   - each component sigma has its own D2Q9 populations, BGK time tau_sigma
+ *     and pseudopotential psi_sigma = rho0 (1 - exp(-rho_sigma / rho0));
+ *   - force on sigma: F_sigma(x) = -psi_sigma(x) sum_s' G_{sigma s'} S_s'(x),
+ *     S_s'(x) = sum_i w_i psi~_s'(x + e_i) e_i, with G_mm (melt cohesion, the
+ *     single-component G), G_mg = G_gm (melt-gas repulsion) and G_gg, and the
+ *     barrier substitution psi~ = psi_s'(x) across a blocked edge;
+ *   - common velocity ("u_total", read as momentum over total density):
+ *     u' = (sum_s j_s / tau_s) / (sum_s rho_s / tau_s), which is
+ *     (j_m + j_g) / (rho_m + rho_g) for equal relaxation times;
+ *   - equilibrium velocity of each component u_s = u' + tau_s F_s / rho_s
+ *     (Eqs. 39-40; a component with rho_s = 0 has f^eq = 0 and takes u');
+ *   - pressure p = (rho_m + rho_g)/3 + (1/6) sum_{s,s'} G_{ss'} psi_s psi_s'
+ *     (Eq. 29 summed over the pairs; with no gas it is Eq. 29);
+ *   - bubbles (for the barrier) are the 4-connected regions of melt density
+ *     below gas_threshold; the rupture test uses the pressure above.
+ * With an empty gas lattice the step is the single-component step.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t nx, ny;
+  int32_t barrier, relabel_every, zone_radius, reserved;
+  double tau_m, tau_g;
+  double G_mm, G_mg, G_gg;
+  double rho0;
+  double gas_threshold; /* gas point iff melt density < this */
+  double rupture_eps;
+} orc2_params;
+
+typedef struct {
+  double *fm, *fg;           /* [9][ny][nx] incoming populations per component */
+  double *fm_next, *fg_next; /* scratch */
+  double *rm, *rg, *psim, *psig, *pr; /* [ny][nx] scratch */
+  int32_t *label, *owner;
+  int8_t *sgn;
+  uint8_t *open, *mask;
+  int64_t t, opened_total;
+} orc2_state;
+
+static orc_params orc2_as_single(const orc2_params *q) {
+  orc_params p;
+  memset(&p, 0, sizeof(p));
+  p.nx = q->nx;
+  p.ny = q->ny;
+  p.barrier = q->barrier;
+  p.relabel_every = q->relabel_every;
+  p.zone_radius = q->zone_radius;
+  p.tau = q->tau_m;
+  p.G = q->G_mm;
+  p.rho0 = q->rho0;
+  p.gas_threshold = q->gas_threshold;
+  p.rupture_eps = q->rupture_eps;
+  return p;
+}
+
+/* Mixture pressure of the reading above. */
+double orc2_pressure(const orc2_params *q, double rm, double rg) {
+  const double a = orc_psi(rm, q->rho0), b = orc_psi(rg, q->rho0);
+  return (rm + rg) / 3.0 + (q->G_mm * a * a + 2.0 * q->G_mg * a * b + q->G_gg * b * b) / 6.0;
+}
+
+/* S(x) = sum_i w_i psi~(x + e_i) e_i with the barrier substitution. */
+static void neighbour_sum(int nx, int ny, const double *psi, const uint8_t *mask, size_t c, int x, int y,
+                          double *sx, double *sy) {
+  double ax = 0.0, ay = 0.0;
+  for (int i = 1; i < Q; ++i) {
+    size_t nb = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+    double v = psi[nb];
+    if (mask && ((mask[c] >> (i - 1)) & 1u)) v = psi[c];
+    ax += WT[i] * v * EX[i];
+    ay += WT[i] * v * EY[i];
+  }
+  *sx = ax;
+  *sy = ay;
+}
+
+void orc2_init_state(const orc2_params *q, orc2_state *s, const double *rho_m, const double *rho_g) {
+  const size_t N = (size_t)q->nx * q->ny;
+  for (int i = 0; i < Q; ++i)
+    for (size_t c = 0; c < N; ++c) {
+      s->fm[i * N + c] = WT[i] * rho_m[c];
+      s->fg[i * N + c] = WT[i] * rho_g[c];
+    }
+  memset(s->sgn, 0, N);
+  memset(s->open, 0, N);
+  memset(s->mask, 0, N);
+  for (size_t c = 0; c < N; ++c) s->label[c] = s->owner[c] = -1;
+  s->t = 0;
+  s->opened_total = 0;
+}
+
+/* Barrier pipeline on the melt density (labels, owners, mask) with the
+ * rupture test on the mixture pressure. */
+void orc2_relabel(const orc2_params *q, orc2_state *s) {
+  const orc_params p = orc2_as_single(q);
+  const size_t N = (size_t)q->nx * q->ny;
+  orc_moments(&p, s->fm, s->rm, NULL, NULL);
+  orc_moments(&p, s->fg, s->rg, NULL, NULL);
+  for (size_t c = 0; c < N; ++c) s->pr[c] = orc2_pressure(q, s->rm[c], s->rg[c]);
+  orc_label(&p, s->rm, s->label);
+  orc_owner(&p, s->label, s->owner);
+  int32_t opened = 0;
+  rupture_on_pressure(&p, s->pr, s->owner, s->sgn, s->open, &opened);
+  orc_mask(&p, s->owner, s->open, s->mask);
+  s->opened_total += opened;
+}
+
+/* One step of both lattices. */
+void orc2_step(const orc2_params *q, orc2_state *s) {
+  const int nx = q->nx, ny = q->ny;
+  const size_t N = (size_t)nx * ny;
+  const orc_params p = orc2_as_single(q);
+  const int barrier = q->barrier != 0;
+  if (barrier && s->t % q->relabel_every == 0) orc2_relabel(q, s);
+  const uint8_t *mask = barrier ? s->mask : NULL;
+  orc_moments(&p, s->fm, s->rm, NULL, NULL);
+  orc_moments(&p, s->fg, s->rg, NULL, NULL);
+  for (size_t c = 0; c < N; ++c) {
+    s->psim[c] = orc_psi(s->rm[c], q->rho0);
+    s->psig[c] = orc_psi(s->rg[c], q->rho0);
+  }
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const size_t c = (size_t)y * nx + x;
+      double rm = 0.0, rg = 0.0, jxm = 0.0, jym = 0.0, jxg = 0.0, jyg = 0.0;
+      for (int i = 0; i < Q; ++i) {
+        const double a = s->fm[i * N + c], b = s->fg[i * N + c];
+        rm += a;
+        rg += b;
+        jxm += EX[i] * a;
+        jym += EY[i] * a;
+        jxg += EX[i] * b;
+        jyg += EY[i] * b;
+      }
+      double smx, smy, sgx, sgy;
+      neighbour_sum(nx, ny, s->psim, mask, c, x, y, &smx, &smy);
+      neighbour_sum(nx, ny, s->psig, mask, c, x, y, &sgx, &sgy);
+      const double Fmx = -s->psim[c] * (q->G_mm * smx + q->G_mg * sgx);
+      const double Fmy = -s->psim[c] * (q->G_mm * smy + q->G_mg * sgy);
+      const double Fgx = -s->psig[c] * (q->G_mg * smx + q->G_gg * sgx);
+      const double Fgy = -s->psig[c] * (q->G_mg * smy + q->G_gg * sgy);
+      const double den = rm / q->tau_m + rg / q->tau_g;
+      const double ux = (jxm / q->tau_m + jxg / q->tau_g) / den;
+      const double uy = (jym / q->tau_m + jyg / q->tau_g) / den;
+      double um_x = ux, um_y = uy, ug_x = ux, ug_y = uy;
+      if (rm > 0.0) {
+        um_x += q->tau_m * Fmx / rm;
+        um_y += q->tau_m * Fmy / rm;
+      }
+      if (rg > 0.0) {
+        ug_x += q->tau_g * Fgx / rg;
+        ug_y += q->tau_g * Fgy / rg;
+      }
+      double feq_m[Q], feq_g[Q];
+      orc_equilibrium(rm, um_x, um_y, feq_m);
+      orc_equilibrium(rg, ug_x, ug_y, feq_g);
+      for (int i = 0; i < Q; ++i) {
+        const size_t dst = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+        const double a = s->fm[i * N + c], b = s->fg[i * N + c];
+        s->fm_next[i * N + dst] = a - (a - feq_m[i]) / q->tau_m;
+        s->fg_next[i * N + dst] = b - (b - feq_g[i]) / q->tau_g;
+      }
+    }
+  memcpy(s->fm, s->fm_next, Q * N * sizeof(double));
+  memcpy(s->fg, s->fg_next, Q * N * sizeof(double));
+  s->t += 1;
+}
+
+void orc2_run(const orc2_params *q, orc2_state *s, int64_t nsteps) {
+  for (int64_t k = 0; k < nsteps; ++k) orc2_step(q, s);
+}
+
+/* Diagnostics at the start of the current step: component densities, the
+ * physical common velocity u = (sum_s (j_s + F_s / 2)) / (rho_m + rho_g),
+ * and the mixture pressure. Any output may be NULL. */
+void orc2_fields(const orc2_params *q, orc2_state *s, double *rho_m, double *rho_g, double *ux, double *uy,
+                 double *pr) {
+  const int nx = q->nx, ny = q->ny;
+  const size_t N = (size_t)nx * ny;
+  const orc_params p = orc2_as_single(q);
+  const uint8_t *mask = q->barrier ? s->mask : NULL;
+  orc_moments(&p, s->fm, s->rm, NULL, NULL);
+  orc_moments(&p, s->fg, s->rg, NULL, NULL);
+  for (size_t c = 0; c < N; ++c) {
+    s->psim[c] = orc_psi(s->rm[c], q->rho0);
+    s->psig[c] = orc_psi(s->rg[c], q->rho0);
+  }
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const size_t c = (size_t)y * nx + x;
+      double jx = 0.0, jy = 0.0;
+      for (int i = 0; i < Q; ++i) {
+        jx += EX[i] * (s->fm[i * N + c] + s->fg[i * N + c]);
+        jy += EY[i] * (s->fm[i * N + c] + s->fg[i * N + c]);
+      }
+      double smx, smy, sgx, sgy;
+      neighbour_sum(nx, ny, s->psim, mask, c, x, y, &smx, &smy);
+      neighbour_sum(nx, ny, s->psig, mask, c, x, y, &sgx, &sgy);
+      const double Fx = -s->psim[c] * (q->G_mm * smx + q->G_mg * sgx) - s->psig[c] * (q->G_mg * smx + q->G_gg * sgx);
+      const double Fy = -s->psim[c] * (q->G_mm * smy + q->G_mg * sgy) - s->psig[c] * (q->G_mg * smy + q->G_gg * sgy);
+      const double r = s->rm[c] + s->rg[c];
+      if (rho_m) rho_m[c] = s->rm[c];
+      if (rho_g) rho_g[c] = s->rg[c];
+      if (ux) ux[c] = (jx + 0.5 * Fx) / r;
+      if (uy) uy[c] = (jy + 0.5 * Fy) / r;
+      if (pr) pr[c] = orc2_pressure(q, s->rm[c], s->rg[c]);
+    }
 }

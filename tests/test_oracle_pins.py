@@ -650,3 +650,125 @@ def test_nucleation_schedule_is_seeded_and_in_range():
     assert a[:, 0].min() >= 0 and a[:, 0].max() < 500 and np.all(a[:, 0] == np.floor(a[:, 0]))
     assert np.all((a[:, 1] >= 0) & (a[:, 1] < 200) & (a[:, 2] >= 0) & (a[:, 2] < 100))
     assert np.all((a[:, 3] >= 3.0) & (a[:, 3] <= 8.0))
+
+
+# ------------------------------------------- two-component variant (melt / gas lattices)
+def test_two_component_with_empty_gas_lattice_is_the_single_component_step():
+    """With no gas component the coupled step reduces to the single-component
+    step (u' = j/rho, the melt force uses G_mm only)."""
+    nx, ny = 64, 48
+    rho = inputs.noise_density(nx, ny, seed=1)
+    two = O.OracleSim2(O.make_params2(nx, ny, G_mm=-5.5, G_mg=2.0))
+    two.init_density(rho, np.zeros_like(rho))
+    one = O.OracleSim(O.make_params(nx, ny, G=-5.5))
+    one.init_density(rho)
+    two.step(100)
+    one.step(100)
+    assert np.abs(two.fm - one.f).max() < 1e-12
+    assert not two.fg.any()
+
+
+def test_two_component_ideal_mixture_sums_to_one_lattice():
+    """With all couplings zero and equal relaxation times the sum of the two
+    lattices obeys the single-component BGK step on the summed density
+    (f^eq is linear in rho at the common velocity)."""
+    nx, ny = 48, 40
+    a = inputs.noise_density(nx, ny, seed=3, rho_mean=0.5)
+    b = inputs.noise_density(nx, ny, seed=4, rho_mean=0.9)
+    two = O.OracleSim2(O.make_params2(nx, ny, tau_m=0.8, tau_g=0.8, G_mm=0.0, G_mg=0.0, G_gg=0.0))
+    two.init_density(a, b)
+    one = O.OracleSim(O.make_params(nx, ny, tau=0.8, G=0.0))
+    one.init_density(a + b)
+    two.step(50)
+    one.step(50)
+    assert np.abs(two.fm + two.fg - one.f).max() < 1e-13
+
+
+def test_two_component_swap_symmetry_bitwise():
+    """Exchanging the melt and gas roles (densities, relaxation times and the
+    self couplings) exchanges the results exactly."""
+    nx, ny = 40, 32
+    a = inputs.noise_density(nx, ny, seed=5, rho_mean=0.7)
+    b = inputs.noise_density(nx, ny, seed=6, rho_mean=0.6)
+    s1 = O.OracleSim2(O.make_params2(nx, ny, tau_m=1.0, tau_g=0.7, G_mm=-1.0, G_mg=2.5, G_gg=-0.5))
+    s2 = O.OracleSim2(O.make_params2(nx, ny, tau_m=0.7, tau_g=1.0, G_mm=-0.5, G_mg=2.5, G_gg=-1.0))
+    s1.init_density(a, b)
+    s2.init_density(b, a)
+    s1.step(30)
+    s2.step(30)
+    assert np.array_equal(s1.fm, s2.fg) and np.array_equal(s1.fg, s2.fm)
+
+
+def test_two_component_conservation_and_uniform_flow():
+    """Each lattice keeps its own mass; the mixture momentum sum_s (j_s +
+    F_s/2) is conserved (symmetric melt-gas coupling); a uniform mixture
+    moving at a uniform velocity stays as it is."""
+    nx, ny = 64, 64
+    a = inputs.noise_density(nx, ny, seed=7, rho_mean=0.7)
+    b = inputs.noise_density(nx, ny, seed=8, rho_mean=0.7)
+    s = O.OracleSim2(O.make_params2(nx, ny, tau_m=1.0, tau_g=0.9, G_mm=-1.0, G_mg=3.0, G_gg=0.0))
+    s.init_density(a, b)
+    m0, p0 = s.masses(), s.momentum()
+    s.step(500)
+    m1, p1 = s.masses(), s.momentum()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-12 and abs(m1[1] - m0[1]) / m0[1] < 1e-12
+    tot = m0[0] + m0[1]
+    assert abs(p1[0] - p0[0]) < 1e-12 * tot and abs(p1[1] - p0[1]) < 1e-12 * tot
+    u = O.OracleSim2(O.make_params2(16, 12, G_mm=-5.5, G_mg=3.0))
+    u.init_density(np.full((12, 16), 0.6), np.full((12, 16), 0.3))
+    feq_m, feq_g = O.equilibrium(0.6, 0.05, -0.02), O.equilibrium(0.3, 0.05, -0.02)
+    u.fm[...] = feq_m[:, None, None]
+    u.fg[...] = feq_g[:, None, None]
+    u.step(20)
+    assert np.abs(u.fm - feq_m[:, None, None]).max() < 1e-15
+    assert np.abs(u.fg - feq_g[:, None, None]).max() < 1e-15
+
+
+def test_two_component_demixing_needs_enough_repulsion():
+    """A 50/50 mixture at rho = 0.7 each separates into melt-rich and
+    gas-rich regions under a strong melt-gas repulsion and stays mixed under
+    a weak one."""
+    n = 64
+    a = inputs.noise_density(n, n, seed=1, rho_mean=0.7)
+    b = inputs.noise_density(n, n, seed=2, rho_mean=0.7)
+    spread = {}
+    for G in (1.0, 3.0):
+        s = O.OracleSim2(O.make_params2(n, n, G_mm=0.0, G_mg=G))
+        s.init_density(a, b)
+        s.step(3000)
+        r = s.fields()["rho_m"]
+        spread[G] = r.max() - r.min()
+    assert spread[1.0] < 1e-3 and spread[3.0] > 1.0
+
+
+def test_two_component_pressure_reduces_to_eq29():
+    P = O.make_params2(8, 8, G_mm=-5.5, G_mg=2.0, G_gg=0.5)
+    for r in (0.1, 0.7, 2.3):
+        assert O.pressure2(P, r, 0.0) == pytest.approx(O.pressure(r, -5.5), abs=1e-15)
+    # symmetric cross term: p(rm, rg) = (rm + rg)/3 + (G_mm a^2 + 2 G_mg a b + G_gg b^2)/6
+    a, b = O.psi(0.8), O.psi(0.3)
+    assert O.pressure2(P, 0.8, 0.3) == pytest.approx(1.1 / 3 + (-5.5 * a * a + 4.0 * a * b + 0.5 * b * b) / 6,
+                                                     abs=1e-15)
+
+
+def test_two_component_bubbles_barrier_and_rupture():
+    """Two gas bubbles (melt vapour plus a gas component) with a 3-cell film:
+    without the barrier they merge; with it and rupture disabled the film
+    holds; with the rupture criterion a film cell opens and they merge
+    (the paper's Fig. 7 story, in the two-lattice model)."""
+    nx, ny, R, gap = 160, 80, 12, 3.0
+    b = [[nx / 2 - R - gap / 2, ny / 2, R], [nx / 2 + R + gap / 2, ny / 2, R]]
+    rm = O.init_bubbles(O.make_params(nx, ny), b, inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, 4.0)
+    inside = (inputs.RHO_LIQ_G55 - rm) / (inputs.RHO_LIQ_G55 - inputs.RHO_GAS_G55)
+    rg = 0.005 + 0.3 * inside
+    counts = {}
+    for barrier, eps in ((False, 1e-6), (True, -1.0), (True, 1e-6)):
+        s = O.OracleSim2(O.make_params2(nx, ny, G_mm=-5.5, G_mg=1.0, barrier=barrier, relabel_every=1,
+                                        rupture_eps=eps))
+        s.init_density(rm, rg)
+        s.step(500)
+        labels = O.label(O.make_params(nx, ny), s.fields()["rho_m"])
+        counts[(barrier, eps)] = (len(np.unique(labels[labels >= 0])), s.opened_total)
+    assert counts[(False, 1e-6)][0] == 1
+    assert counts[(True, -1.0)] == (2, 0)
+    assert counts[(True, 1e-6)][0] == 1 and counts[(True, 1e-6)][1] > 0
