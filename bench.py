@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-growth", action="store_true", help="skip the nucleation/growth leg")
+    ap.add_argument("--no-2c", action="store_true", help="skip the two-component leg")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-step-scale", type=float, default=0.1)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
@@ -306,6 +307,8 @@ def run_gpu(args, world, rank, local):
                          "extra_ms_per_relabel_step": round(statistics.mean(r["relab"]) - statistics.mean(base["relab"]), 5)
                          if r["relab"] and base["relab"] else None,
                          "storage": "f32", "gpu_launches": int(r["launches"])}
+    if not args.no_2c:
+        out["two_component"] = run_two_component(args, dev, n, bub, RL, RG, world, peak, peak_kind)
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, dev, n, bub, RL, RG, world)
     if not args.no_batch:
@@ -313,6 +316,60 @@ def run_gpu(args, world, rank, local):
     if not args.no_serve:
         cap = out.get("batched", {}).get("sequential", 45000.0) * 1e6
         out["served"] = run_served(args, dev, world, rank, cap)
+    return out
+
+
+def run_two_component(args, dev, n, bub, RL, RG, world, peak, peak_kind):
+    """Two-component variant (melt and gas lattices) on the benchmark box:
+    melt density of the foam, a gas component filling the bubbles (0.3 inside,
+    0.005 outside), G_mm = -5.5, G_mg = 1.0, FP32, barrier on, K as the main
+    leg. Roofline of the fused two-lattice step: 2 x 18 x 4 + 1 = 145 B/cell."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1708_01613_gb300 import Simulation, make_config
+
+    N = n * n
+    K = args.relabel_every
+    sim = Simulation(make_config(n, n, components=2, barrier=True, relabel_every=K, G_mg=1.0), device=dev)
+    prof = Simulation(make_config(n, n, barrier=False), device=dev)  # density of the foam, FP64 tanh profile
+    prof.init_bubbles(bub, RL, RG, 4.0)
+    rm = prof.read("rho", device=True)["rho"].to(torch.float64)
+    del prof
+    rg = 0.005 + 0.3 * (RL - rm) / (RL - RG)
+    sim.init_density(rm.cpu().numpy(), rg.cpu().numpy())
+    del rm, rg
+    sim.step(min(args.warmup, 3))
+    sim.sync()
+    stream = sim.stream
+    steps = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t_first = sim.steps_done
+    l0 = sim.kernel_launches
+    for k in range(steps):
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    sim.sync()
+    per = [a.elapsed_time(b) for a, b in ev]
+    plain = [d for k, d in enumerate(per) if (t_first + k) % K != 0]
+    kern_ms = statistics.mean(plain) if plain else sum(per) / steps
+    total = max_over_ranks(world, sum(per), dev)
+    bytes_cell = 2 * 18 * 4 + 1
+    achieved = bytes_cell * N / (kern_ms * 1e-3) / 1e9
+    out = {"value": round(world * N * steps / (total * 1e-3) / 1e6, 1), "unit": "MLUPS",
+           "ms_per_step": round(total / steps, 5), "storage": "f32", "components": 2,
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "algorithmic_bytes_per_cell": bytes_cell,
+                        "kernel": "k_step2_strip", "kernel_ms_avg": round(kern_ms, 5), "peak_kind": peak_kind},
+           "gpu_launches": int(sim.kernel_launches - l0)}
+    del sim
+    torch.cuda.empty_cache()
     return out
 
 

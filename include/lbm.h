@@ -68,7 +68,11 @@ enum {
   LBM_FIELD_OWNER = 1u << 5, /* int32: interaction-zone owner or -1 (barrier on) */
   LBM_FIELD_MASK = 1u << 6,  /* uint8: bit i-1 set = edge (x, x+e_i) blocked */
   LBM_FIELD_OPEN = 1u << 7,  /* uint8: 1 = cell has ruptured (barrier on) */
-  LBM_FIELD_POPS = 1u << 8   /* float32 [9][ny][nx]: incoming f_i of the next step */
+  LBM_FIELD_POPS = 1u << 8,  /* float32 [9][ny][nx] ([18][ny][nx] with two
+                                components, melt then gas): incoming f_i of
+                                the next step */
+  LBM_FIELD_RHO_GAS = 1u << 9 /* float32: gas-component density (two
+                                components; zeros otherwise) */
 };
 
 typedef struct {
@@ -88,6 +92,22 @@ typedef struct {
   double rho_ref;                /* reference density of 16-bit deviations */
   double gas_threshold;          /* gas iff rho < this (default ln 2) */
   double rupture_eps;            /* open when |D2| <= eps; eps < 0: never */
+  /* Two-component variant (Sec. 2.1.5, melt and gas lattices coupled every
+   * step; Eqs. 36-40). components = 2 adds a gas lattice: tau, G above are
+   * the melt's tau_m and self coupling G_mm; each component s feels
+   * F_s = -psi_s(x) sum_s' G_ss' sum_i w_i psi_s'(x + e_i) e_i (barrier
+   * substitution as for one component), the common velocity is
+   * u' = (sum_s j_s / tau_s) / (sum_s rho_s / tau_s) and the equilibrium
+   * velocity u' + tau_s F_s / rho_s. rho and the barrier act on the melt
+   * density; P and the rupture test use the mixture pressure
+   * (rho_m + rho_g)/3 + (G_mm psi_m^2 + 2 G_mg psi_m psi_g + G_gg psi_g^2)/6.
+   * Two components need FP32 storage, growth = 0 and, with the barrier,
+   * nx % 32 == 0 and ny % 8 == 0; they cannot join a batch. */
+  int32_t components;            /* 1 (default) or 2 */
+  int32_t reserved2;             /* must be 0 */
+  double tau_g;                  /* gas relaxation time > 0.5 */
+  double G_mg;                   /* melt-gas coupling (symmetric) */
+  double G_gg;                   /* gas self coupling */
 } lbm_config;
 
 typedef struct {
@@ -121,20 +141,23 @@ int lbm_create(const lbm_config* cfg, void* d_workspace, size_t bytes, void* cud
                lbm_handle** out);
 
 /* f_i = f_i^eq(rho, 0) = w_i rho from nx*ny FP64 densities (row-major),
- * read from host memory (src_is_device = 0) or device memory (1). Resets the
- * step counter, the rupture state and the error flags. */
+ * read from host memory (src_is_device = 0) or device memory (1); with two
+ * components, 2*nx*ny values: the melt densities, then the gas densities.
+ * Resets the step counter, the rupture state and the error flags. */
 int lbm_init_density(lbm_handle* h, const double* rho, int src_is_device);
 
 /* Same as lbm_init_density with rho made on the device from n bubbles
  * (host array): each cell takes the bubble whose surface is nearest,
  * s = min_k (|x - c_k|_torus - r_k), and
  * rho = (rho_l + rho_g)/2 + (rho_l - rho_g)/2 tanh(s / (width / 2)),
- * computed in FP64. n = 0 gives a uniform liquid. */
+ * computed in FP64. n = 0 gives a uniform liquid. One component only
+ * (LBM_ENOTSUP with two). */
 int lbm_init_bubbles(lbm_handle* h, const lbm_bubble* b, int32_t n, double rho_l, double rho_g,
                      double width);
 
-/* Loads incoming populations f[9][ny][nx] (float32, host or device) as the
- * state of the next step (bitwise resume for F32 storage). */
+/* Loads incoming populations f[9][ny][nx] ([18][ny][nx] with two
+ * components, melt then gas; float32, host or device) as the state of the
+ * next step (bitwise resume for F32 storage). */
 int lbm_load_populations(lbm_handle* h, const float* f, int src_is_device);
 
 /* Enqueues nsteps time steps (each: barrier pipeline when t % K == 0, then
@@ -170,7 +193,8 @@ size_t lbm_fields_bytes(const lbm_handle* h, uint32_t fields);
 int lbm_read_fields(lbm_handle* h, uint32_t fields, void* dst, size_t dst_bytes,
                     int dst_is_device);
 
-/* FP64 sum of rho over the box, reduced in a fixed order. Synchronises. */
+/* FP64 sum of rho over the box (of both components with two), reduced in
+ * a fixed order. Synchronises. */
 int lbm_mass(lbm_handle* h, double* out);
 
 /* Nucleation (Sec. 2.1.3, "Random Nucleation" of the main flowchart):

@@ -39,6 +39,16 @@ bool valid_config(const lbm_config* c, char* why, size_t n) {
   if (c->stop_on_first_rupture != 0 && c->stop_on_first_rupture != 1)
     return snprintf(why, n, "stop_on_first_rupture must be 0 or 1"), false;
   if (c->growth != 0 && c->growth != 1) return snprintf(why, n, "growth must be 0 or 1"), false;
+  if (c->components != 1 && c->components != 2) return snprintf(why, n, "components must be 1 or 2"), false;
+  if (c->reserved2 != 0) return snprintf(why, n, "reserved2 must be 0"), false;
+  if (c->components == 2) {
+    if (c->storage != LBM_F32) return snprintf(why, n, "two components need FP32 storage"), false;
+    if (c->growth) return snprintf(why, n, "two components do not take the growth source"), false;
+    if (!(c->tau_g > 0.5) || !isfinite(c->tau_g)) return snprintf(why, n, "tau_g must be > 0.5"), false;
+    if (!isfinite(c->G_mg) || !isfinite(c->G_gg)) return snprintf(why, n, "G_mg, G_gg must be finite"), false;
+    if (c->barrier && !relabel_tiled_ok(c->nx, c->ny, c->zone_radius))
+      return snprintf(why, n, "two components with the barrier need nx %% 32 == 0, ny %% 8 == 0, R_z <= 16"), false;
+  }
   if (!(c->tau > 0.5) || !isfinite(c->tau)) return snprintf(why, n, "tau must be > 0.5"), false;
   if (!isfinite(c->G)) return snprintf(why, n, "G must be finite"), false;
   if (!(c->rho0 > 0.0) || !isfinite(c->rho0)) return snprintf(why, n, "rho0 must be > 0"), false;
@@ -57,8 +67,9 @@ Layout layout_for(const lbm_config& c) {
     return o;
   };
   const size_t eb = (size_t)storage_bytes(c.storage);
-  L.pops[0] = take(Q * N * eb);
-  L.pops[1] = take(Q * N * eb);
+  const size_t comps = c.components == 2 ? 2 : 1;
+  L.pops[0] = take(comps * Q * N * eb);
+  L.pops[1] = take(comps * Q * N * eb);
   L.rho = take(4 * N);
   L.label = take(4 * N);
   if (c.barrier) {
@@ -72,6 +83,7 @@ Layout layout_for(const lbm_config& c) {
     L.rbox = take(sizeof(RelabelBox) + 2 * sizeof(RelabelEntry));
   }
   if (c.growth) L.gas_list = take(4 * N);
+  if (c.components == 2 && c.barrier) L.pr = take(4 * N);
   L.flags = take(sizeof(int) * FLAG_COUNT);
   L.nparts = mass_partials_needed();
   L.partials = take(sizeof(double) * L.nparts);
@@ -102,6 +114,33 @@ int fail(lbm_handle* h, int code, const char* fmt, ...) {
     if (e_ != cudaSuccess)                                                              \
       return fail((h), LBM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));             \
   } while (0)
+
+// Buffer `buf`'s planes of component k (two-component boxes are FP32).
+void* component_pops(lbm_handle* h, int buf, int k) {
+  return static_cast<char*>(h->pops(buf)) + (size_t)k * Q * h->N() * storage_bytes(h->cfg.storage);
+}
+
+Step2Params step2_params(lbm_handle* h) {
+  const lbm_config& c = h->cfg;
+  Step2Params q{};
+  q.src = h->pops(h->cur);
+  q.dst = h->pops(1 - h->cur);
+  q.mask = c.barrier ? h->mask() : nullptr;
+  q.flags = h->flags();
+  q.nx = c.nx;
+  q.ny = c.ny;
+  q.N = (long long)h->N();
+  q.tau_m = (float)c.tau;
+  q.tau_g = (float)c.tau_g;
+  q.inv_tau_m = (float)(1.0 / c.tau);
+  q.inv_tau_g = (float)(1.0 / c.tau_g);
+  q.G_mm = (float)c.G;
+  q.G_mg = (float)c.G_mg;
+  q.G_gg = (float)c.G_gg;
+  q.rho0 = (float)c.rho0;
+  q.inv_rho0 = (float)(1.0 / c.rho0);
+  return q;
+}
 
 FieldParams field_params(lbm_handle* h) {
   FieldParams fp{};
@@ -199,12 +238,14 @@ size_t field_bytes(const lbm_handle* h, uint32_t bit) {
     case LBM_FIELD_OWNER: return 4 * N;
     case LBM_FIELD_MASK:
     case LBM_FIELD_OPEN: return N;
-    case LBM_FIELD_POPS: return 4 * Q * N;
+    case LBM_FIELD_POPS: return 4 * Q * N * h->comps();
+    case LBM_FIELD_RHO_GAS: return 4 * N;
     default: return 0;
   }
 }
 
-constexpr uint32_t kAllFields = (LBM_FIELD_POPS << 1) - 1;
+constexpr uint32_t kLastField = LBM_FIELD_RHO_GAS;
+constexpr uint32_t kAllFields = (kLastField << 1) - 1;
 
 }  // namespace
 
@@ -243,6 +284,9 @@ RelabelBox handle_relabel_box(lbm_handle* h) {
   b.tile_prev = h->tiles(2);
   b.tile_list = reinterpret_cast<int*>(h->ws + h->L.tile_list);
   b.flags = h->flags();
+  b.pr = h->pr();
+  b.G_mg = (float)c.G_mg;
+  b.G_gg = (float)c.G_gg;
   b.nx = c.nx;
   b.ny = c.ny;
   b.ntx = c.nx / kRelabelTileX;
@@ -298,6 +342,8 @@ void lbm_config_default(lbm_config* cfg) {
   cfg->rho_ref = 1.0;
   cfg->gas_threshold = log(2.0);
   cfg->rupture_eps = 1e-6;
+  cfg->components = 1;
+  cfg->tau_g = 1.0;
 }
 
 size_t lbm_workspace_bytes(const lbm_config* cfg) {
@@ -348,19 +394,22 @@ int lbm_init_density(lbm_handle* h, const double* rho, int src_is_device) {
   int rc = select_device(h);
   if (rc) return rc;
   const double* src = rho;
+  const int comps = h->comps();
   if (!src_is_device) {
     void* stage = h->pops(1 - h->cur);
-    CUDA_TRY(h, cudaMemcpyAsync(stage, rho, 8 * h->N(), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(stage, rho, 8 * h->N() * comps, cudaMemcpyHostToDevice, h->stream));
     src = static_cast<const double*>(stage);
   }
-  CUDA_TRY(h, launch_init_from_rho(h->cfg.storage, h->pops(h->cur), src, h->cfg.nx, h->cfg.ny, h->wref,
-                                   h->stream));
+  for (int k = 0; k < comps; ++k)  // component k's planes follow the previous component's nine
+    CUDA_TRY(h, launch_init_from_rho(h->cfg.storage, component_pops(h, h->cur, k), src + (size_t)k * h->N(),
+                                     h->cfg.nx, h->cfg.ny, h->wref, h->stream));
   return reset_state(h);
 }
 
 int lbm_init_bubbles(lbm_handle* h, const lbm_bubble* b, int32_t n, double rho_l, double rho_g,
                      double width) {
   if (!h) return LBM_EINVAL;
+  if (h->comps() != 1) return fail(h, LBM_ENOTSUP, "bubble initialisation is for one component");
   if (n < 0 || (n > 0 && !b)) return fail(h, LBM_EINVAL, "bad bubble list");
   if (!(width > 0.0) || !isfinite(rho_l) || !isfinite(rho_g))
     return fail(h, LBM_EINVAL, "width must be > 0 and densities finite");
@@ -391,15 +440,15 @@ int lbm_load_populations(lbm_handle* h, const float* f, int src_is_device) {
   int rc = select_device(h);
   if (rc) return rc;
   const size_t N = h->N();
-  for (int i = 0; i < Q; ++i) {
-    const float* plane = f + (size_t)i * N;
+  for (int pl = 0; pl < Q * h->comps(); ++pl) {
+    const float* plane = f + (size_t)pl * N;
     if (!src_is_device) {
       float* stage = static_cast<float*>(h->pops(1 - h->cur));
       CUDA_TRY(h, cudaMemcpyAsync(stage, plane, 4 * N, cudaMemcpyHostToDevice, h->stream));
       plane = stage;
     }
-    CUDA_TRY(h, launch_load_plane(h->cfg.storage, h->pops(h->cur), plane, i, h->cfg.nx, h->cfg.ny,
-                                  h->wref, h->stream));
+    CUDA_TRY(h, launch_load_plane(h->cfg.storage, component_pops(h, h->cur, pl / Q), plane, pl % Q, h->cfg.nx,
+                                  h->cfg.ny, h->wref, h->stream));
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->halted = 0;
@@ -435,7 +484,12 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     }
     p.src = h->pops(h->cur);
     p.dst = h->pops(1 - h->cur);
-    CUDA_TRY(h, launch_step(c.storage, p, h->stream));
+    if (c.components == 2) {
+      const Step2Params q = step2_params(h);
+      CUDA_TRY(h, launch_step2(q, h->stream));
+    } else {
+      CUDA_TRY(h, launch_step(c.storage, p, h->stream));
+    }
     h->launches += 1;
     if (growing) {
       CUDA_TRY(h, launch_growth(c.storage, p.dst, h->gas_list(), h->flags() + FLAG_GAS, (long long)h->N(),
@@ -469,7 +523,7 @@ int lbm_halted(const lbm_handle* h) { return h ? h->halted : 0; }
 size_t lbm_fields_bytes(const lbm_handle* h, uint32_t fields) {
   if (!h || (fields & ~kAllFields)) return 0;
   size_t total = 0;
-  for (uint32_t bit = 1; bit <= LBM_FIELD_POPS; bit <<= 1)
+  for (uint32_t bit = 1; bit <= kLastField; bit <<= 1)
     if (fields & bit) total += field_bytes(h, bit);
   return total;
 }
@@ -486,16 +540,27 @@ int lbm_read_fields(lbm_handle* h, uint32_t fields, void* dst, size_t dst_bytes,
   float* stage = static_cast<float*>(h->pops(1 - h->cur));
   const cudaMemcpyKind d2x = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   CUDA_TRY(h, launch_density(fp, h->rho(), h->stream));
-  for (uint32_t bit = 1; bit <= LBM_FIELD_POPS; bit <<= 1) {
+  for (uint32_t bit = 1; bit <= kLastField; bit <<= 1) {
     if (!(fields & bit)) continue;
     const size_t nb = field_bytes(h, bit);
     switch (bit) {
       case LBM_FIELD_RHO:
       case LBM_FIELD_UX:
       case LBM_FIELD_UY:
-      case LBM_FIELD_P: {
+      case LBM_FIELD_P:
+      case LBM_FIELD_RHO_GAS: {
         float* target = dst_is_device ? reinterpret_cast<float*>(out) : stage;
-        CUDA_TRY(h, launch_fields(fp, h->rho(), h->mask(), bit, target, h->stream));
+        if (h->comps() == 2) {
+          const Step2Params q = step2_params(h);
+          CUDA_TRY(h, launch_fields2(q, bit == LBM_FIELD_RHO ? target : nullptr,
+                                     bit == LBM_FIELD_RHO_GAS ? target : nullptr, bit == LBM_FIELD_UX ? target : nullptr,
+                                     bit == LBM_FIELD_UY ? target : nullptr, bit == LBM_FIELD_P ? target : nullptr,
+                                     h->stream));
+        } else if (bit == LBM_FIELD_RHO_GAS) {
+          CUDA_TRY(h, cudaMemsetAsync(target, 0, nb, h->stream));
+        } else {
+          CUDA_TRY(h, launch_fields(fp, h->rho(), h->mask(), bit, target, h->stream));
+        }
         if (!dst_is_device) CUDA_TRY(h, cudaMemcpyAsync(out, stage, nb, d2x, h->stream));
         break;
       }
@@ -522,11 +587,13 @@ int lbm_read_fields(lbm_handle* h, uint32_t fields, void* dst, size_t dst_bytes,
         break;
       }
       case LBM_FIELD_POPS:
-        for (int i = 0; i < Q; ++i) {
-          float* target = dst_is_device ? reinterpret_cast<float*>(out + 4 * N * i) : stage;
-          CUDA_TRY(h, launch_pops_out(fp, i, target, h->stream));
+        for (int pl = 0; pl < Q * h->comps(); ++pl) {
+          FieldParams fk = fp;
+          fk.pops = component_pops(h, h->cur, pl / Q);
+          float* target = dst_is_device ? reinterpret_cast<float*>(out + 4 * N * pl) : stage;
+          CUDA_TRY(h, launch_pops_out(fk, pl % Q, target, h->stream));
           if (!dst_is_device)
-            CUDA_TRY(h, cudaMemcpyAsync(out + 4 * N * i, stage, 4 * N, d2x, h->stream));
+            CUDA_TRY(h, cudaMemcpyAsync(out + 4 * N * pl, stage, 4 * N, d2x, h->stream));
         }
         break;
     }
@@ -592,8 +659,15 @@ int lbm_mass(lbm_handle* h, double* out) {
   if (!out) return fail(h, LBM_EINVAL, "out is NULL");
   int rc = select_device(h);
   if (rc) return rc;
-  CUDA_TRY(h, launch_mass(field_params(h), h->partials(), h->L.nparts, h->scalars(), h->stream));
-  CUDA_TRY(h, cudaMemcpyAsync(out, h->scalars(), sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  double part[2] = {0.0, 0.0};
+  for (int k = 0; k < h->comps(); ++k) {
+    FieldParams fk = field_params(h);
+    fk.pops = component_pops(h, h->cur, k);
+    CUDA_TRY(h, launch_mass(fk, h->partials(), h->L.nparts, h->scalars(), h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(&part[k], h->scalars(), sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // the scalar slot is reused by the next component
+  }
+  *out = part[0] + part[1];
   return check_flags(h);
 }
 

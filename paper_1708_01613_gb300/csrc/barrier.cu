@@ -557,6 +557,18 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
   const float r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   const size_t c = r0 + x;
   B.rho[c] = r;
+  if (B.pr) {  // two components (FP32): the gas lattice follows the melt's nine planes
+    const float* pg = reinterpret_cast<const float*>(p) + (size_t)Q * N;
+    float g = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+      const int xs = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : x);
+      g += __ldg(pg + (size_t)i * N + row + xs);
+    }
+    const float a = B.rho0 * (1.0f - expf(-r / B.rho0)), b = B.rho0 * (1.0f - expf(-g / B.rho0));
+    B.pr[c] = (r + g) * (1.0f / 3.0f) + (B.G * a * a + 2.0f * B.G_mg * a * b + B.G_gg * b * b) * (1.0f / 6.0f);
+  }
   const bool gas = r < B.threshold;
   B.label[c] = gas ? (int32_t)c : -1;
   const int any = __syncthreads_or(gas);
@@ -716,9 +728,11 @@ __global__ void __launch_bounds__(kTX * kTY) kb_rupture(const RelabelBox* __rest
           ex = cx(i);
           ey = cy(i);
         }
-      const float pp = pressure_of(B.rho[(size_t)wrap1(y + ey, ny) * nx + wrap1(x + ex, nx)], B.G, B.rho0);
-      const float p0 = pressure_of(B.rho[c], B.G, B.rho0);
-      const float pm = pressure_of(B.rho[(size_t)wrap1(y - ey, ny) * nx + wrap1(x - ex, nx)], B.G, B.rho0);
+      const size_t cp = (size_t)wrap1(y + ey, ny) * nx + wrap1(x + ex, nx);
+      const size_t cm = (size_t)wrap1(y - ey, ny) * nx + wrap1(x - ex, nx);
+      const float pp = B.pr ? B.pr[cp] : pressure_of(B.rho[cp], B.G, B.rho0);
+      const float p0 = B.pr ? B.pr[c] : pressure_of(B.rho[c], B.G, B.rho0);
+      const float pm = B.pr ? B.pr[cm] : pressure_of(B.rho[cm], B.G, B.rho0);
       const float d2 = pp - 2.0f * p0 + pm;
       const int sg = (d2 > 0.f) - (d2 < 0.f);
       const int prevs = B.sgn[c];

@@ -346,7 +346,7 @@ int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, s
     if (h->in_batch) return LBM_EINVAL;
     if (h->cfg.storage != h0->cfg.storage || h->cfg.barrier != h0->cfg.barrier) return LBM_EINVAL;
     if (h->cfg.barrier && h->cfg.relabel_every != h0->cfg.relabel_every) return LBM_EINVAL;
-    if (h->cfg.stop_on_first_rupture || h->cfg.growth) return LBM_ENOTSUP;
+    if (h->cfg.stop_on_first_rupture || h->cfg.growth || h->cfg.components != 1) return LBM_ENOTSUP;
     if (h->device != h0->device || h->halted) return LBM_EINVAL;
     if (h->cfg.nx % 16 != 0) return LBM_ENOTSUP;  // bulk copies need 16-byte rows
   }

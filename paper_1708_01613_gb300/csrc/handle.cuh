@@ -11,8 +11,8 @@ namespace lbm {
 
 // Offsets of the slices of the caller's workspace.
 struct Layout {
-  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, tile_list, rbox, gas_list, flags, partials, scalars,
-      total;
+  size_t pops[2], rho, label, owner, mask, open, sgn, tiles, tile_list, rbox, gas_list, pr, flags, partials,
+      scalars, total;
   int nparts, ntiles;
 };
 
@@ -52,7 +52,10 @@ struct lbm_handle {
   double* partials() { return reinterpret_cast<double*>(ws + L.partials); }
   double* scalars() { return reinterpret_cast<double*>(ws + L.scalars); }
   size_t N() const { return (size_t)cfg.nx * cfg.ny; }
-  size_t pops_bytes() const { return lbm::Q * N() * lbm::storage_bytes(cfg.storage); }
+  int comps() const { return cfg.components == 2 ? 2 : 1; }
+  // bytes of one population buffer (all components)
+  size_t pops_bytes() const { return (size_t)lbm::Q * comps() * N() * lbm::storage_bytes(cfg.storage); }
+  float* pr() { return cfg.components == 2 && cfg.barrier ? reinterpret_cast<float*>(ws + L.pr) : nullptr; }
 };
 
 namespace lbm {

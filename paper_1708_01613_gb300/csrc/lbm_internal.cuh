@@ -111,6 +111,24 @@ struct StepParams {
   float wref[Q];         // w_i * rho_ref (16-bit deviation base)
 };
 
+// Two-component step (step2.cu): 18 FP32 planes per buffer, melt then gas.
+struct Step2Params {
+  const void* src;
+  void* dst;
+  const uint8_t* mask;  // nullptr: no barrier
+  int* flags;
+  int nx, ny;
+  long long N;
+  int rows_per_chunk;
+  float tau_m, tau_g, inv_tau_m, inv_tau_g;
+  float G_mm, G_mg, G_gg, rho0, inv_rho0;
+};
+cudaError_t launch_step2(const Step2Params& p, cudaStream_t s);
+// Melt/gas densities, mixture velocity (j + F/2)/rho and pressure of the
+// state in p.src; any output may be nullptr.
+cudaError_t launch_fields2(const Step2Params& p, float* rho_m, float* rho_g, float* ux, float* uy, float* pr,
+                           cudaStream_t s);
+
 // One box of a batched launch (device array).
 struct BatchInst {
   void* pops0;
@@ -214,8 +232,11 @@ struct RelabelBox {
   uint8_t* tile_prev;
   int* tile_list;
   int* flags;
+  float* pr;  // two components: mixture pressure written by the density
+              // phase and used by the rupture test (nullptr: one component)
   int nx, ny, ntx, nty, R, cur;
   float threshold, G, rho0, eps;
+  float G_mg, G_gg;  // two components: melt-gas and gas-gas couplings
   float wref[Q];
 };
 

@@ -1,0 +1,265 @@
+// Two-component step: melt (m) and gas (g) lattices coupled every step
+// (Sec. 2.1.5, the two-lattice description with the common velocity and the
+// per-component velocities of Eqs. 36-40), read as the Shan-Chen mixture:
+//
+//   F_s(x) = -psi_s(x) sum_s' G_ss' S_s'(x),  S_s'(x) = sum_i w_i psi~_s'(x+e_i) e_i
+//   u'     = (j_m/tau_m + j_g/tau_g) / (rho_m/tau_m + rho_g/tau_g)
+//   u_s    = u' + tau_s F_s / rho_s     (u' where rho_s = 0)
+//   f_s,i  <- f_s,i - (f_s,i - f^eq_i(rho_s, u_s)) / tau_s
+//
+// with psi_s = rho0 (1 - exp(-rho_s/rho0)) (Eq. 30), G_mg = G_gm, and the
+// barrier substitution psi~ = psi_s'(x) across a blocked edge. FP32 storage;
+// buffer layout: 18 planes, the nine melt planes then the nine gas planes,
+// each holding f^out at its source cell (the next step pulls f_i(x) from
+// x - e_i).
+//
+// The kernel marches a 256-column strip down a row chunk with plain loads:
+// for each row it pulls both components of the strip's cells (and of one
+// halo column per side), puts psi_m and psi_g into two four-row rings in
+// shared memory, and one barrier later runs force, collision and store of
+// the previous row from registers.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kBX2C = 256;
+
+__device__ __forceinline__ int wrap_1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// The nine pulled populations of one component at (x, row r), rows given
+// as offsets of r - 1, r, r + 1 and columns x - 1, x, x + 1 (wrapped).
+__device__ __forceinline__ void pull9(const float* __restrict__ src, long long N, long long rowm, long long row0,
+                                      long long rowp, int xm, int x, int xp, float f[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    // f_i(x) = B_i(x - e_i)
+    const long long row = cy(i) > 0 ? rowm : (cy(i) < 0 ? rowp : row0);
+    const int xs = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : x);
+    f[i] = __ldg(src + (size_t)i * N + row + xs);
+  }
+}
+
+__device__ __forceinline__ void mom(const float f[Q], float& rho, float& jx, float& jy) {
+  rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  jx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
+  jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
+}
+
+__device__ __forceinline__ float psi2(float rho, const Step2Params& p) {
+  return p.rho0 * (1.0f - __expf(-rho * p.inv_rho0));
+}
+
+// S = sum_i w_i psi~(x + e_i) e_i from a ring (rows sm, s0, sp; column jc),
+// psi~ = psi(x) on blocked edges.
+__device__ __forceinline__ void nsum(const float (*ring)[kBX2C + 2], int sm, int s0, int sp, int jc, unsigned m,
+                                     float& Sx, float& Sy) {
+  const float c = ring[s0][jc];
+  float s[Q];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    s[i] = ring[cy(i) > 0 ? sp : (cy(i) < 0 ? sm : s0)][jc + cx(i)];
+    if ((m >> (i - 1)) & 1u) s[i] = c;
+  }
+  const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
+  Sx = w1 * (s[1] - s[3]) + w5 * ((s[5] - s[7]) + (s[8] - s[6]));
+  Sy = w1 * (s[2] - s[4]) + w5 * ((s[5] - s[7]) + (s[6] - s[8]));
+}
+
+__device__ __forceinline__ void collide9(float f[Q], float rho, float ux, float uy, float inv_tau, bool tau_one) {
+  const float uu = ux * ux + uy * uy;
+  const float a = rho * (1.0f - 1.5f * uu);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float eu = (float)cx(i) * ux + (float)cy(i) * uy;
+    const float feq = (float)wq(i) * (a + rho * (3.0f * eu + 4.5f * eu * eu));
+    f[i] = tau_one ? feq : f[i] + (feq - f[i]) * inv_tau;
+  }
+}
+
+template <bool MASKED>
+__global__ void __launch_bounds__(kBX2C) k_step2_strip(const Step2Params p) {
+  __shared__ float ring_m[4][kBX2C + 2];
+  __shared__ float ring_g[4][kBX2C + 2];
+  const float* __restrict__ src = static_cast<const float*>(p.src);
+  float* __restrict__ dst = static_cast<float*>(p.dst);
+  const long long N = p.N;
+  const float* __restrict__ srcg = src + 9 * N;
+  float* __restrict__ dstg = dst + 9 * N;
+  const int nx = p.nx, ny = p.ny;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kBX2C;
+  const int x = x0 + tid;
+  const bool active = x < nx;
+  const int last = min(x0 + kBX2C, nx) - 1;
+  const int y0 = blockIdx.y * p.rows_per_chunk;
+  const int y1 = min(y0 + p.rows_per_chunk, ny);
+  if (y0 >= y1) return;  // uniform over the block
+  const int xc = active ? x : last;
+  const int xm = wrap_1(xc - 1, nx), xp = wrap_1(xc + 1, nx);
+  const int xl = wrap_1(x0 - 1, nx), xlm = wrap_1(x0 - 2, nx);
+  const int xr = wrap_1(last + 1, nx), xrp = wrap_1(last + 2, nx);
+  const int jc = tid + 1;
+  const bool tau_one = p.tau_m == 1.0f && p.tau_g == 1.0f;
+
+  float pm[Q], pg[Q];
+  float rm_p = 1.f, jxm_p = 0.f, jym_p = 0.f, rg_p = 0.f, jxg_p = 0.f, jyg_p = 0.f;
+  int bad = 0;
+  for (int r = y0 - 1, k = 0; r <= y1; ++r, ++k) {
+    const int rr = wrap_1(r, ny);  // r in [-1, ny]
+    const long long row0 = (long long)rr * nx;
+    const long long rowm = (long long)wrap_1(rr - 1, ny) * nx;
+    const long long rowp = (long long)wrap_1(rr + 1, ny) * nx;
+    float fm[Q], fg[Q];
+    float rm = 1.f, jxm = 0.f, jym = 0.f, rg = 0.f, jxg = 0.f, jyg = 0.f;
+    if (active) {
+      pull9(src, N, rowm, row0, rowp, xm, x, xp, fm);
+      pull9(srcg, N, rowm, row0, rowp, xm, x, xp, fg);
+      mom(fm, rm, jxm, jym);
+      mom(fg, rg, jxg, jyg);
+      ring_m[k & 3][jc] = psi2(rm, p);
+      ring_g[k & 3][jc] = psi2(rg, p);
+    }
+    if (tid == 0) {  // left halo cell x0 - 1
+      float h[Q], a, b, c;
+      pull9(src, N, rowm, row0, rowp, xlm, xl, x0, h);
+      mom(h, a, b, c);
+      ring_m[k & 3][0] = psi2(a, p);
+      pull9(srcg, N, rowm, row0, rowp, xlm, xl, x0, h);
+      mom(h, a, b, c);
+      ring_g[k & 3][0] = psi2(a, p);
+    }
+    if (x == last) {  // right halo cell last + 1
+      float h[Q], a, b, c;
+      pull9(src, N, rowm, row0, rowp, last, xr, xrp, h);
+      mom(h, a, b, c);
+      ring_m[k & 3][last - x0 + 2] = psi2(a, p);
+      pull9(srcg, N, rowm, row0, rowp, last, xr, xrp, h);
+      mom(h, a, b, c);
+      ring_g[k & 3][last - x0 + 2] = psi2(a, p);
+    }
+    __syncthreads();
+    if (k >= 2 && active) {
+      const int rc = r - 1;
+      const unsigned m = MASKED ? p.mask[(size_t)rc * nx + x] : 0u;
+      const int sm = (k - 2) & 3, s0 = (k - 1) & 3, sp = k & 3;
+      float Smx, Smy, Sgx, Sgy;
+      nsum(ring_m, sm, s0, sp, jc, m, Smx, Smy);
+      nsum(ring_g, sm, s0, sp, jc, m, Sgx, Sgy);
+      const float psim = ring_m[s0][jc], psig = ring_g[s0][jc];
+      const float Fmx = -psim * (p.G_mm * Smx + p.G_mg * Sgx), Fmy = -psim * (p.G_mm * Smy + p.G_mg * Sgy);
+      const float Fgx = -psig * (p.G_mg * Smx + p.G_gg * Sgx), Fgy = -psig * (p.G_mg * Smy + p.G_gg * Sgy);
+      const float den = rm_p * p.inv_tau_m + rg_p * p.inv_tau_g;
+      bad |= !(rm_p >= 0.f && rg_p >= 0.f && den > 0.f && den < 1e30f);
+      const float ux = (jxm_p * p.inv_tau_m + jxg_p * p.inv_tau_g) / den;
+      const float uy = (jym_p * p.inv_tau_m + jyg_p * p.inv_tau_g) / den;
+      const float umx = rm_p > 0.f ? ux + p.tau_m * Fmx / rm_p : ux;
+      const float umy = rm_p > 0.f ? uy + p.tau_m * Fmy / rm_p : uy;
+      const float ugx = rg_p > 0.f ? ux + p.tau_g * Fgx / rg_p : ux;
+      const float ugy = rg_p > 0.f ? uy + p.tau_g * Fgy / rg_p : uy;
+      collide9(pm, rm_p, umx, umy, p.inv_tau_m, tau_one);
+      collide9(pg, rg_p, ugx, ugy, p.inv_tau_g, tau_one);
+      const size_t base = (size_t)rc * nx + x;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        dst[(size_t)i * N + base] = pm[i];
+        dstg[(size_t)i * N + base] = pg[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      pm[i] = fm[i];
+      pg[i] = fg[i];
+    }
+    rm_p = rm;
+    jxm_p = jxm;
+    jym_p = jym;
+    rg_p = rg;
+    jxg_p = jxg;
+    jyg_p = jyg;
+  }
+  if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
+}
+
+// Diagnostics: melt and gas densities, the physical mixture velocity
+// u = sum_s (j_s + F_s / 2) / (rho_m + rho_g) and the mixture pressure.
+__global__ void k_fields2(const Step2Params p, float* __restrict__ rho_m, float* __restrict__ rho_g,
+                          float* __restrict__ ux, float* __restrict__ uy, float* __restrict__ pr) {
+  const float* src = static_cast<const float*>(p.src);
+  const long long N = p.N;
+  const int nx = p.nx, ny = p.ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    const unsigned m = p.mask ? p.mask[c] : 0u;
+    float Sm[2] = {0.f, 0.f}, Sg[2] = {0.f, 0.f}, own[2] = {0.f, 0.f};
+    float rm = 0.f, rg = 0.f, jx = 0.f, jy = 0.f;
+    // densities of the cell and the neighbour sums from the neighbours' densities
+    for (int i = 0; i < Q; ++i) {
+      const int xx = wrap_1(x + cx(i), nx), yy = wrap_1(y + cy(i), ny);
+      float a = 0.f, b = 0.f, ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+      for (int j = 0; j < Q; ++j) {
+        const size_t idx = (size_t)wrap_1(yy - cy(j), ny) * nx + wrap_1(xx - cx(j), nx);
+        const float fa = src[(size_t)j * N + idx], fb = src[(size_t)(9 + j) * N + idx];
+        a += fa;
+        b += fb;
+        ax += cx(j) * fa;
+        ay += cy(j) * fa;
+        bx += cx(j) * fb;
+        by += cy(j) * fb;
+      }
+      if (i == 0) {
+        rm = a;
+        rg = b;
+        jx = ax + bx;
+        jy = ay + by;
+        own[0] = psi2(a, p);
+        own[1] = psi2(b, p);
+      } else {  // i = 0 comes first, so own[] is known; blocked edges take it
+        const bool blocked = (m >> (i - 1)) & 1u;
+        const float wa = (float)wq(i);
+        const float pa = blocked ? own[0] : psi2(a, p), pb = blocked ? own[1] : psi2(b, p);
+        Sm[0] += wa * cx(i) * pa;
+        Sm[1] += wa * cy(i) * pa;
+        Sg[0] += wa * cx(i) * pb;
+        Sg[1] += wa * cy(i) * pb;
+      }
+    }
+    const float Fx = -own[0] * (p.G_mm * Sm[0] + p.G_mg * Sg[0]) - own[1] * (p.G_mg * Sm[0] + p.G_gg * Sg[0]);
+    const float Fy = -own[0] * (p.G_mm * Sm[1] + p.G_mg * Sg[1]) - own[1] * (p.G_mg * Sm[1] + p.G_gg * Sg[1]);
+    const float r = rm + rg;
+    if (rho_m) rho_m[c] = rm;
+    if (rho_g) rho_g[c] = rg;
+    if (ux) ux[c] = (jx + 0.5f * Fx) / r;
+    if (uy) uy[c] = (jy + 0.5f * Fy) / r;
+    if (pr)
+      pr[c] = r * (1.0f / 3.0f) +
+              (p.G_mm * own[0] * own[0] + 2.0f * p.G_mg * own[0] * own[1] + p.G_gg * own[1] * own[1]) *
+                  (1.0f / 6.0f);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_step2(const Step2Params& p, cudaStream_t s) {
+  const int gx = (p.nx + kBX2C - 1) / kBX2C;
+  int g = (152 * 4 + gx - 1) / gx;  // a few CTAs per SM
+  if (g > p.ny) g = p.ny;
+  if (g < 1) g = 1;
+  Step2Params q = p;
+  q.rows_per_chunk = (p.ny + g - 1) / g;
+  const int gy = (p.ny + q.rows_per_chunk - 1) / q.rows_per_chunk;
+  if (p.mask) k_step2_strip<true><<<dim3(gx, gy), kBX2C, 0, s>>>(q);
+  else k_step2_strip<false><<<dim3(gx, gy), kBX2C, 0, s>>>(q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fields2(const Step2Params& p, float* rho_m, float* rho_g, float* ux, float* uy, float* pr,
+                           cudaStream_t s) {
+  long long b = (p.N + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  k_fields2<<<(unsigned)b, 256, 0, s>>>(p, rho_m, rho_g, ux, uy, pr);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

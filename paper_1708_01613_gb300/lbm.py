@@ -22,10 +22,12 @@ STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 
 FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_P = 1 << 0, 1 << 1, 1 << 2, 1 << 3
 FIELD_LABEL, FIELD_OWNER, FIELD_MASK, FIELD_OPEN, FIELD_POPS = 1 << 4, 1 << 5, 1 << 6, 1 << 7, 1 << 8
+FIELD_RHO_GAS = 1 << 9
 FIELDS = {"rho": (FIELD_RHO, np.float32), "ux": (FIELD_UX, np.float32), "uy": (FIELD_UY, np.float32),
           "p": (FIELD_P, np.float32), "label": (FIELD_LABEL, np.int32),
           "owner": (FIELD_OWNER, np.int32), "mask": (FIELD_MASK, np.uint8),
-          "open": (FIELD_OPEN, np.uint8), "pops": (FIELD_POPS, np.float32)}
+          "open": (FIELD_OPEN, np.uint8), "pops": (FIELD_POPS, np.float32),
+          "rho_gas": (FIELD_RHO_GAS, np.float32)}
 
 
 class LbmError(RuntimeError):
@@ -40,7 +42,8 @@ class lbm_config(C.Structure):
                 ("stop_on_first_rupture", C.c_int32), ("growth", C.c_int32),
                 ("tau", C.c_double), ("G", C.c_double), ("rho0", C.c_double),
                 ("rho_ref", C.c_double), ("gas_threshold", C.c_double),
-                ("rupture_eps", C.c_double)]
+                ("rupture_eps", C.c_double), ("components", C.c_int32), ("reserved2", C.c_int32),
+                ("tau_g", C.c_double), ("G_mg", C.c_double), ("G_gg", C.c_double)]
 
 
 class lbm_bubble(C.Structure):
@@ -139,7 +142,8 @@ def make_config(nx: int, ny: int, *, storage: str = "f32", barrier: bool = False
                 zone_radius: int = 4, stop_on_first_rupture: bool = False, tau: float = 1.0,
                 G: float = -5.5, rho0: float = 1.0, rho_ref: float = 1.0,
                 gas_threshold: float = math.log(2.0), rupture_eps: float = 1e-6,
-                growth: bool = False) -> lbm_config:
+                growth: bool = False, components: int = 1, tau_g: float = 1.0, G_mg: float = 0.0,
+                G_gg: float = 0.0) -> lbm_config:
     c = lbm_config_default()
     c.nx, c.ny = int(nx), int(ny)
     c.storage = STORAGE[storage]
@@ -150,6 +154,8 @@ def make_config(nx: int, ny: int, *, storage: str = "f32", barrier: bool = False
     c.tau, c.G, c.rho0, c.rho_ref = float(tau), float(G), float(rho0), float(rho_ref)
     c.gas_threshold, c.rupture_eps = float(gas_threshold), float(rupture_eps)
     c.growth = int(bool(growth))
+    c.components = int(components)
+    c.tau_g, c.G_mg, c.G_gg = float(tau_g), float(G_mg), float(G_gg)
     return c
 
 
@@ -211,17 +217,30 @@ class Simulation:
         with torch.cuda.device(self.device):
             _check(getattr(load_library(), name)(self.handle, *args), self.handle)
 
-    def init_density(self, rho) -> None:
+    @property
+    def components(self) -> int:
+        return 2 if self.cfg.components == 2 else 1
+
+    def init_density(self, rho, rho_gas=None) -> None:
+        """Rest equilibrium at the FP64 densities; with two components the
+        gas density `rho_gas` is required too (melt first)."""
         import torch
 
+        if self.components == 2:
+            if rho_gas is None:
+                raise LbmError(LBM_EINVAL, "two components need rho and rho_gas")
+            rho = np.concatenate([np.asarray(rho, np.float64).ravel(), np.asarray(rho_gas, np.float64).ravel()])
+        elif rho_gas is not None:
+            raise LbmError(LBM_EINVAL, "rho_gas is for two-component boxes")
+        n = self.nx * self.ny * self.components
         if isinstance(rho, torch.Tensor) and rho.is_cuda:
             t = rho.to(torch.float64).contiguous()
-            assert t.numel() == self.nx * self.ny
+            assert t.numel() == n
             self._call("lbm_init_density", C.c_void_p(t.data_ptr()), 1)
             self.stream.synchronize()
         else:
             a = np.ascontiguousarray(np.asarray(rho, dtype=np.float64))
-            assert a.size == self.nx * self.ny
+            assert a.size == n
             self._call("lbm_init_density", C.c_void_p(a.ctypes.data), 0)
             self.stream.synchronize()
 
@@ -235,10 +254,11 @@ class Simulation:
 
         if isinstance(f, torch.Tensor) and f.is_cuda:
             t = f.to(torch.float32).contiguous()
+            assert t.numel() == 9 * self.components * self.nx * self.ny
             self._call("lbm_load_populations", C.c_void_p(t.data_ptr()), 1)
         else:
             a = np.ascontiguousarray(np.asarray(f, dtype=np.float32))
-            assert a.size == 9 * self.nx * self.ny
+            assert a.size == 9 * self.components * self.nx * self.ny
             self._call("lbm_load_populations", C.c_void_p(a.ctypes.data), 0)
 
     def set_step_variant(self, variant: int) -> None:
@@ -261,7 +281,7 @@ class Simulation:
         return bool(load_library().lbm_halted(self.handle))
 
     def read(self, *names: str, device: bool = False) -> dict:
-        """Fields by name (rho, ux, uy, p, label, owner, mask, open, pops).
+        """Fields by name (rho, ux, uy, p, label, owner, mask, open, pops, rho_gas).
 
         Host numpy arrays by default; with ``device=True`` torch CUDA tensors
         written directly by the library."""
@@ -272,7 +292,7 @@ class Simulation:
         for name in names:
             bit, dt = FIELDS[name]
             nb = int(lib.lbm_fields_bytes(self.handle, bit))
-            shape = (9, self.ny, self.nx) if name == "pops" else (self.ny, self.nx)
+            shape = (9 * self.components, self.ny, self.nx) if name == "pops" else (self.ny, self.nx)
             if device:
                 t = torch.empty(shape, dtype=getattr(torch, np.dtype(dt).name), device=self.device)
                 self._call("lbm_read_fields", C.c_uint32(bit), C.c_void_p(t.data_ptr()), nb, 1)
