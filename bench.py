@@ -366,7 +366,8 @@ def run_two_component(args, dev, n, bub, RL, RG, world, peak, peak_kind):
            "ms_per_step": round(total / steps, 5), "storage": "f32", "components": 2,
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(achieved / peak, 4), "algorithmic_bytes_per_cell": bytes_cell,
-                        "kernel": "k_step2_strip", "kernel_ms_avg": round(kern_ms, 5), "peak_kind": peak_kind},
+                        "kernel": "k_step2_tma" if n % 16 == 0 and n >= 272 else "k_step2_strip",
+                        "kernel_ms_avg": round(kern_ms, 5), "peak_kind": peak_kind},
            "gpu_launches": int(sim.kernel_launches - l0)}
     del sim
     torch.cuda.empty_cache()

@@ -23,6 +23,7 @@
 //    cells, so the eight compute warps are balanced and the bytes in flight
 //    do not depend on occupancy. Needs nx % 16 == 0 and nx >= kBX + 16.
 #include "lbm_internal.cuh"
+#include "tma.cuh"
 
 namespace lbm {
 namespace {
@@ -256,54 +257,6 @@ __global__ void __launch_bounds__(kBX) k_step_strip(const StepParams p) {
 }
 
 // ---------------------------------------------------------------- TMA-staged kernel
-__device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait: false if the phase did not complete within limit_ns.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = 2000000000ull) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (global_ns() - t0 < limit_ns)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
 template <int S>
 struct TmaGeom {
   using T = typename Store<S>::T;
@@ -312,16 +265,6 @@ struct TmaGeom {
   static constexpr int WIN = kBX + 2 * PAD;  // elements per staged plane row
   static constexpr int ROW_BYTES = WIN * E;  // multiple of 16
 };
-
-// Copy len elements of a periodic row starting at column start (may be
-// negative) into dst, in one or two pieces (len <= row length).
-template <typename T>
-__device__ __forceinline__ void copy_row_wrapped(T* dst, const T* row, int start, int len, int nx, uint64_t* bar) {
-  const int s0 = start < 0 ? start + nx : start;
-  const int first = min(len, nx - s0);
-  bulk_g2s(dst, row + s0, (uint32_t)(first * sizeof(T)), bar);
-  if (first < len) bulk_g2s(dst + first, row, (uint32_t)((len - first) * sizeof(T)), bar);
-}
 
 // Issued by the lanes of the ninth warp: lane 0 arms the stage's mbarrier,
 // lanes 0..8 copy plane `lane`, lane 9 copies the mask row.

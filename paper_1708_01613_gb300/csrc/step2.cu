@@ -19,6 +19,7 @@
 // shared memory, and one barrier later runs force, collision and store of
 // the previous row from registers.
 #include "lbm_internal.cuh"
+#include "tma.cuh"
 
 namespace lbm {
 namespace {
@@ -77,8 +78,42 @@ __device__ __forceinline__ void collide9(float f[Q], float rho, float ux, float 
   }
 }
 
-template <bool MASKED>
-__global__ void __launch_bounds__(kBX2C) k_step2_strip(const Step2Params p) {
+// Force (both components, barrier substitution), common velocity, both
+// collisions and the 18 stores of one cell whose psi rows sit in the rings.
+template <bool TAU_ONE>
+__device__ __forceinline__ void finish2(const Step2Params& p, const float (*ring_m)[kBX2C + 2],
+                                        const float (*ring_g)[kBX2C + 2], int sm, int s0, int sp, int jc, unsigned m,
+                                        float pm[Q], float pg[Q], float rm, float jxm, float jym, float rg, float jxg,
+                                        float jyg, float* __restrict__ dst, float* __restrict__ dstg, size_t base,
+                                        int& bad) {
+  float Smx, Smy, Sgx, Sgy;
+  nsum(ring_m, sm, s0, sp, jc, m, Smx, Smy);
+  nsum(ring_g, sm, s0, sp, jc, m, Sgx, Sgy);
+  const float psim = ring_m[s0][jc], psig = ring_g[s0][jc];
+  const float Fmx = -psim * (p.G_mm * Smx + p.G_mg * Sgx), Fmy = -psim * (p.G_mm * Smy + p.G_mg * Sgy);
+  const float Fgx = -psig * (p.G_mg * Smx + p.G_gg * Sgx), Fgy = -psig * (p.G_mg * Smy + p.G_gg * Sgy);
+  const float den = rm * p.inv_tau_m + rg * p.inv_tau_g;
+  bad |= !(rm >= 0.f && rg >= 0.f && den > 0.f && den < 1e30f);
+  const float ux = (jxm * p.inv_tau_m + jxg * p.inv_tau_g) / den;
+  const float uy = (jym * p.inv_tau_m + jyg * p.inv_tau_g) / den;
+  const float umx = rm > 0.f ? ux + p.tau_m * Fmx / rm : ux;
+  const float umy = rm > 0.f ? uy + p.tau_m * Fmy / rm : uy;
+  const float ugx = rg > 0.f ? ux + p.tau_g * Fgx / rg : ux;
+  const float ugy = rg > 0.f ? uy + p.tau_g * Fgy / rg : uy;
+  collide9(pm, rm, umx, umy, p.inv_tau_m, TAU_ONE);
+  collide9(pg, rg, ugx, ugy, p.inv_tau_g, TAU_ONE);
+  const size_t N = (size_t)p.N;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    dst[(size_t)i * N + base] = pm[i];
+    dstg[(size_t)i * N + base] = pg[i];
+  }
+}
+
+// TAU_ONE (both relaxation times 1): the collision output is the
+// equilibrium alone, so only the moments of the previous row are kept.
+template <bool MASKED, bool TAU_ONE>
+__global__ void __launch_bounds__(kBX2C, TAU_ONE ? 4 : 2) k_step2_strip(const Step2Params p) {
   __shared__ float ring_m[4][kBX2C + 2];
   __shared__ float ring_g[4][kBX2C + 2];
   const float* __restrict__ src = static_cast<const float*>(p.src);
@@ -100,7 +135,6 @@ __global__ void __launch_bounds__(kBX2C) k_step2_strip(const Step2Params p) {
   const int xl = wrap_1(x0 - 1, nx), xlm = wrap_1(x0 - 2, nx);
   const int xr = wrap_1(last + 1, nx), xrp = wrap_1(last + 2, nx);
   const int jc = tid + 1;
-  const bool tau_one = p.tau_m == 1.0f && p.tau_g == 1.0f;
 
   float pm[Q], pg[Q];
   float rm_p = 1.f, jxm_p = 0.f, jym_p = 0.f, rg_p = 0.f, jxg_p = 0.f, jyg_p = 0.f;
@@ -120,56 +154,39 @@ __global__ void __launch_bounds__(kBX2C) k_step2_strip(const Step2Params p) {
       ring_m[k & 3][jc] = psi2(rm, p);
       ring_g[k & 3][jc] = psi2(rg, p);
     }
-    if (tid == 0) {  // left halo cell x0 - 1
-      float h[Q], a, b, c;
-      pull9(src, N, rowm, row0, rowp, xlm, xl, x0, h);
-      mom(h, a, b, c);
-      ring_m[k & 3][0] = psi2(a, p);
-      pull9(srcg, N, rowm, row0, rowp, xlm, xl, x0, h);
-      mom(h, a, b, c);
-      ring_g[k & 3][0] = psi2(a, p);
-    }
-    if (x == last) {  // right halo cell last + 1
-      float h[Q], a, b, c;
-      pull9(src, N, rowm, row0, rowp, last, xr, xrp, h);
-      mom(h, a, b, c);
-      ring_m[k & 3][last - x0 + 2] = psi2(a, p);
-      pull9(srcg, N, rowm, row0, rowp, last, xr, xrp, h);
-      mom(h, a, b, c);
-      ring_g[k & 3][last - x0 + 2] = psi2(a, p);
+    // halo cells x0 - 1 (warp 0) and last + 1 (warp 1): one population per
+    // lane (melt in lanes 0-8, gas in lanes 16-24), summed per half-warp
+    if (tid < 64) {
+      const int lane = tid & 31, i = lane & 15;
+      const bool right = tid >= 32;
+      float v = 0.f;
+      if (i < Q) {
+        const float* base = lane < 16 ? src : srcg;
+        const long long row = cy(i) > 0 ? rowm : (cy(i) < 0 ? rowp : row0);
+        const int xs = cx(i) > 0 ? (right ? last : xlm) : (cx(i) < 0 ? (right ? xrp : x0) : (right ? xr : xl));
+        v = __ldg(base + (size_t)i * N + row + xs);
+      }
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      const int col = right ? last - x0 + 2 : 0;
+      if (lane == 0) ring_m[k & 3][col] = psi2(v, p);
+      if (lane == 16) ring_g[k & 3][col] = psi2(v, p);
     }
     __syncthreads();
     if (k >= 2 && active) {
       const int rc = r - 1;
       const unsigned m = MASKED ? p.mask[(size_t)rc * nx + x] : 0u;
-      const int sm = (k - 2) & 3, s0 = (k - 1) & 3, sp = k & 3;
-      float Smx, Smy, Sgx, Sgy;
-      nsum(ring_m, sm, s0, sp, jc, m, Smx, Smy);
-      nsum(ring_g, sm, s0, sp, jc, m, Sgx, Sgy);
-      const float psim = ring_m[s0][jc], psig = ring_g[s0][jc];
-      const float Fmx = -psim * (p.G_mm * Smx + p.G_mg * Sgx), Fmy = -psim * (p.G_mm * Smy + p.G_mg * Sgy);
-      const float Fgx = -psig * (p.G_mg * Smx + p.G_gg * Sgx), Fgy = -psig * (p.G_mg * Smy + p.G_gg * Sgy);
-      const float den = rm_p * p.inv_tau_m + rg_p * p.inv_tau_g;
-      bad |= !(rm_p >= 0.f && rg_p >= 0.f && den > 0.f && den < 1e30f);
-      const float ux = (jxm_p * p.inv_tau_m + jxg_p * p.inv_tau_g) / den;
-      const float uy = (jym_p * p.inv_tau_m + jyg_p * p.inv_tau_g) / den;
-      const float umx = rm_p > 0.f ? ux + p.tau_m * Fmx / rm_p : ux;
-      const float umy = rm_p > 0.f ? uy + p.tau_m * Fmy / rm_p : uy;
-      const float ugx = rg_p > 0.f ? ux + p.tau_g * Fgx / rg_p : ux;
-      const float ugy = rg_p > 0.f ? uy + p.tau_g * Fgy / rg_p : uy;
-      collide9(pm, rm_p, umx, umy, p.inv_tau_m, tau_one);
-      collide9(pg, rg_p, ugx, ugy, p.inv_tau_g, tau_one);
-      const size_t base = (size_t)rc * nx + x;
+      finish2<TAU_ONE>(p, ring_m, ring_g, (k - 2) & 3, (k - 1) & 3, k & 3, jc, m, pm, pg, rm_p, jxm_p, jym_p,
+                       rg_p, jxg_p, jyg_p, dst, dstg, (size_t)rc * nx + x, bad);
+    }
+    if (!TAU_ONE) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        dst[(size_t)i * N + base] = pm[i];
-        dstg[(size_t)i * N + base] = pg[i];
+        pm[i] = fm[i];
+        pg[i] = fg[i];
       }
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      pm[i] = fm[i];
-      pg[i] = fg[i];
     }
     rm_p = rm;
     jxm_p = jxm;
@@ -179,6 +196,197 @@ __global__ void __launch_bounds__(kBX2C) k_step2_strip(const Step2Params p) {
     jyg_p = jyg;
   }
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
+}
+
+// ------------------------------------------------------------------ staged
+// The same march with the 18 source rows of every output row (with a
+// 16-byte halo) copied into shared-memory stages by cp.async.bulk, issued
+// NSTAGE - 1 rows ahead by a ninth warp that also sums the four halo cells
+// (melt and gas, left and right) lane-parallel. Needs nx % 16 == 0 (16-byte
+// rows and mask pieces) and nx >= kBX2C + 16 (a staged row wraps at most
+// once).
+constexpr int kPad2C = 4;                        // halo pad: 16 bytes of FP32
+constexpr int kWin2C = kBX2C + 2 * kPad2C;       // floats per staged row
+constexpr int kRow2C = kWin2C * 4;               // bytes, a multiple of 16
+constexpr int kThreads2C = kBX2C + 32;
+
+template <bool MASKED>
+constexpr int stage2c_bytes() { return 2 * Q * kRow2C + (MASKED ? kBX2C : 0); }
+
+template <bool MASKED, int NSTAGE>
+constexpr size_t smem2c_bytes() {
+  return (size_t)NSTAGE * stage2c_bytes<MASKED>() + 2 * 4 * (kBX2C + 2) * 4 + NSTAGE * 8 + 16;
+}
+
+// Lane l < 18 of the ninth warp copies plane l (melt 0-8, gas 9-17) of
+// stage k (output row y0 - 1 + k); lane 18 copies the mask row.
+template <bool MASKED, int NSTAGE>
+__device__ __forceinline__ void issue2c(const Step2Params& p, unsigned char* stages, uint64_t* bars, int k, int y0,
+                                        int x0, int lane) {
+  constexpr uint32_t STAGE = stage2c_bytes<MASKED>();
+  const int slot = k % NSTAGE;
+  unsigned char* st = stages + (size_t)slot * STAGE;
+  uint64_t* bar = bars + slot;
+  const int r = y0 - 1 + k;
+  const int ny = p.ny, nx = p.nx;
+  if (lane < 2 * Q + (MASKED ? 1 : 0)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (lane == 0) mbar_expect_tx(bar, STAGE);
+  __syncwarp();
+  if (lane < 2 * Q) {
+    const int i = lane % Q;
+    int g = r - cy(i);
+    g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
+    g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
+    const float* row = static_cast<const float*>(p.src) + (size_t)lane * p.N + (size_t)g * nx;
+    copy_row_wrapped<float>(reinterpret_cast<float*>(st + lane * kRow2C), row, x0 - kPad2C, kWin2C, nx, bar);
+  } else if (MASKED && lane == 2 * Q) {
+    const int g = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+    copy_row_wrapped<uint8_t>(st + 2 * Q * kRow2C, p.mask + (size_t)g * nx, x0, kBX2C, nx, bar);
+  }
+}
+
+template <bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Params p) {
+  constexpr int STAGE = stage2c_bytes<MASKED>();
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* stages = smem;
+  float(*ring_m)[kBX2C + 2] = reinterpret_cast<float(*)[kBX2C + 2]>(smem + (size_t)NSTAGE * STAGE);
+  float(*ring_g)[kBX2C + 2] = ring_m + 4;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE + 2 * 4 * (kBX2C + 2) * 4);
+  int* abort_flag = reinterpret_cast<int*>(bars + NSTAGE);
+
+  float* __restrict__ dst = static_cast<float*>(p.dst);
+  float* __restrict__ dstg = dst + (size_t)Q * p.N;
+  const int nx = p.nx, ny = p.ny;
+  const int tid = threadIdx.x;
+  const bool helper = tid >= kBX2C;
+  const int lane = tid & 31;
+  const int x0 = blockIdx.x * kBX2C;
+  const int width = min(kBX2C, nx - x0);
+  const bool active = !helper && tid < width;
+  const int y0 = blockIdx.y * p.rows_per_chunk;
+  const int y1 = min(y0 + p.rows_per_chunk, ny);
+  if (y0 >= y1) return;
+  const int nst = (y1 - y0) + 2;  // stages = rows y0-1 .. y1
+
+  if (tid == 0) {
+    for (int q = 0; q < NSTAGE; ++q) mbar_init(bars + q, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (helper)
+    for (int k = 0; k < NSTAGE - 1 && k < nst; ++k) issue2c<MASKED, NSTAGE>(p, stages, bars, k, y0, x0, lane);
+
+  // halo lanes: lanes 0..8 the left cell (column x0 - 1), lanes 16..24 the
+  // right one (column x0 + width), plane lane & 15 of the component summed
+  const int hplane = lane & 15;
+  const bool hlane = helper && hplane < Q;
+  const int hpos = (lane < 16 ? kPad2C - 1 : kPad2C + width) - cx(hplane < Q ? hplane : 0);
+
+  const int jc = tid + 1;
+  const int pos = kPad2C + tid;
+  float pm[Q], pg[Q];
+  float rm_p = 1.f, jxm_p = 0.f, jym_p = 0.f, rg_p = 0.f, jxg_p = 0.f, jyg_p = 0.f;
+  unsigned m_prev = 0;
+  int bad = 0, k_abort = 0;
+  for (int k = 0; k < nst; ++k) {
+    const int slot = k % NSTAGE;
+    const unsigned char* st = stages + (size_t)slot * STAGE;
+    if (!mbar_wait(bars + slot, (uint32_t)((k / NSTAGE) & 1))) *abort_flag = 1;
+    float fm[Q], fg[Q];
+    float rm = 1.f, jxm = 0.f, jym = 0.f, rg = 0.f, jxg = 0.f, jyg = 0.f;
+    unsigned m = 0;
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        fm[i] = reinterpret_cast<const float*>(st + i * kRow2C)[pos - cx(i)];
+        fg[i] = reinterpret_cast<const float*>(st + (Q + i) * kRow2C)[pos - cx(i)];
+      }
+      mom(fm, rm, jxm, jym);
+      mom(fg, rg, jxg, jyg);
+      ring_m[k & 3][jc] = psi2(rm, p);
+      ring_g[k & 3][jc] = psi2(rg, p);
+      if (MASKED) m = st[2 * Q * kRow2C + tid];
+    } else if (helper) {
+#pragma unroll
+      for (int comp = 0; comp < 2; ++comp) {
+        float v = hlane ? reinterpret_cast<const float*>(st + (comp * Q + hplane) * kRow2C)[hpos] : 0.f;
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        float(*ring)[kBX2C + 2] = comp ? ring_g : ring_m;
+        if (lane == 0) ring[k & 3][0] = psi2(v, p);
+        if (lane == 16) ring[k & 3][width + 1] = psi2(v, p);
+      }
+    }
+    __syncthreads();
+    if (*abort_flag) {
+      k_abort = k;
+      break;
+    }
+    if (helper) {
+      if (k + NSTAGE - 1 < nst) issue2c<MASKED, NSTAGE>(p, stages, bars, k + NSTAGE - 1, y0, x0, lane);
+    } else if (k >= 2 && active) {
+      const int rc = y0 + k - 2;
+      finish2<TAU_ONE>(p, ring_m, ring_g, (k - 2) & 3, (k - 1) & 3, k & 3, jc, m_prev, pm, pg, rm_p, jxm_p, jym_p,
+                       rg_p, jxg_p, jyg_p, dst, dstg, (size_t)rc * nx + x0 + tid, bad);
+    }
+    if (!TAU_ONE) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        pm[i] = fm[i];
+        pg[i] = fg[i];
+      }
+    }
+    rm_p = rm;
+    jxm_p = jxm;
+    jym_p = jym;
+    rg_p = rg;
+    jxg_p = jxg;
+    jyg_p = jyg;
+    m_prev = m;
+  }
+  if (*abort_flag) {
+    // a stage never completed: record it, then wait (bounded) for the copies
+    // of every stage issued and not consumed before the CTA leaves
+    if (tid == 0) {
+      atomicOr(p.flags + FLAG_TIMEOUT, 1);
+      const int issued = min(nst, k_abort + NSTAGE - 1);
+      for (int q = k_abort; q < issued; ++q) mbar_wait(bars + q % NSTAGE, (uint32_t)((q / NSTAGE) & 1), 500000000ull);
+    }
+    __syncthreads();
+    return;
+  }
+  if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
+}
+
+template <bool MASKED, bool TAU_ONE>
+cudaError_t launch_step2_tma(const Step2Params& p, cudaStream_t s) {
+  constexpr int NS = 3, MINB = TAU_ONE ? 3 : 2;
+  auto kern = k_step2_tma<MASKED, TAU_ONE, NS, MINB>;
+  constexpr size_t smem = smem2c_bytes<MASKED, NS>();
+  static int resident = 0;  // per instantiation
+  if (resident == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads2C, smem);
+    if (e != cudaSuccess) return e;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaErrorInvalidDevice;
+    resident = (occ > 0 ? occ : 1) * sms;
+  }
+  const int gx = (p.nx + kBX2C - 1) / kBX2C;
+  int g = resident / gx;
+  if (g < 1) g = 1;
+  if (g > p.ny) g = p.ny;
+  Step2Params q = p;
+  q.rows_per_chunk = (p.ny + g - 1) / g;
+  const int gy = (p.ny + q.rows_per_chunk - 1) / q.rows_per_chunk;
+  kern<<<dim3(gx, gy), kThreads2C, smem, s>>>(q);
+  return cudaGetLastError();
 }
 
 // Diagnostics: melt and gas densities, the physical mixture velocity
@@ -242,6 +450,11 @@ __global__ void k_fields2(const Step2Params p, float* __restrict__ rho_m, float*
 }  // namespace
 
 cudaError_t launch_step2(const Step2Params& p, cudaStream_t s) {
+  const bool one = p.tau_m == 1.0f && p.tau_g == 1.0f;
+  if (p.nx % 16 == 0 && p.nx >= kBX2C + 16) {  // staged rows
+    if (p.mask) return one ? launch_step2_tma<true, true>(p, s) : launch_step2_tma<true, false>(p, s);
+    return one ? launch_step2_tma<false, true>(p, s) : launch_step2_tma<false, false>(p, s);
+  }
   const int gx = (p.nx + kBX2C - 1) / kBX2C;
   int g = (152 * 4 + gx - 1) / gx;  // a few CTAs per SM
   if (g > p.ny) g = p.ny;
@@ -249,8 +462,13 @@ cudaError_t launch_step2(const Step2Params& p, cudaStream_t s) {
   Step2Params q = p;
   q.rows_per_chunk = (p.ny + g - 1) / g;
   const int gy = (p.ny + q.rows_per_chunk - 1) / q.rows_per_chunk;
-  if (p.mask) k_step2_strip<true><<<dim3(gx, gy), kBX2C, 0, s>>>(q);
-  else k_step2_strip<false><<<dim3(gx, gy), kBX2C, 0, s>>>(q);
+  if (p.mask) {
+    if (one) k_step2_strip<true, true><<<dim3(gx, gy), kBX2C, 0, s>>>(q);
+    else k_step2_strip<true, false><<<dim3(gx, gy), kBX2C, 0, s>>>(q);
+  } else {
+    if (one) k_step2_strip<false, true><<<dim3(gx, gy), kBX2C, 0, s>>>(q);
+    else k_step2_strip<false, false><<<dim3(gx, gy), kBX2C, 0, s>>>(q);
+  }
   return cudaGetLastError();
 }
 

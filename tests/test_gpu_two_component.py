@@ -32,13 +32,15 @@ def both(orc):
     return np.concatenate([orc.fm, orc.fg])
 
 
-@pytest.mark.parametrize("nx,ny", [(96, 64), (300, 70), (37, 9)])
-def test_mixture_parity(nx, ny):
-    """Demixing mixture (melt cohesion, melt-gas repulsion, unequal
-    relaxation times): several strips, ragged last strip, a tiny box."""
+@pytest.mark.parametrize("nx,ny", [(96, 64), (300, 70), (37, 9), (320, 64), (784, 24)])
+@pytest.mark.parametrize("taus", [(1.0, 0.8), (1.0, 1.0)])
+def test_mixture_parity(nx, ny, taus):
+    """Demixing mixture (melt cohesion, melt-gas repulsion): plain-load
+    kernel (96, 300, 37 columns) and staged kernel (320, 784: full strips
+    and a ragged one), unequal and unit relaxation times."""
     a = inputs.noise_density(nx, ny, seed=11, rho_mean=0.7)
     b = inputs.noise_density(nx, ny, seed=12, rho_mean=0.6)
-    sim, orc = pair(nx, ny, a, b, tau_m=1.0, tau_g=0.8, G_mm=-1.0, G_mg=2.5, G_gg=-0.3)
+    sim, orc = pair(nx, ny, a, b, tau_m=taus[0], tau_g=taus[1], G_mm=-1.0, G_mg=2.5, G_gg=-0.3)
     for n in (1, 9, 40):
         sim.step(n)
         orc.step(n)
@@ -47,8 +49,10 @@ def test_mixture_parity(nx, ny):
         assert err < 1e-5
 
 
-def test_two_bubbles_with_barrier_parity():
-    nx, ny, R, gap = 160, 80, 12, 3.0
+@pytest.mark.parametrize("nx", [160, 352])
+def test_two_bubbles_with_barrier_parity(nx):
+    """Plain (160 columns) and staged (352) kernels with the barrier mask."""
+    ny, R, gap = 80, 12, 3.0
     b = [[nx / 2 - R - gap / 2, ny / 2, R], [nx / 2 + R + gap / 2, ny / 2, R]]
     rm = O.init_bubbles(O.make_params(nx, ny), b, RL, RG, 4.0)
     rg = 0.005 + 0.3 * (RL - rm) / (RL - RG)
