@@ -135,6 +135,27 @@ def lockstep_steps(jobs: list[_Job], budget_s: float, launch_s: float, s_per_upd
     return {j.req.rid: min(j.remaining, L) for j in jobs}
 
 
+def tiered_steps(jobs: list[_Job], budget_updates: float, big_updates: float, small_share: float = 0.5) -> dict[int, int]:
+    """Two classes: a job with at least `big_updates` cell updates left is
+    big. Small jobs share up to `small_share` of the budget by work
+    (`fair_steps`; all of it when no big job is resident); the oldest big job
+    (by arrival) takes the rest, and the other big jobs wait (0 steps), so
+    big requests are served first come, first served at nearly the full rate
+    while small ones keep overtaking them."""
+    small = [j for j in jobs if j.remaining * j.cells < big_updates]
+    big = sorted((j for j in jobs if j.remaining * j.cells >= big_updates), key=lambda j: (j.req.arrival_s, j.req.rid))
+    out = {j.req.rid: 0 for j in jobs}
+    used = 0.0
+    if small:
+        share = fair_steps(small, budget_updates * (small_share if big else 1.0))
+        out.update(share)
+        used = sum(share[j.req.rid] * j.cells for j in small)
+    if big:
+        j = big[0]
+        out[j.req.rid] = min(j.remaining, max(1, int(max(0.0, budget_updates - used) // j.cells)))
+    return out
+
+
 def _water_fill(jobs: list[_Job], budget: float, cost) -> dict[int, int]:
     out: dict[int, int] = {}
     left = float(budget)
@@ -175,14 +196,16 @@ class FoamServer:
     follow `policy`: "work" shares the cell updates equally (`fair_steps`;
     `quantum_updates` fixes the budget), "time" shares GPU time counting a
     launch cost per step (`fair_time_steps`), "lockstep" steps every box in
-    every launch (`lockstep_steps`). Every batch runs its plan as multi-rate
+    every launch (`lockstep_steps`), "tiered" serves big jobs first come,
+    first served beside equally shared small ones (`tiered_steps`). Every batch runs its plan as multi-rate
     steps (lbm_batch_step_each), so small boxes can take many cheap steps
     while large ones take few."""
     memory_budget_bytes: int
     max_boxes: int = 64
     quantum_s: float = 0.01
     quantum_updates: float | None = None
-    policy: str = "work"            # "work" | "time" | "lockstep"
+    policy: str = "work"            # "work" | "time" | "lockstep" | "tiered"
+    big_s: float = 0.05             # "tiered": a job with more work left than this much GPU time is big
     device: str = "cuda"
     keep_pops: bool = False
     stats: dict = field(default_factory=dict)
@@ -254,6 +277,9 @@ class FoamServer:
                 share = fair_time_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
             elif self.policy == "lockstep":
                 share = lockstep_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
+            elif self.policy == "tiered":
+                budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
+                share = tiered_steps(jobs_now, budget, self.big_s / model.s_per_update)
             else:
                 raise ValueError(f"unknown policy {self.policy!r}")
             ts = time.perf_counter()

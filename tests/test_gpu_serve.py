@@ -78,6 +78,23 @@ def test_time_share_and_lockstep_plans():
     assert lockstep_steps(jobs, 0.0, 1e-5, 1e-9) == {0: 1, 1: 1}
 
 
+def test_tiered_plan():
+    from paper_1708_01613_gb300.serve import _Job, tiered_steps
+
+    def job(rid, t, cells, rem):
+        return _Job(Request(rid, t, cells, 1, np.zeros((0, 3)), rem), None, rem, 0.0, 0)
+
+    jobs = [job(0, 0.2, 100, 10), job(1, 0.1, 10**6, 1000), job(2, 0.0, 10**6, 500), job(3, 0.3, 1000, 10**4)]
+    s = tiered_steps(jobs, 4e6, big_updates=1e8)
+    # small jobs 0 and 3 share half the budget (job 0 needs 1e3 updates, job 3
+    # gets the rest of 2e6); big job 2 arrived first and takes the remainder;
+    # big job 1 waits
+    assert s[0] == 10 and s[3] == int((2e6 - 1e3) // 1000)
+    assert s[2] == int((4e6 - 1e3 - s[3] * 1000) // 10**6) and s[1] == 0
+    only_small = tiered_steps(jobs[:1] + jobs[3:], 4e6, big_updates=1e8)
+    assert only_small == {0: 10, 3: int((4e6 - 1e3) // 1000)}
+
+
 @pytest.mark.gpu
 def test_request_larger_than_budget_is_refused():
     r = requests()[3]
