@@ -312,6 +312,8 @@ def run_gpu(args, world, rank, local):
                          "storage": "f32", "gpu_launches": int(r["launches"])}
     if not args.no_2c:
         out["two_component"] = run_two_component(args, dev, n, bub, RL, RG, world, peak, peak_kind)
+        if rank == 0 and not args.no_cpu:
+            out["two_component"]["cpu_baseline"] = cpu_sample_two_component()
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, dev, n, bub, RL, RG, world)
     if not args.no_batch:
@@ -571,6 +573,30 @@ def cpu_sample(steps: int, warmup: int, budget_s: float | None):
     s.step(steps)
     dt = time.perf_counter() - t0
     return n * n * steps / dt / 1e6, steps, dt, O.max_threads()
+
+
+def cpu_sample_two_component(budget_s: float = 4.0):
+    """The FP64 two-component oracle on a 256^2 box of the two-component
+    leg's kind (one melt bubble filled with gas, G_mm = -5.5, G_mg = 1.0,
+    barrier on, K = 10), timed for about `budget_s` seconds."""
+    import inputs
+    import oracle as O
+
+    n = 256
+    RL, RG = inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55
+    rm = O.init_bubbles(O.make_params(n, n), [[n / 2, n / 2, 30.0]], RL, RG, 4.0)
+    rg = 0.005 + 0.3 * (RL - rm) / (RL - RG)
+    s = O.OracleSim2(O.make_params2(n, n, G_mm=-5.5, G_mg=1.0, barrier=True, relabel_every=10))
+    s.init_density(rm, rg)
+    s.step(2)
+    t0 = time.perf_counter()
+    s.step(2)
+    steps = max(2, int(budget_s / ((time.perf_counter() - t0) / 2)))
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(n * n * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": O.max_threads(),
+            "kind": "oracle", "sample": f"{steps} steps of a 256^2 two-component box ({dt:.1f} s, FP64 oracle, OpenMP)"}
 
 
 def main():
