@@ -206,7 +206,8 @@ int relabel(lbm_handle* h) {
   if (handle_relabel_tiled(h)) {
     int totals[3];
     relabel_entry_sizes(c.nx, c.ny, &totals[0], &totals[1], &totals[2]);
-    CUDA_TRY(h, launch_relabel_boxes(c.storage, h->rbox(), h->rentries(), 1, totals, h->cur, h->stream));
+    CUDA_TRY(h, launch_relabel_boxes(c.storage, h->rbox(), h->rentries(), 1, totals, h->cur, h->stream,
+                                     h->comps() == 2));
     h->launches += 7;
     return LBM_OK;
   }

@@ -534,7 +534,10 @@ __device__ __forceinline__ int find_entry(const RelabelEntry* __restrict__ e, in
   return lo;
 }
 
-template <int S>
+// TWO: two-component boxes (FP32), which also get the mixture pressure; a
+// separate instantiation so that one-component relabels keep their register
+// budget.
+template <int S, bool TWO>
 __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* __restrict__ boxes,
                                                               const RelabelEntry* __restrict__ e, int m, int parity) {
   using T = typename Store<S>::T;
@@ -557,7 +560,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
   const float r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   const size_t c = r0 + x;
   B.rho[c] = r;
-  if (B.pr) {  // two components (FP32): the gas lattice follows the melt's nine planes
+  if (TWO) {  // two components (FP32): the gas lattice follows the melt's nine planes
     const float* pg = reinterpret_cast<const float*>(p) + (size_t)Q * N;
     float g = 0.f;
 #pragma unroll
@@ -697,6 +700,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_owner(const RelabelBox* __restri
   }
 }
 
+template <bool TWO>
 __global__ void __launch_bounds__(kTX * kTY) kb_rupture(const RelabelBox* __restrict__ boxes,
                                                         const RelabelEntry* __restrict__ e, int m) {
   const ListWalk lw = list_walk(boxes, e, m);
@@ -730,9 +734,9 @@ __global__ void __launch_bounds__(kTX * kTY) kb_rupture(const RelabelBox* __rest
         }
       const size_t cp = (size_t)wrap1(y + ey, ny) * nx + wrap1(x + ex, nx);
       const size_t cm = (size_t)wrap1(y - ey, ny) * nx + wrap1(x - ex, nx);
-      const float pp = B.pr ? B.pr[cp] : pressure_of(B.rho[cp], B.G, B.rho0);
-      const float p0 = B.pr ? B.pr[c] : pressure_of(B.rho[c], B.G, B.rho0);
-      const float pm = B.pr ? B.pr[cm] : pressure_of(B.rho[cm], B.G, B.rho0);
+      const float pp = TWO ? B.pr[cp] : pressure_of(B.rho[cp], B.G, B.rho0);
+      const float p0 = TWO ? B.pr[c] : pressure_of(B.rho[c], B.G, B.rho0);
+      const float pm = TWO ? B.pr[cm] : pressure_of(B.rho[cm], B.G, B.rho0);
       const float d2 = pp - 2.0f * p0 + pm;
       const int sg = (d2 > 0.f) - (d2 < 0.f);
       const int prevs = B.sgn[c];
@@ -942,20 +946,28 @@ void relabel_entry_sizes(int nx, int ny, int* tiles, int* scan, int* list) {
 }
 
 cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const RelabelEntry* entries, int m,
-                                 const int totals[3], int parity, cudaStream_t s) {
+                                 const int totals[3], int parity, cudaStream_t s, bool two) {
   if (m <= 0) return cudaSuccess;
   const dim3 block(kTX, kTY);
-  switch (storage) {
-    case LBM_F32: kb_density_label<LBM_F32><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
-    case LBM_F16_DEV: kb_density_label<LBM_F16_DEV><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
-    case LBM_BF16_DEV: kb_density_label<LBM_BF16_DEV><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
-    default: return cudaErrorInvalidValue;
+  if (two) {  // two components: FP32 only
+    if (storage != LBM_F32) return cudaErrorInvalidValue;
+    kb_density_label<LBM_F32, true><<<totals[0], block, 0, s>>>(boxes, entries, m, parity);
+  } else {
+    switch (storage) {
+      case LBM_F32: kb_density_label<LBM_F32, false><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
+      case LBM_F16_DEV: kb_density_label<LBM_F16_DEV, false><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
+      case LBM_BF16_DEV:
+        kb_density_label<LBM_BF16_DEV, false><<<totals[0], block, 0, s>>>(boxes, entries, m, parity);
+        break;
+      default: return cudaErrorInvalidValue;
+    }
   }
   kb_active<<<totals[1], kThreads, 0, s>>>(boxes, entries, m);
   kb_union<<<totals[2], block, 0, s>>>(boxes, entries, m);
   kb_flatten<<<totals[2], block, 0, s>>>(boxes, entries, m);
   kb_owner<<<totals[2], block, 0, s>>>(boxes, entries, m);
-  kb_rupture<<<totals[2], block, 0, s>>>(boxes, entries, m);
+  if (two) kb_rupture<true><<<totals[2], block, 0, s>>>(boxes, entries, m);
+  else kb_rupture<false><<<totals[2], block, 0, s>>>(boxes, entries, m);
   kb_mask<<<totals[2], block, 0, s>>>(boxes, entries, m);
   return cudaGetLastError();
 }

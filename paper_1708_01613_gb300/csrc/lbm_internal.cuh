@@ -250,8 +250,9 @@ struct RelabelEntry {
 // CTAs a box takes in each kind of phase.
 void relabel_entry_sizes(int nx, int ny, int* tiles, int* scan, int* list);
 // The seven phases over the first m entries; totals = entries[m]'s offsets.
+// two_component: the boxes are two-component (FP32; mixture pressure).
 cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const RelabelEntry* entries, int m,
-                                 const int totals[3], int parity, cudaStream_t s);
+                                 const int totals[3], int parity, cudaStream_t s, bool two_component = false);
 int mass_partials_needed();
 
 // Nucleation and growth (growth.cu). The gas census appends every cell with
