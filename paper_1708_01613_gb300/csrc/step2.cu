@@ -364,7 +364,9 @@ __global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Param
 
 template <bool MASKED, bool TAU_ONE>
 cudaError_t launch_step2_tma(const Step2Params& p, cudaStream_t s) {
-  constexpr int NS = 3, MINB = TAU_ONE ? 3 : 2;
+  // measured at 8192^2: with tau = 1, 2 stages at 4 CTAs per SM (56
+  // registers) edge out 3 stages at 3 CTAs; 2 CTAs per SM lose 25 %
+  constexpr int NS = TAU_ONE ? 2 : 3, MINB = TAU_ONE ? 4 : 2;
   auto kern = k_step2_tma<MASKED, TAU_ONE, NS, MINB>;
   constexpr size_t smem = smem2c_bytes<MASKED, NS>();
   static int resident = 0;  // per instantiation
