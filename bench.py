@@ -253,7 +253,7 @@ def run_gpu(args, world, rank, local):
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_cell": bytes_cell,
-                "kernel": ("k_step_tma" if storage == "f32" else "k_step_tma2") if n % 16 == 0 else "k_step_strip",
+                "kernel": "k_step_dyn" if n % 16 == 0 else "k_step_strip",
                 "kernel_ms_avg": round(kern_ms, 5),
                 "kernel_mlups": round(N / (kern_ms * 1e-3) / 1e6, 1),
                 "roofline_mlups": round(peak * 1e9 / bytes_cell / 1e6, 1)}

@@ -171,11 +171,13 @@ int64_t lbm_kernel_launches(const lbm_handle* h);
 
 /* Selects the fused-step kernel: 0 = automatic, 1 = plain-load kernel (any
  * box), 2 = TMA-staged kernel with one cell per thread (nx % 16 == 0 and
- * nx >= 272), 3 = TMA-staged kernel with two cells per thread
- * (nx % 16 == 0). Automatic picks 3 for 16-bit storage and 2 for FP32 where
- * the box allows, else 1. A variant the box does not allow returns
- * LBM_ENOTSUP. All variants compute the same operations in the same order
- * and give bitwise the same populations. */
+ * nx >= 272), 3 = TMA-staged kernel with two cells per thread, one row
+ * chunk per CTA (nx % 16 == 0), 4 = the same with row chunks drawn by the
+ * CTAs from a counter (nx % 16 == 0). Automatic picks 4 where the box
+ * allows, else 1. A variant the box does not allow returns LBM_ENOTSUP. All
+ * variants compute the same operations in the same order and give bitwise
+ * the same populations. The same handle must not be stepped by two streams
+ * at once (variant 4 keeps its chunk counter in the handle's workspace). */
 int lbm_set_step_variant(lbm_handle* h, int variant);
 
 /* Steps done since the last init/load. */

@@ -34,6 +34,8 @@ enum Flag : int {
   FLAG_OPENED = 2,    // cells opened by the latest rupture test
   FLAG_TILES = 3,     // tiles in the relabel work list
   FLAG_GAS = 4,       // gas points in the growth list
+  FLAG_ITEM = 5,      // work-item counter of the dynamically scheduled step (0 between launches)
+  FLAG_DONE = 6,      // CTAs of that launch that have finished (0 between launches)
   FLAG_HIST = 64,     // 64 histogram counters
   FLAG_COUNT = 128
 };
@@ -105,7 +107,8 @@ struct StepParams {
   int nx, ny;
   long long N;           // nx * ny (plane stride)
   int rows_per_chunk;    // rows marched by one CTA
-  int force_generic;     // kernel variant: 0 automatic, 1 plain loads, 2 one-cell staged, 3 two-cell staged
+  int force_generic;     // kernel variant: 0 automatic, 1 plain loads, 2 one-cell staged, 3 two-cell staged,
+                         // 4 two-cell staged with dynamically scheduled row chunks
   float tau, inv_tau, G, rho0, inv_rho0;
   float rho_ref;         // reference density of 16-bit deviations
   float wref[Q];         // w_i * rho_ref (16-bit deviation base)

@@ -305,7 +305,7 @@ def test_tma_staged_kernel_matches_plain_kernel_bitwise(storage, nx, ny, barrier
         rho = O.init_bubbles(O.make_params(nx, ny), b, RL, RG, 4.0)
     else:
         rho = inputs.noise_density(nx, ny, seed=9)
-    variants = (1, 2, 3) if nx >= 528 else (1, 2)
+    variants = (1, 2, 3, 4) if nx >= 528 else (1, 2, 4)
     sims = []
     for variant in variants:
         s = gpu_sim(nx, ny, rho, storage=storage, barrier=barrier, rho_ref=float(np.mean(rho)), tau=tau)
@@ -334,8 +334,12 @@ def test_step_variant_selection_errors():
     with pytest.raises(LbmError) as e:
         odd.set_step_variant(3)
     assert e.value.code == 6
+    with pytest.raises(LbmError) as e:
+        odd.set_step_variant(4)  # dynamic chunks: also the two-cell kernel
+    assert e.value.code == 6
+    sim.set_step_variant(4)
     with pytest.raises(LbmError):
-        sim.set_step_variant(4)
+        sim.set_step_variant(5)
     sim.set_step_variant(1)
     sim.step(1)
 
