@@ -219,12 +219,13 @@ constexpr size_t smem2c_bytes() {
 }
 
 // Lane l < 18 of the ninth warp copies plane l (melt 0-8, gas 9-17) of
-// stage k (output row y0 - 1 + k); lane 18 copies the mask row.
+// stage k (output row y0 - 1 + k) into the slot of the CTA's stage count gk;
+// lane 18 copies the mask row.
 template <bool MASKED, int NSTAGE>
-__device__ __forceinline__ void issue2c(const Step2Params& p, unsigned char* stages, uint64_t* bars, int k, int y0,
-                                        int x0, int lane) {
+__device__ __forceinline__ void issue2c(const Step2Params& p, unsigned char* stages, uint64_t* bars, unsigned gk, int k,
+                                        int y0, int x0, int lane) {
   constexpr uint32_t STAGE = stage2c_bytes<MASKED>();
-  const int slot = k % NSTAGE;
+  const int slot = (int)(gk % NSTAGE);
   unsigned char* st = stages + (size_t)slot * STAGE;
   uint64_t* bar = bars + slot;
   const int r = y0 - 1 + k;
@@ -245,38 +246,45 @@ __device__ __forceinline__ void issue2c(const Step2Params& p, unsigned char* sta
   }
 }
 
-template <bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
-__global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Params p) {
-  constexpr int STAGE = stage2c_bytes<MASKED>();
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* stages = smem;
-  float(*ring_m)[kBX2C + 2] = reinterpret_cast<float(*)[kBX2C + 2]>(smem + (size_t)NSTAGE * STAGE);
-  float(*ring_g)[kBX2C + 2] = ring_m + 4;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE + 2 * 4 * (kBX2C + 2) * 4);
-  int* abort_flag = reinterpret_cast<int*>(bars + NSTAGE);
+// Shared-memory layout of the staged kernel.
+template <bool MASKED, int NSTAGE>
+struct Smem2C {
+  unsigned char* stages;
+  float (*ring_m)[kBX2C + 2];
+  float (*ring_g)[kBX2C + 2];
+  uint64_t* bars;
+  int* abort_flag;
+  __device__ __forceinline__ explicit Smem2C(unsigned char* smem) {
+    constexpr int STAGE = stage2c_bytes<MASKED>();
+    stages = smem;
+    ring_m = reinterpret_cast<float(*)[kBX2C + 2]>(smem + (size_t)NSTAGE * STAGE);
+    ring_g = ring_m + 4;
+    bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * STAGE + 2 * 4 * (kBX2C + 2) * 4);
+    abort_flag = reinterpret_cast<int*>(bars + NSTAGE);
+  }
+};
 
+// The staged march of one chunk: columns x0 .. x0 + width, rows y0 .. y1.
+// `gstage` counts the stages this CTA consumed before (mbarrier phases carry
+// over between chunks). Returns false if a stage wait timed out (recorded;
+// the CTA must leave).
+template <bool MASKED, bool TAU_ONE, int NSTAGE>
+__device__ __forceinline__ bool march2c(const Step2Params& p, const Smem2C<MASKED, NSTAGE>& sm, int x0, int y0, int y1,
+                                        unsigned& gstage, int& bad) {
+  constexpr int STAGE = stage2c_bytes<MASKED>();
   float* __restrict__ dst = static_cast<float*>(p.dst);
   float* __restrict__ dstg = dst + (size_t)Q * p.N;
-  const int nx = p.nx, ny = p.ny;
+  const int nx = p.nx;
   const int tid = threadIdx.x;
   const bool helper = tid >= kBX2C;
   const int lane = tid & 31;
-  const int x0 = blockIdx.x * kBX2C;
   const int width = min(kBX2C, nx - x0);
   const bool active = !helper && tid < width;
-  const int y0 = blockIdx.y * p.rows_per_chunk;
-  const int y1 = min(y0 + p.rows_per_chunk, ny);
-  if (y0 >= y1) return;
   const int nst = (y1 - y0) + 2;  // stages = rows y0-1 .. y1
+  const unsigned g0 = gstage;
 
-  if (tid == 0) {
-    for (int q = 0; q < NSTAGE; ++q) mbar_init(bars + q, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
   if (helper)
-    for (int k = 0; k < NSTAGE - 1 && k < nst; ++k) issue2c<MASKED, NSTAGE>(p, stages, bars, k, y0, x0, lane);
+    for (int k = 0; k < NSTAGE - 1 && k < nst; ++k) issue2c<MASKED, NSTAGE>(p, sm.stages, sm.bars, g0 + k, k, y0, x0, lane);
 
   // halo lanes: lanes 0..8 the left cell (column x0 - 1), lanes 16..24 the
   // right one (column x0 + width), plane lane & 15 of the component summed
@@ -289,11 +297,11 @@ __global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Param
   float pm[Q], pg[Q];
   float rm_p = 1.f, jxm_p = 0.f, jym_p = 0.f, rg_p = 0.f, jxg_p = 0.f, jyg_p = 0.f;
   unsigned m_prev = 0;
-  int bad = 0, k_abort = 0;
+  int k_abort = -1;
   for (int k = 0; k < nst; ++k) {
-    const int slot = k % NSTAGE;
-    const unsigned char* st = stages + (size_t)slot * STAGE;
-    if (!mbar_wait(bars + slot, (uint32_t)((k / NSTAGE) & 1))) *abort_flag = 1;
+    const unsigned gk = g0 + k;
+    const unsigned char* st = sm.stages + (size_t)(gk % NSTAGE) * STAGE;
+    if (!mbar_wait(sm.bars + gk % NSTAGE, (gk / NSTAGE) & 1u)) *sm.abort_flag = 1;
     float fm[Q], fg[Q];
     float rm = 1.f, jxm = 0.f, jym = 0.f, rg = 0.f, jxg = 0.f, jyg = 0.f;
     unsigned m = 0;
@@ -305,8 +313,8 @@ __global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Param
       }
       mom(fm, rm, jxm, jym);
       mom(fg, rg, jxg, jyg);
-      ring_m[k & 3][jc] = psi2(rm, p);
-      ring_g[k & 3][jc] = psi2(rg, p);
+      sm.ring_m[k & 3][jc] = psi2(rm, p);
+      sm.ring_g[k & 3][jc] = psi2(rg, p);
       if (MASKED) m = st[2 * Q * kRow2C + tid];
     } else if (helper) {
 #pragma unroll
@@ -316,22 +324,23 @@ __global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Param
         v += __shfl_xor_sync(0xffffffffu, v, 2);
         v += __shfl_xor_sync(0xffffffffu, v, 4);
         v += __shfl_xor_sync(0xffffffffu, v, 8);
-        float(*ring)[kBX2C + 2] = comp ? ring_g : ring_m;
+        float(*ring)[kBX2C + 2] = comp ? sm.ring_g : sm.ring_m;
         if (lane == 0) ring[k & 3][0] = psi2(v, p);
         if (lane == 16) ring[k & 3][width + 1] = psi2(v, p);
       }
     }
     __syncthreads();
-    if (*abort_flag) {
+    if (*sm.abort_flag) {
       k_abort = k;
       break;
     }
     if (helper) {
-      if (k + NSTAGE - 1 < nst) issue2c<MASKED, NSTAGE>(p, stages, bars, k + NSTAGE - 1, y0, x0, lane);
+      if (k + NSTAGE - 1 < nst)
+        issue2c<MASKED, NSTAGE>(p, sm.stages, sm.bars, gk + NSTAGE - 1, k + NSTAGE - 1, y0, x0, lane);
     } else if (k >= 2 && active) {
       const int rc = y0 + k - 2;
-      finish2<TAU_ONE>(p, ring_m, ring_g, (k - 2) & 3, (k - 1) & 3, k & 3, jc, m_prev, pm, pg, rm_p, jxm_p, jym_p,
-                       rg_p, jxg_p, jyg_p, dst, dstg, (size_t)rc * nx + x0 + tid, bad);
+      finish2<TAU_ONE>(p, sm.ring_m, sm.ring_g, (k - 2) & 3, (k - 1) & 3, k & 3, jc, m_prev, pm, pg, rm_p, jxm_p,
+                       jym_p, rg_p, jxg_p, jyg_p, dst, dstg, (size_t)rc * nx + x0 + tid, bad);
     }
     if (!TAU_ONE) {
 #pragma unroll
@@ -348,18 +357,56 @@ __global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Param
     jyg_p = jyg;
     m_prev = m;
   }
-  if (*abort_flag) {
+  if (k_abort >= 0) {
     // a stage never completed: record it, then wait (bounded) for the copies
     // of every stage issued and not consumed before the CTA leaves
     if (tid == 0) {
       atomicOr(p.flags + FLAG_TIMEOUT, 1);
       const int issued = min(nst, k_abort + NSTAGE - 1);
-      for (int q = k_abort; q < issued; ++q) mbar_wait(bars + q % NSTAGE, (uint32_t)((q / NSTAGE) & 1), 500000000ull);
+      for (int q = k_abort; q < issued; ++q)
+        mbar_wait(sm.bars + (g0 + q) % NSTAGE, ((g0 + q) / NSTAGE) & 1u, 500000000ull);
     }
     __syncthreads();
-    return;
+    return false;
+  }
+  gstage = g0 + nst;
+  return true;
+}
+
+// As many CTAs as fit draw row chunks (strip w % gx, chunk w / gx of
+// `rows` rows) from a device counter until all are done, so fast CTAs take
+// more chunks; the last CTA to finish resets the counters for the next
+// launch.
+template <bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Params p, int rows, int gx, int nitems) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int item_sh;
+  const Smem2C<MASKED, NSTAGE> sm(smem);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NSTAGE; ++q) mbar_init(sm.bars + q, 1);
+    *sm.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  unsigned gstage = 0;
+  int bad = 0;
+  for (int guard = 0; guard < nitems + 1; ++guard) {
+    __syncthreads();  // the previous chunk's ring and item index are no longer read
+    if (threadIdx.x == 0) item_sh = atomicAdd(p.flags + FLAG_ITEM, 1);
+    __syncthreads();
+    const int w = item_sh;
+    if (w >= nitems) break;
+    const int y0 = (w / gx) * rows;
+    if (!march2c<MASKED, TAU_ONE, NSTAGE>(p, sm, (w % gx) * kBX2C, y0, min(y0 + rows, p.ny), gstage, bad)) break;
   }
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // every CTA arrives here after its last draw from the counter
+    if (atomicAdd(p.flags + FLAG_DONE, 1) == (int)gridDim.x - 1) {
+      p.flags[FLAG_ITEM] = 0;
+      p.flags[FLAG_DONE] = 0;
+    }
+  }
 }
 
 template <bool MASKED, bool TAU_ONE>
@@ -381,13 +428,13 @@ cudaError_t launch_step2_tma(const Step2Params& p, cudaStream_t s) {
     resident = (occ > 0 ? occ : 1) * sms;
   }
   const int gx = (p.nx + kBX2C - 1) / kBX2C;
-  int g = resident / gx;
-  if (g < 1) g = 1;
-  if (g > p.ny) g = p.ny;
-  Step2Params q = p;
-  q.rows_per_chunk = (p.ny + g - 1) / g;
-  const int gy = (p.ny + q.rows_per_chunk - 1) / q.rows_per_chunk;
-  kern<<<dim3(gx, gy), kThreads2C, smem, s>>>(q);
+  // about four chunks per resident CTA, at most 48 rows
+  long long r = ((long long)gx * p.ny + 4LL * resident - 1) / (4LL * resident);
+  const int rows = (int)(r < 1 ? 1 : (r > 48 ? 48 : r));
+  const long long items = (long long)gx * ((p.ny + rows - 1) / rows);
+  if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int nitems = (int)items;
+  kern<<<nitems < resident ? nitems : resident, kThreads2C, smem, s>>>(p, rows, gx, nitems);
   return cudaGetLastError();
 }
 
