@@ -699,12 +699,13 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
 }
 
-// One box, dynamically scheduled: as many CTAs as fit take row chunks
-// (strip w % gx, chunk w / gx of `rows` rows) from a device counter until
-// all are done. With chunks a few times shorter than a static split, CTAs
-// that march fast take more chunks and the launch does not wait for the
-// slowest of one-chunk-per-CTA (8192^2: FP16 0.51 -> 0.47 ms). The counters
-// are zero between launches: the last CTA to finish resets them.
+// One box, dynamically scheduled: as many CTAs as fit take row chunks (of
+// `rows` rows, gx strips) from a device counter until all are done. With
+// chunks a few times shorter than a static split, CTAs that march fast take
+// more chunks and the launch does not wait for the slowest of
+// one-chunk-per-CTA (8192^2: FP32 0.817 -> 0.757 ms, FP16 0.509 -> 0.481
+// ms). The counters are zero between launches: the last CTA to finish
+// resets them.
 template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_dyn(const StepParams p, int rows, int gx, int nitems) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -720,7 +721,21 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_dyn(const StepParams
     __syncthreads();
     const int w = item_sh;
     if (w >= nitems) break;
-    const int x0 = (w % gx) * kBX2, y0 = (w / gx) * rows;
+    // chunk order (measured): row-major for FP32; for 16-bit storage strip
+    // by strip, with the shorter last chunk row at the end (1.6 % faster)
+    int sx, cyk;
+    const int nch = (p.ny + rows - 1) / rows, full = gx * (nch - 1);
+    if (S == LBM_F32) {
+      sx = w % gx;
+      cyk = w / gx;
+    } else if (w < full) {
+      sx = w / (nch - 1);
+      cyk = w % (nch - 1);
+    } else {
+      sx = w - full;
+      cyk = nch - 1;
+    }
+    const int x0 = sx * kBX2, y0 = cyk * rows;
     const int y1 = min(y0 + rows, p.ny), width = min(kBX2, p.nx - x0);
     // full strips take the compile-time-width march (with tau != 1 the two
     // inlined copies would spill at this kernel's register budget)
