@@ -536,7 +536,7 @@ int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, float* best_ms_per_step) {
   if (trial_steps < 1) return bfail(b, LBM_EINVAL, "trial_steps must be >= 1");
   if (active_count(b) == 0) return bfail(b, LBM_EINVAL, "no active box");
   static const int strips[2] = {512, 256};
-  static const int rowsc[5] = {32, 64, 128, 256, 512};
+  static const int rowsc[5] = {32, 48, 64, 128, 256};  // 48: best for one large box
   const int use_graph = b->use_graph;
   b->use_graph = 0;
   cudaEvent_t e0, e1;
