@@ -174,7 +174,7 @@ int64_t lbm_kernel_launches(const lbm_handle* h);
  * nx >= 272), 3 = TMA-staged kernel with two cells per thread, one row
  * chunk per CTA (nx % 16 == 0), 4 = the same with row chunks drawn by the
  * CTAs from a counter (nx % 16 == 0). Automatic picks 4 where the box
- * allows, else 1. A variant the box does not allow returns LBM_ENOTSUP. All
+ * allows (3 when the box has no more chunks than CTAs fit the GPU), else 1. A variant the box does not allow returns LBM_ENOTSUP. All
  * variants compute the same operations in the same order and give bitwise
  * the same populations. The same handle must not be stepped by two streams
  * at once (variant 4 keeps its chunk counter in the handle's workspace). */

@@ -914,12 +914,18 @@ cudaError_t launch_dyn(const StepParams& p, cudaStream_t s) {
     resident = (occ > 0 ? occ : 1) * sm_count();
   }
   const int gx = (p.nx + kBX2 - 1) / kBX2;
-  // about four chunks per resident CTA, at most 48 rows (measured best at 8192^2)
-  long long r = ((long long)gx * p.ny + 4LL * resident - 1) / (4LL * resident);
+  // chunks of at most 48 rows (measured best at 8192^2), but no shorter than
+  // one chunk per resident CTA needs: a CTA pays a pipeline fill per chunk,
+  // so a mid-size box gets one chunk per CTA as a static split would
+  long long r = ((long long)gx * p.ny + resident - 1) / resident;
   const int rows = (int)(r < 1 ? 1 : (r > kDynRows ? kDynRows : r));
   const long long items = (long long)gx * ((p.ny + rows - 1) / rows);
   if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int nitems = (int)items;
+  // automatic choice: with no more chunks than resident CTAs there is nothing
+  // to balance, and the static split saves the counter's round trips (a
+  // few microseconds, a large part of a small box's step)
+  if (p.force_generic == 0 && nitems <= resident) return launch_tma2<S, MASKED, TAU_ONE>(p, s);
   const int grid = nitems < resident ? nitems : resident;
   kern<<<grid, kTmaThreads, smem, s>>>(p, rows, gx, nitems);
   return cudaGetLastError();
@@ -937,8 +943,9 @@ cudaError_t launch_strip(const StepParams& p, cudaStream_t s) {
 
 // Variant 0 (automatic): the two-cell staged march over dynamically
 // scheduled row chunks wherever rows are 16-byte multiples (measured fastest
-// for every storage: 8192^2 FP32 0.80 ms against 0.815 for the one-cell
-// static kernel), else plain loads; 1: plain loads; 2: one-cell staged;
+// for every storage: 8192^2 FP32 0.757 ms against 0.815 for the one-cell
+// static kernel; boxes with no more chunks than resident CTAs take the
+// static split of variant 3), else plain loads; 1: plain loads; 2: one-cell staged;
 // 3: two-cell staged, one chunk per CTA; 4: two-cell staged, dynamic chunks.
 template <int S, bool MASKED, bool TAU_ONE>
 cudaError_t launch_variant(const StepParams& p, cudaStream_t s) {

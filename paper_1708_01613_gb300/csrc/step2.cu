@@ -428,8 +428,9 @@ cudaError_t launch_step2_tma(const Step2Params& p, cudaStream_t s) {
     resident = (occ > 0 ? occ : 1) * sms;
   }
   const int gx = (p.nx + kBX2C - 1) / kBX2C;
-  // about four chunks per resident CTA, at most 48 rows
-  long long r = ((long long)gx * p.ny + 4LL * resident - 1) / (4LL * resident);
+  // chunks of at most 48 rows, but no shorter than one chunk per resident
+  // CTA needs (a CTA pays a pipeline fill per chunk)
+  long long r = ((long long)gx * p.ny + resident - 1) / resident;
   const int rows = (int)(r < 1 ? 1 : (r > 48 ? 48 : r));
   const long long items = (long long)gx * ((p.ny + rows - 1) / rows);
   if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
