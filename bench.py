@@ -625,6 +625,13 @@ def main():
         out["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                                "sample": f"{steps} steps of a 512^2 box at the workload's bubble density, "
                                          f"barrier on, K=10 ({dt:.1f} s, FP64 oracle, OpenMP)"}
+        import oracle as O
+
+        O.set_threads(1)
+        m1, s1, d1, _ = cpu_sample(0, 1, budget_s=4.0)
+        O.set_threads(cores)
+        out["cpu_baseline"]["single_thread"] = {"value": round(m1, 3), "unit": "MLUPS", "cores": 1,
+                                                "sample": f"{s1} steps of the same box ({d1:.1f} s, one thread)"}
     if world > 1:
         import torch.distributed as dist
 
