@@ -519,3 +519,36 @@ def test_config_1024_clustered_foam(K):
               f"gas {st['gas_fraction']:.5f} ({so['gas_fraction']:.5f})")
         assert abs(st["n_bubbles"] - so["n_bubbles"]) <= max(1, 0.1 * so["n_bubbles"])
         assert abs(st["gas_fraction"] - so["gas_fraction"]) <= 0.01
+
+
+def test_laplace_sweep_gpu():
+    """The configuration's static Laplace sweep (R = 10, 20, 40, 60, 20000
+    steps) on the GPU in FP32: p_in - p_out linear in 1/R (R^2 >= 0.999, intercept within
+    5 % of the smallest droplet's jump), and at R = 10 and 20 the jump equals
+    the oracle's within 1e-3. Liquid droplets in gas (small gas bubbles in a
+    closed box dissolve)."""
+    pts, first = [], {}
+    for R, L in ((10, 96), (20, 128), (40, 256), (60, 256)):
+        rho = O.init_bubbles(O.make_params(L, L), [[L / 2, L / 2, R]], RG, RL, 4.0)  # liquid inside
+        sim = gpu_sim(L, L, rho)
+        sim.step(20000)
+        fl = sim.read("rho", "p")
+        yy, xx = np.mgrid[0:L, 0:L]
+        d = np.hypot(xx - L / 2, yy - L / 2)
+        A = np.sum((fl["rho"].astype(np.float64) - RG) / (RL - RG))
+        dp = float(fl["p"][d < R - 5].mean() - fl["p"][d > R + 10].mean())
+        pts.append((1 / math.sqrt(A / math.pi), dp))
+        if R <= 20:
+            ref = oracle_sim(L, L, rho)
+            ref.step(20000)
+            fo = ref.fields()
+            dpo = float(fo["p"][d < R - 5].mean() - fo["p"][d > R + 10].mean())
+            first[R] = (dp, dpo)
+            assert dp == pytest.approx(dpo, rel=1e-3)
+    xs, dps = np.array(pts).T
+    slope, icpt = np.polyfit(xs, dps, 1)
+    fit = slope * xs + icpt
+    r2 = 1 - np.sum((dps - fit) ** 2) / np.sum((dps - dps.mean()) ** 2)
+    print(f"GPU Laplace: points {pts}, sigma {slope:.5f}, intercept {icpt:.2e}, R^2 {r2:.6f}, vs oracle {first}")
+    assert slope > 0 and r2 >= 0.999
+    assert abs(icpt) <= 0.05 * dps[0]
