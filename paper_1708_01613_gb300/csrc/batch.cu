@@ -436,7 +436,8 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
   if (active_count(b) == 0 || nsteps == 0) return LBM_OK;
   int rc;
   if ((rc = enter(b))) return rc;
-  if ((rc = upload(b))) return rc;
+  rc = upload(b);
+  if (rc) return rc;
   int64_t left = nsteps;
   // blocks start where the batch counter is a multiple of K; each box's
   // relabel offset to that counter is fixed while the membership is, so a
