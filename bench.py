@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--serve-load", type=float, default=0.9,
                     help="offered load as a fraction of the one-box-at-a-time throughput")
     ap.add_argument("--batch-step-scale", type=float, default=1.0)
+    ap.add_argument("--clocks-dir", default=os.path.join(ROOT, "bench_out"),
+                    help="directory for the nvidia-smi clock samples taken during the timed region")
     return ap.parse_args()
 
 
@@ -100,10 +102,10 @@ def kernel_traffic(storage: str):
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, directory: str):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(directory, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -213,7 +215,7 @@ def run_gpu(args, world, rank, local):
               for _ in range(steps)]
         t_all0 = torch.cuda.Event(enable_timing=True)
         t_all1 = torch.cuda.Event(enable_timing=True)
-        sampler = ClockSampler(local) if sample_clocks else None
+        sampler = ClockSampler(local, args.clocks_dir) if sample_clocks else None
         if sampler:
             sampler.start()
         barrier(world)

@@ -262,7 +262,8 @@ class Simulation:
             self._call("lbm_load_populations", C.c_void_p(a.ctypes.data), 0)
 
     def set_step_variant(self, variant: int) -> None:
-        """0 automatic, 1 plain-load kernel, 2 TMA-staged kernel."""
+        """0 automatic, 1 plain loads, 2 one-cell staged, 3 two-cell staged,
+        4 two-cell staged with dynamically drawn row chunks (3 and 4 need nx % 16 == 0)."""
         self._call("lbm_set_step_variant", int(variant))
 
     def step(self, n: int = 1) -> None:
