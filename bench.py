@@ -85,17 +85,31 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(storage: str):
-    """DRAM bytes per launch of the fused step from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+TRAFFIC_SOURCES = {"step": ("step.cu", "lbm_internal.cuh", "tma.cuh"),
+                   "step2": ("step2.cu", "lbm_internal.cuh", "tma.cuh")}
+
+
+def sources_sha256(kind: str) -> str:
+    """Hash of the sources a step kernel is built from."""
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[kind]:
+        h.update(open(os.path.join(ROOT, "paper_1708_01613_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def kernel_traffic(key: str, cells: int):
+    """DRAM bytes per launch of a fused step kernel ("f32", "f16" or
+    "two_component") from the committed ncu summary, if it was taken on the
+    current kernel sources and on a box of this many cells (else None)."""
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = open(os.path.join(ROOT, "paper_1708_01613_gb300", "csrc", "step.cu"), "rb").read()
-    if d.get("step_cu_sha256") != hashlib.sha256(src).hexdigest():
+    entry = d.get(key, {})
+    kind = "step2" if key == "two_component" else "step"
+    if d.get("cells") != cells or d.get("sources_sha256", {}).get(kind) != sources_sha256(kind):
         return None
-    v = d.get(storage, {}).get("bytes_per_launch_full")
+    v = entry.get("bytes_per_launch_full")
     return float(v) if v else None
 
 
@@ -249,7 +263,7 @@ def run_gpu(args, world, rank, local):
         bytes_cell = 2 * 9 * eb + 1
         kern_ms = statistics.mean(r["plain"]) if r["plain"] else r["total_ms"] / args.steps
         achieved = bytes_cell * N / (kern_ms * 1e-3) / 1e9
-        traffic = kernel_traffic(storage)
+        traffic = kernel_traffic(storage, N)
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"
@@ -372,7 +386,8 @@ def run_two_component(args, dev, n, bub, RL, RG, world, peak, peak_kind):
     out = {"value": round(world * N * steps / (total * 1e-3) / 1e6, 1), "unit": "MLUPS",
            "ms_per_step": round(total / steps, 5), "storage": "f32", "components": 2,
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(achieved / peak, 4), "algorithmic_bytes_per_cell": bytes_cell,
+                        "frac": round(achieved / peak, 4), "traffic": kernel_traffic("two_component", N),
+                        "algorithmic_bytes_per_cell": bytes_cell,
                         "kernel": "k_step2_tma" if n % 16 == 0 and n >= 272 else "k_step2_strip",
                         "kernel_ms_avg": round(kern_ms, 5), "peak_kind": peak_kind},
            "gpu_launches": int(sim.kernel_launches - l0)}

@@ -98,6 +98,27 @@ struct Store<LBM_BF16_DEV> {
 
 inline int storage_bytes(int s) { return s == LBM_F32 ? 4 : 2; }
 
+// Row-chunk height of a launch whose `resident` CTAs draw chunks (gx strips
+// by ny rows) from a counter. Chunks of max_rows rows give `items48` chunks;
+// if those make at least keep_waves waves (chunks / resident CTAs), the last
+// wave's tail is small beside the whole and max_rows stays. Otherwise the
+// height is the one that fills a whole number of waves: the fewest that
+// max_rows allows, but at least min_waves once the chunks overflow one wave
+// (more, shorter chunks let the fast CTAs take more). A last wave that
+// fills only part of the GPU leaves the rest idle for a whole chunk time.
+inline int dyn_chunk_rows(long long gx, long long ny, long long resident, int max_rows, int keep_waves,
+                          int min_waves) {
+  if (gx < 1 || ny < 1 || resident < 1 || max_rows < 1) return 1;
+  const long long items = gx * ((ny + max_rows - 1) / max_rows);
+  if (items >= (long long)keep_waves * resident) return max_rows;
+  long long waves = (items + resident - 1) / resident;
+  if (items > resident && waves < min_waves) waves = min_waves;
+  long long per = waves * resident / gx;  // chunks per strip
+  if (per < 1) per = 1;
+  const long long rows = (ny + per - 1) / per;
+  return (int)(rows < 1 ? 1 : (rows > max_rows ? max_rows : rows));
+}
+
 // Arguments of the fused step kernel.
 struct StepParams {
   const void* src;       // populations after collision of the previous step

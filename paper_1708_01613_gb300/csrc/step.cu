@@ -914,11 +914,12 @@ cudaError_t launch_dyn(const StepParams& p, cudaStream_t s) {
     resident = (occ > 0 ? occ : 1) * sm_count();
   }
   const int gx = (p.nx + kBX2 - 1) / kBX2;
-  // chunks of at most 48 rows (measured best at 8192^2), but no shorter than
-  // one chunk per resident CTA needs: a CTA pays a pipeline fill per chunk,
-  // so a mid-size box gets one chunk per CTA as a static split would
-  long long r = ((long long)gx * p.ny + resident - 1) / resident;
-  const int rows = (int)(r < 1 ? 1 : (r > kDynRows ? kDynRows : r));
+  // 48-row chunks (best at 8192^2, 4.5 waves) unless they make fewer than
+  // four waves; then whole waves: the fewest for 16-bit storage, at least
+  // four for FP32 (4096^2: FP16 0.170 -> 0.135 ms, FP32 0.214 -> 0.207 ms;
+  // 5120^2: 0.224 -> 0.207, 0.320 -> 0.309; 6144^2: 0.305 -> 0.287,
+  // 0.442 -> 0.437). A box of at most one wave gets one chunk per CTA.
+  const int rows = dyn_chunk_rows(gx, p.ny, resident, kDynRows, 4, S == LBM_F32 ? 4 : 1);
   const long long items = (long long)gx * ((p.ny + rows - 1) / rows);
   if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int nitems = (int)items;
