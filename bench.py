@@ -562,7 +562,8 @@ def run_e2e(args, dev, n, bub, RL, RG, world):
     lib.lbm_destroy(h)
     dt = max_over_ranks(world, t1 - t0, dev)
     return {"value": round(world * N * job_steps * iters / dt / 1e6, 1), "unit": "MLUPS",
-            "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 4 * N,
+            "h2d_bytes_per_step": 8 * N // job_steps, "d2h_bytes_per_step": 4 * N // job_steps,
+            "h2d_bytes_per_job": 8 * N, "d2h_bytes_per_job": 4 * N,
             "job": f"init_density(host FP64) + {job_steps} steps + read_fields(RHO, host)",
             "steps_per_job": job_steps, "jobs": iters}
 
