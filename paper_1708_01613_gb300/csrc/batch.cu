@@ -102,18 +102,38 @@ void drop_graphs(lbm_batch* b) {
 
 // Work items. A CTA walks its item row by row, each row a dependent
 // load-compute-store round of a few microseconds, so a launch lasts about
-// (rows per item) x (items per CTA) such rounds. Chunks are therefore no
-// taller than needed to give every resident CTA one item (and at most the
-// tuned height). For multi-rate steps (`spread`) a box also gets at least
-// kMinItems items, so that the launches over a few small boxes at the end
-// of a call stay short too.
+// (rows per item) x (items per CTA) such rounds. While the tuned height
+// gives at least four waves of items over the resident CTAs it stays;
+// otherwise chunks take the smallest height whose items fill the fewest
+// whole waves (at least four for FP32 once one is exceeded), as for a lone
+// box: a fractional last wave idles the rest of the GPU for a chunk time,
+// and with less than one wave every resident CTA gets one item. For
+// multi-rate steps (`spread`) a box also gets at least kMinItems items, so
+// that the launches over a few small boxes at the end of a call stay short
+// too.
 void build_items(lbm_batch* b, bool spread) {
   b->items.clear();
-  long long total_rows = 0;
-  for (int i = 0; i < b->n; ++i)
-    if (b->active[i]) total_rows += (long long)((b->h[i]->cfg.nx + b->strip - 1) / b->strip) * b->h[i]->cfg.ny;
   const int res = std::max(1, batch_resident_ctas(b->storage, b->masked != 0, b->tau_one != 0));
-  const int rows_all = (int)std::max(1LL, std::min<long long>(b->rows, (total_rows + res - 1) / res));
+  auto count = [&](int rows) {
+    long long c = 0;
+    for (int i = 0; i < b->n; ++i)
+      if (b->active[i])
+        c += (long long)((b->h[i]->cfg.nx + b->strip - 1) / b->strip) * ((b->h[i]->cfg.ny + rows - 1) / rows);
+    return c;
+  };
+  int rows_all = std::max(1, b->rows);
+  const long long items_tuned = count(rows_all);
+  if (items_tuned > 0 && items_tuned < 4LL * res) {
+    long long waves = (items_tuned + res - 1) / res;
+    if (b->storage == LBM_F32 && items_tuned > res && waves < 4) waves = 4;
+    int lo = 1, hi = rows_all;  // smallest height whose items fit `waves` waves
+    while (lo < hi) {
+      const int mid = lo + (hi - lo) / 2;
+      if (count(mid) <= waves * res) hi = mid;
+      else lo = mid + 1;
+    }
+    rows_all = lo;
+  }
   for (int i = 0; i < b->n; ++i) {
     if (!b->active[i]) continue;
     const int nx = b->h[i]->cfg.nx, ny = b->h[i]->cfg.ny;
