@@ -431,6 +431,46 @@ def test_dynamic_chunks_counter_survives_mixed_variants(storage):
     assert np.array_equal(mixed.read("pops")["pops"], plain.read("pops")["pops"])
 
 
+@pytest.mark.parametrize("storage,nx,ny", [("f32", 4096, 4096), ("f16", 4096, 4096), ("f16", 6144, 3072)])
+def test_whole_wave_chunks_match_plain_kernel(storage, nx, ny):
+    """Mid-size boxes, where the automatic step draws chunks of the height
+    that fills whole waves of resident CTAs (4096^2: 14 rows FP32, 27 rows
+    FP16; 6144 x 3072: 31 rows, ragged last chunk row), give bitwise the
+    plain kernel's populations and masks over steps with relabels."""
+    import torch
+
+    pair = two_bubbles(nx, ny, R=20, gap=3.0)  # a film in the middle of the box
+    bub = [b for b in inputs.poisson_disk_bubbles(nx, ny, 60, 8.0, 48.0, 2.0, seed=17)
+           if all(math.hypot(b[0] - q[0], b[1] - q[1]) > b[2] + q[2] + 12 for q in pair)] + pair
+    kw = dict(storage=storage, barrier=True, relabel_every=3)
+    auto = gpu_sim(nx, ny, bubbles=bub, rho_ref=RL, **kw)
+    plain = gpu_sim(nx, ny, bubbles=bub, rho_ref=RL, **kw)
+    plain.set_step_variant(1)
+    auto.step(7)
+    plain.step(7)
+    a, p = auto.read("pops", "mask", device=True), plain.read("pops", "mask", device=True)
+    assert torch.equal(a["pops"], p["pops"]) and torch.equal(a["mask"], p["mask"])
+    assert bool(a["mask"].any())
+
+
+def test_two_component_whole_wave_chunks_empty_gas():
+    """Two-component box of 3072^2 (16-row chunks, four waves) with an empty
+    gas lattice stays with the one-component box, as in the small case."""
+    n = 3072
+    bub = inputs.poisson_disk_bubbles(n, n, 30, 8.0, 48.0, 2.0, seed=19)
+    one = gpu_sim(n, n, bubbles=bub, barrier=True, relabel_every=5, rho_ref=RL)
+    rho = one.read("rho")["rho"].astype(np.float64)
+    one.init_density(rho)
+    two = Simulation(make_config(n, n, components=2, barrier=True, relabel_every=5, G_mg=1.0))
+    two.init_density(rho, np.zeros_like(rho))
+    one.step(12)
+    two.step(12)
+    p1, p2 = one.read("pops")["pops"], two.read("pops")["pops"]
+    assert not p2[9:].any()
+    assert rel_inf(p2[:9], p1) < 1e-5
+    assert np.array_equal(two.read("mask")["mask"], one.read("mask")["mask"])
+
+
 @pytest.fixture(scope="module")
 def foam_oracle_1000():
     """The FP64 oracle's statistics of a coarsening 512^2 foam (40 Poisson-disk
