@@ -427,9 +427,12 @@ __global__ void __launch_bounds__(kThreads2C, MINB) k_step2_tma(const Step2Param
 
 template <bool MASKED, bool TAU_ONE>
 cudaError_t launch_step2_tma(const Step2Params& p, cudaStream_t s) {
-  // measured at 8192^2: with tau = 1, 2 stages at 4 CTAs per SM (56
-  // registers) edge out 3 stages at 3 CTAs; 2 CTAs per SM lose 25 %
-  constexpr int NS = TAU_ONE ? 2 : 3, MINB = TAU_ONE ? 4 : 2;
+  // measured at 8192^2 with tau = 1: since the per-cell arithmetic was cut
+  // the kernel waits on its staged rows, and 3 stages at 3 CTAs per SM (72
+  // registers) beat 2 stages at 4 (1.621 -> 1.498 ms; 4096^2 0.433 ->
+  // 0.405, 3072^2 0.261 -> 0.237); before the cut 2 at 4 edged out 3 at 3.
+  // tau != 1 keeps both components' populations across the barrier: 3 at 2.
+  constexpr int NS = 3, MINB = TAU_ONE ? 3 : 2;
   auto kern = k_step2_tma<MASKED, TAU_ONE, NS, MINB>;
   constexpr size_t smem = smem2c_bytes<MASKED, NS>();
   static int resident = 0;  // per instantiation
@@ -444,9 +447,10 @@ cudaError_t launch_step2_tma(const Step2Params& p, cudaStream_t s) {
     resident = (occ > 0 ? occ : 1) * sms;
   }
   const int gx = (p.nx + kBX2C - 1) / kBX2C;
-  // 48-row chunks when they make at least eight waves (8192^2: nine), else
-  // whole waves, at least four once one is exceeded (4096^2: 0.493 -> 0.432
-  // ms; 3072^2: 0.325 -> 0.27; 6144^2: 0.982 -> 0.96)
+  // 48-row chunks when they make at least eight waves (8192^2: twelve),
+  // else whole waves, at least four once one is exceeded (measured with 2
+  // stages at 4 CTAs per SM: 4096^2 0.493 -> 0.432 ms, 3072^2 0.325 ->
+  // 0.262, 6144^2 0.982 -> 0.935)
   const int rows = dyn_chunk_rows(gx, p.ny, resident, 48, 8, 4);
   const long long items = (long long)gx * ((p.ny + rows - 1) / rows);
   if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
