@@ -914,9 +914,10 @@ cudaError_t launch_dyn(const StepParams& p, cudaStream_t s) {
     resident = (occ > 0 ? occ : 1) * sm_count();
   }
   const int gx = (p.nx + kBX2 - 1) / kBX2;
-  // 48-row chunks (best at 8192^2, 4.5 waves) unless they make fewer than
-  // four waves; then whole waves: the fewest for 16-bit storage, at least
-  // four for FP32 (4096^2: FP16 0.170 -> 0.135 ms, FP32 0.214 -> 0.207 ms;
+  // 48-row chunks (best at 8192^2: 4.5 waves of 608 CTAs for 16-bit
+  // storage, 6 of 456 for FP32) unless they make fewer than four waves;
+  // then whole waves: the fewest for 16-bit storage, at least four for FP32
+  // (4096^2: FP16 0.170 -> 0.135 ms, FP32 0.214 -> 0.205 ms;
   // 5120^2: 0.224 -> 0.207, 0.320 -> 0.309; 6144^2: 0.305 -> 0.287,
   // 0.442 -> 0.437). A box of at most one wave gets one chunk per CTA.
   const int rows = dyn_chunk_rows(gx, p.ny, resident, kDynRows, 4, S == LBM_F32 ? 4 : 1);

@@ -434,7 +434,7 @@ def test_dynamic_chunks_counter_survives_mixed_variants(storage):
 @pytest.mark.parametrize("storage,nx,ny", [("f32", 4096, 4096), ("f16", 4096, 4096), ("f16", 6144, 3072)])
 def test_whole_wave_chunks_match_plain_kernel(storage, nx, ny):
     """Mid-size boxes, where the automatic step draws chunks of the height
-    that fills whole waves of resident CTAs (4096^2: 14 rows FP32, 27 rows
+    that fills whole waves of resident CTAs (4096^2: 18 rows FP32, 27 rows
     FP16; 6144 x 3072: 31 rows, ragged last chunk row), give bitwise the
     plain kernel's populations and masks over steps with relabels."""
     import torch
