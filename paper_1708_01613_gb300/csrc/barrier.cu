@@ -581,6 +581,62 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
   }
 }
 
+template <int S>
+__device__ __forceinline__ float dec16(unsigned short v) {
+  if constexpr (S == LBM_F16_DEV) return __half2float(__ushort_as_half(v));
+  else return __bfloat162float(__ushort_as_bfloat16(v));
+}
+
+// 16-bit storage: 16 x 8 threads per 32 x 8 tile, two cells (x, x + 1) per
+// thread from 32-bit loads, so a warp instruction moves 128 bytes as for
+// FP32. A plane the pull shifts by one column takes its pair (source columns
+// s, s + 1 with s odd) from the high half of one word and the low half of the
+// next; where the pull wraps around the box, from two 16-bit loads. Each
+// cell's arithmetic is kb_density_label's, so densities, labels and tile
+// flags are bitwise the same.
+template <int S>
+__global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const RelabelBox* __restrict__ boxes,
+                                                                    const RelabelEntry* __restrict__ e, int m,
+                                                                    int parity) {
+  const int k = find_entry<kOffTiles>(e, m, blockIdx.x);
+  const RelabelBox& B = boxes[e[k].box];
+  const int t = blockIdx.x - e[k].off_tiles;
+  const unsigned short* p = static_cast<const unsigned short*>(B.pops[B.cur ^ parity]);
+  const int nx = B.nx, ny = B.ny;  // nx % 32 == 0: x even, rows start on 4-byte boundaries
+  const size_t N = (size_t)nx * ny;
+  const int x = (t % B.ntx) * kTX + 2 * threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+  const size_t r0 = (size_t)y * nx, rm = (size_t)wrap1(y - 1, ny) * nx, rp = (size_t)wrap1(y + 1, ny) * nx;
+  float f0[Q], f1[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+    const unsigned short* q = p + (size_t)i * N + row;
+    const int s = x - cx(i);  // cell x pulls from column s, cell x + 1 from s + 1
+    uint32_t bits;
+    if (cx(i) == 0) {
+      bits = __ldg(reinterpret_cast<const uint32_t*>(q + x));
+    } else if (s >= 0 && s + 1 < nx) {
+      const uint32_t* w = reinterpret_cast<const uint32_t*>(q);
+      bits = __byte_perm(__ldg(w + ((s - 1) >> 1)), __ldg(w + ((s + 1) >> 1)), 0x5432);
+    } else {
+      bits = (uint32_t)__ldg(q + wrap1(s, nx)) | ((uint32_t)__ldg(q + wrap1(s + 1, nx)) << 16);
+    }
+    f0[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)(bits & 0xffffu)));
+    f1[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)(bits >> 16)));
+  }
+  const float ra = ((f0[0] + f0[1]) + (f0[2] + f0[3])) + ((f0[4] + f0[5]) + (f0[6] + f0[7])) + f0[8];
+  const float rb = ((f1[0] + f1[1]) + (f1[2] + f1[3])) + ((f1[4] + f1[5]) + (f1[6] + f1[7])) + f1[8];
+  const size_t c = r0 + x;
+  *reinterpret_cast<float2*>(B.rho + c) = make_float2(ra, rb);
+  const bool ga = ra < B.threshold, gb = rb < B.threshold;
+  *reinterpret_cast<int2*>(B.label + c) = make_int2(ga ? (int32_t)c : -1, gb ? (int32_t)(c + 1) : -1);
+  const int any = __syncthreads_or(ga || gb);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    B.tile_gas[t] = (uint8_t)(any != 0);
+    if (t == 0) B.flags[FLAG_TILES] = 0;  // the tile list is rebuilt by the next phase
+  }
+}
+
 // Also appends every tile that needs a visit (active now or at the previous
 // relabel) to the box's list; the order of the list does not affect any
 // result.
@@ -955,9 +1011,11 @@ cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const Rel
   } else {
     switch (storage) {
       case LBM_F32: kb_density_label<LBM_F32, false><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
-      case LBM_F16_DEV: kb_density_label<LBM_F16_DEV, false><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
+      case LBM_F16_DEV:
+        kb_density_label16<LBM_F16_DEV><<<totals[0], dim3(kTX / 2, kTY), 0, s>>>(boxes, entries, m, parity);
+        break;
       case LBM_BF16_DEV:
-        kb_density_label<LBM_BF16_DEV, false><<<totals[0], block, 0, s>>>(boxes, entries, m, parity);
+        kb_density_label16<LBM_BF16_DEV><<<totals[0], dim3(kTX / 2, kTY), 0, s>>>(boxes, entries, m, parity);
         break;
       default: return cudaErrorInvalidValue;
     }
