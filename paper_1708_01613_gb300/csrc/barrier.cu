@@ -710,6 +710,32 @@ __global__ void __launch_bounds__(kTX * kTY) kb_flatten(const RelabelBox* __rest
   if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
 }
 
+// Nearest labelled cell within radius R of the window position row0 (window
+// width W), ties to the smaller label; -1 if none. Shells of equal squared
+// distance are scanned in increasing order and the first shell holding a
+// label decides: the unsigned minimum of the labels in it (-1 is the
+// largest unsigned value) is the minimum of (d^2, label). With R known at
+// compile time every offset is one shared load and one min.
+template <int R>
+__device__ __forceinline__ int nearest_label(const int* row0) {
+  constexpr int W = kTX + 2 * R;
+  unsigned best = 0xffffffffu;
+#pragma unroll
+  for (int S = 1; S <= R * R; ++S) {
+    bool any = false;
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx)
+        if (dx * dx + dy * dy == S) {
+          best = min(best, (unsigned)row0[dy * W + dx]);
+          any = true;
+        }
+    if (any && best != 0xffffffffu) break;
+  }
+  return (int)best;
+}
+
 __global__ void __launch_bounds__(kTX * kTY) kb_owner(const RelabelBox* __restrict__ boxes,
                                                       const RelabelEntry* __restrict__ e, int m) {
   __shared__ int32_t sl[(kTY + 2 * kOMaxR) * (kTX + 2 * kOMaxR)];
@@ -736,7 +762,9 @@ __global__ void __launch_bounds__(kTX * kTY) kb_owner(const RelabelBox* __restri
     __syncthreads();
     const int* row0 = sl + (threadIdx.y + R) * W + threadIdx.x + R;
     int result = row0[0];
-    if (result < 0) {
+    if (result < 0 && R == 4) {  // the default zone radius
+      result = nearest_label<4>(row0);
+    } else if (result < 0) {
       int bd = 0x7fffffff;
       for (int dy = -R; dy <= R; ++dy) {
         const int* rowp = row0 + dy * W;
