@@ -537,6 +537,43 @@ __device__ __forceinline__ int find_entry(const RelabelEntry* __restrict__ e, in
 // TWO: two-component boxes (FP32), which also get the mixture pressure; a
 // separate instantiation so that one-component relabels keep their register
 // budget.
+// Union-find inside one 32 x 8 tile in shared memory (local indices
+// ly * kTX + lx, -1 for liquid), hooking the larger root under the smaller,
+// so a root is the smallest local index of its piece. Bounded like the
+// global version.
+__device__ int tile_find(const int* sp, int a, int* fail) {
+  for (int it = 0; it < kTX * kTY; ++it) {
+    const int p = sp[a];
+    if (p == a) return a;
+    a = p;
+  }
+  *fail = 1;
+  return a;
+}
+
+__device__ void tile_unite(int* sp, int a, int b, int* fail) {
+  for (int it = 0; it < kTX * kTY; ++it) {
+    a = tile_find(sp, a, fail);
+    b = tile_find(sp, b, fail);
+    if (a == b) return;
+    if (a < b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicMin(&sp[a], b);
+    if (old == a) return;
+    a = old;
+  }
+  *fail = 1;
+}
+
+// Global index of the tile-local root of local cell li (a gas cell).
+__device__ __forceinline__ int32_t tile_root_index(const int* sp, int li, int x0, int y0, int nx, int* fail) {
+  const int r = tile_find(sp, li, fail);
+  return (int32_t)((y0 + r / kTX) * nx + x0 + r % kTX);
+}
+
 template <int S, bool TWO>
 __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* __restrict__ boxes,
                                                               const RelabelEntry* __restrict__ e, int m, int parity) {
@@ -573,8 +610,25 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
     B.pr[c] = (r + g) * (1.0f / 3.0f) + (B.G * a * a + 2.0f * B.G_mg * a * b + B.G_gg * b * b) * (1.0f / 6.0f);
   }
   const bool gas = r < B.threshold;
-  B.label[c] = gas ? (int32_t)c : -1;
+  // gas cells joined inside the tile here (shared-memory union-find); each
+  // starts the global union-find pointing at the smallest index of its piece
+  // of the tile, and the union phase joins the pieces across tile borders
+  __shared__ int sp[kTX * kTY];
+  const int li = threadIdx.y * kTX + threadIdx.x;
+  sp[li] = gas ? li : -1;
   const int any = __syncthreads_or(gas);
+  int32_t lab = -1;
+  if (any) {
+    int fail = 0;
+    if (gas) {
+      if (threadIdx.x + 1 < kTX && sp[li + 1] >= 0) tile_unite(sp, li, li + 1, &fail);
+      if (threadIdx.y + 1 < kTY && sp[li + kTX] >= 0) tile_unite(sp, li, li + kTX, &fail);
+    }
+    __syncthreads();
+    if (gas) lab = tile_root_index(sp, li, x - threadIdx.x, y - threadIdx.y, nx, &fail);
+    if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
+  }
+  B.label[c] = lab;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     B.tile_gas[t] = (uint8_t)(any != 0);
     if (t == 0) B.flags[FLAG_TILES] = 0;  // the tile list is rebuilt by the next phase
@@ -629,8 +683,29 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
   const size_t c = r0 + x;
   *reinterpret_cast<float2*>(B.rho + c) = make_float2(ra, rb);
   const bool ga = ra < B.threshold, gb = rb < B.threshold;
-  *reinterpret_cast<int2*>(B.label + c) = make_int2(ga ? (int32_t)c : -1, gb ? (int32_t)(c + 1) : -1);
+  __shared__ int sp[kTX * kTY];  // tile-local union-find, as in kb_density_label
+  const int la = threadIdx.y * kTX + 2 * threadIdx.x, lb = la + 1;
+  sp[la] = ga ? la : -1;
+  sp[lb] = gb ? lb : -1;
   const int any = __syncthreads_or(ga || gb);
+  int32_t laba = -1, labb = -1;
+  if (any) {
+    int fail = 0;
+    if (ga) {
+      if (gb) tile_unite(sp, la, lb, &fail);
+      if (threadIdx.y + 1 < kTY && sp[la + kTX] >= 0) tile_unite(sp, la, la + kTX, &fail);
+    }
+    if (gb) {
+      if (2 * threadIdx.x + 2 < kTX && sp[lb + 1] >= 0) tile_unite(sp, lb, lb + 1, &fail);
+      if (threadIdx.y + 1 < kTY && sp[lb + kTX] >= 0) tile_unite(sp, lb, lb + kTX, &fail);
+    }
+    __syncthreads();
+    const int x0 = x - 2 * threadIdx.x, y0 = y - threadIdx.y;
+    if (ga) laba = tile_root_index(sp, la, x0, y0, nx, &fail);
+    if (gb) labb = tile_root_index(sp, lb, x0, y0, nx, &fail);
+    if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
+  }
+  *reinterpret_cast<int2*>(B.label + c) = make_int2(laba, labb);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     B.tile_gas[t] = (uint8_t)(any != 0);
     if (t == 0) B.flags[FLAG_TILES] = 0;  // the tile list is rebuilt by the next phase
@@ -684,13 +759,21 @@ __global__ void __launch_bounds__(kTX * kTY) kb_union(const RelabelBox* __restri
   for (int w = lw.first; w < lw.n; w += lw.stride) {
     const int t = B.tile_list[w];
     if (!B.tile_gas[t]) continue;
+    // edges inside the tile were joined by the density phase: only the
+    // right and bottom borders (periodic wrap included) are left
+    const bool re = threadIdx.x == kTX - 1, be = threadIdx.y == kTY - 1;
+    if (!re && !be) continue;
     const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
     const int c = y * nx + x;
     if (L[c] < 0) continue;
-    const int right = y * nx + (x + 1 == nx ? 0 : x + 1);
-    const int down = (y + 1 == ny ? 0 : y + 1) * nx + x;
-    if (L[right] >= 0) unite(L, c, right, &fail);
-    if (L[down] >= 0) unite(L, c, down, &fail);
+    if (re) {
+      const int right = y * nx + (x + 1 == nx ? 0 : x + 1);
+      if (L[right] >= 0) unite(L, c, right, &fail);
+    }
+    if (be) {
+      const int down = (y + 1 == ny ? 0 : y + 1) * nx + x;
+      if (L[down] >= 0) unite(L, c, down, &fail);
+    }
   }
   if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
 }
