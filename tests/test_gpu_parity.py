@@ -471,6 +471,31 @@ def test_two_component_whole_wave_chunks_empty_gas():
     assert np.array_equal(two.read("mask")["mask"], one.read("mask")["mask"])
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("nx,ny", [(256, 128), (32, 8)])
+def test_degenerate_all_gas_and_all_liquid(storage, nx, ny):
+    """A box that is gas everywhere is one component on the torus (label 0,
+    the smallest index; every cell its own owner's bubble, no blocked edge,
+    one bubble covering the box); a box of liquid has no labels, owners or
+    bubbles. 32 x 8 is a single tile, whose periodic edges all wrap onto
+    itself (zone radius 3, the largest that box allows; the generic owner
+    search beside the R_z = 4 shell scan)."""
+    R = 4 if ny > 9 else 3
+    for rho, gas in ((RG, True), (RL, False)):
+        sim = gpu_sim(nx, ny, np.full((ny, nx), rho), storage=storage, barrier=True, relabel_every=1, rho_ref=RL,
+                      zone_radius=R)
+        sim.step(3)
+        d = sim.read("label", "owner", "mask")
+        st = sim.stats()
+        if gas:
+            assert (d["label"] == 0).all() and (d["owner"] == 0).all() and not d["mask"].any()
+            assert st["n_bubbles"] == 1 and st["gas_fraction"] == 1.0
+            assert st["mean_diameter"] == pytest.approx(2.0 * math.sqrt(nx * ny / math.pi), rel=1e-12)
+        else:
+            assert (d["label"] == -1).all() and (d["owner"] == -1).all() and not d["mask"].any()
+            assert st["n_bubbles"] == 0 and st["gas_fraction"] == 0.0
+
+
 @pytest.fixture(scope="module")
 def foam_oracle_1000():
     """The FP64 oracle's statistics of a coarsening 512^2 foam (40 Poisson-disk
