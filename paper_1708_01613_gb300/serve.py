@@ -206,6 +206,7 @@ class FoamServer:
     quantum_updates: float | None = None
     policy: str = "work"            # "work" | "time" | "lockstep" | "tiered"
     big_s: float = 0.05             # "tiered": a job with more work left than this much GPU time is big
+    small_share: float = 0.5        # "tiered": most of a quantum the small jobs take while a big one runs
     device: str = "cuda"
     keep_pops: bool = False
     stats: dict = field(default_factory=dict)
@@ -279,7 +280,7 @@ class FoamServer:
                 share = lockstep_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
             elif self.policy == "tiered":
                 budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
-                share = tiered_steps(jobs_now, budget, self.big_s / model.s_per_update)
+                share = tiered_steps(jobs_now, budget, self.big_s / model.s_per_update, self.small_share)
             else:
                 raise ValueError(f"unknown policy {self.policy!r}")
             ts = time.perf_counter()
