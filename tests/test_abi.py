@@ -53,6 +53,39 @@ def test_workspace_bytes_and_validation():
     assert lbm.lbm_workspace_bytes(c) == 0
 
 
+def test_config_rules_of_the_variants():
+    """The rules of the growth source and the two-component mode, and the
+    field ranges, are checked on the host before any device work."""
+    ok = lbm.make_config(256, 64, components=2, barrier=True, G_mg=1.0)
+    assert lbm.lbm_workspace_bytes(ok) > 2 * lbm.lbm_workspace_bytes(lbm.make_config(256, 64))
+    bad = [
+        dict(components=2, storage="f16"),                  # two components: FP32 only
+        dict(components=2, growth=True),                    # no growth source with two lattices
+        dict(components=2, tau_g=0.5),                      # tau_g > 0.5
+        dict(components=2, G_mg=float("nan")),
+        dict(components=3),
+        dict(components=2, barrier=True, nx=100),           # two-lattice barrier: tiled sizes only
+        dict(components=2, barrier=True, ny=60),
+        dict(nx=65536, ny=65536),                           # nx * ny beyond int32
+        dict(G=float("inf")),
+        dict(rupture_eps=float("nan")),
+        dict(barrier=True, zone_radius=-1),
+        dict(barrier=True, zone_radius=32),                 # 2 R_z + 1 must stay below ny = 64
+    ]
+    for kw in bad:
+        nx, ny = kw.pop("nx", 256), kw.pop("ny", 64)
+        assert lbm.lbm_workspace_bytes(lbm.make_config(nx, ny, **kw)) == 0, kw
+    c = lbm.make_config(256, 64)
+    c.barrier = 2
+    assert lbm.lbm_workspace_bytes(c) == 0
+    c = lbm.make_config(256, 64)
+    c.growth = 3
+    assert lbm.lbm_workspace_bytes(c) == 0
+    # growth reserves a gas-point list of 4 bytes per cell
+    g = lbm.lbm_workspace_bytes(lbm.make_config(256, 64, growth=True, barrier=True))
+    assert g >= lbm.lbm_workspace_bytes(lbm.make_config(256, 64, barrier=True)) + 4 * 256 * 64
+
+
 def test_create_rejects_bad_arguments_without_gpu_work():
     lib = lbm.load_library()
     c = lbm.make_config(64, 64)
