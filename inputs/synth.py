@@ -202,8 +202,9 @@ def serving_requests(count: int = 2000, rate_per_s: float = 10.0, side_lo: int =
 def request_bubbles(req: dict) -> np.ndarray:
     """Bubble list of one serving request (Poisson-disk, log-uniform radii).
 
-    The requested count is capped so that bubbles of the smallest radius (4)
-    cover at most a fifth of the box; dart throwing then always succeeds."""
+    The requested count is capped so that bubbles of radius 5 cover at most
+    a fifth of the box (radii start at 4); dart throwing then always
+    succeeds."""
     side = req["nx"]
     cap = max(1, int(0.2 * req["nx"] * req["ny"] / (math.pi * 5.0**2)))
     nb = min(req["n_bubbles"], cap)

@@ -510,6 +510,54 @@ def test_inputs_are_seeded_and_independent_of_order():
             assert math.hypot(dx, dy) - bub[i, 2] - bub[j, 2] >= 2.0
 
 
+def test_splitmix64_reference_outputs():
+    """Draw k of stream s is the published SplitMix64 output number k + 1 of
+    a generator whose state starts at s: seeded with 0, that generator's
+    first three outputs are 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4 and
+    0x06C45D188009454F; the draws are their top 53 bits over 2^53."""
+    ref = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    u = inputs.splitmix64_uniform(0, np.arange(3))
+    assert [float(x) for x in u] == [(r >> 11) / 2.0**53 for r in ref]
+
+
+def torus_gaps(b, nx, ny):
+    g = []
+    for i in range(len(b)):
+        for j in range(i):
+            dx = abs(b[i, 0] - b[j, 0]); dx = min(dx, nx - dx)
+            dy = abs(b[i, 1] - b[j, 1]); dy = min(dy, ny - dy)
+            g.append((i, j, math.hypot(dx, dy) - b[i, 2] - b[j, 2]))
+    return g
+
+
+def test_workload_recipes_hold_their_stated_properties():
+    """Clustered bubbles touch an earlier one at a gap in [gap_lo, gap_hi]
+    and keep gap_lo to all; batch and serving draws stay in their ranges,
+    sides are multiples of 64, arrivals increase, request bubble counts are
+    capped and keep the Poisson-disk gap."""
+    n = 1024
+    b = inputs.clustered_bubbles(n, n, 20, 10.0, 40.0, 2.0, 6.0, seed=11)
+    gaps = torus_gaps(b, n, n)
+    assert min(g for _, _, g in gaps) >= 2.0 - 1e-9
+    for i in range(1, len(b)):
+        assert min(g for a, c, g in gaps if a == i and c < i) <= 6.0 + 1e-9
+    inst = inputs.batch_instances(16)
+    for it in inst:
+        assert 256 <= it["nx"] <= 2048 and it["nx"] % 64 == 0 and it["nx"] == it["ny"]
+        assert 1000 <= it["steps"] <= 20000
+        assert min([g for _, _, g in torus_gaps(it["bubbles"], it["nx"], it["ny"])] + [2.0]) >= 2.0 - 1e-9
+    reqs = inputs.serving_requests(200)
+    t = [r["arrival_s"] for r in reqs]
+    assert all(a < c for a, c in zip(t, t[1:]))
+    assert {r["storage"] for r in reqs} == {"f32", "f16"}
+    for r in reqs[:40]:
+        assert 128 <= r["nx"] <= 4096 and r["nx"] % 64 == 0 and 1000 <= r["steps"] <= 20000
+        bub = inputs.request_bubbles(r)
+        cap = max(1, int(0.2 * r["nx"] * r["ny"] / (math.pi * 25.0)))
+        assert len(bub) == min(r["n_bubbles"], cap)
+        assert min([g for _, _, g in torus_gaps(bub, r["nx"], r["ny"])] + [2.0]) >= 2.0 - 1e-9
+
+
 # ------------------------------------------------ nucleation and growth (Sec. 2.1.3)
 def test_growth_uniform_gas_box_closed_form():
     """All cells are gas points and the box stays uniform (no gradient, no
