@@ -8,20 +8,27 @@
 // The buffer read by a step holds the post-collision populations of the
 // previous step at their source cell; the step pulls f_i(x) from x - e_i.
 //
-// Both kernels march a strip of kBX columns down a chunk of rows. For every
-// row they pull the populations of the strip's cells and of one halo column
-// on each side, form rho and psi once per cell, and put psi into a four-row
-// ring in shared memory; one barrier later the ring holds psi for rows r-2..r
-// and the force and collision of row r-1 run on the populations kept in
-// registers. All per-cell arithmetic lives in the shared device functions
-// below, so the two kernels give bitwise the same populations.
+// Every kernel marches a strip of columns down a chunk of rows. For every
+// row it pulls the populations of the strip's cells and of one halo column
+// on each side, forms rho and psi once per cell, and puts psi into a
+// four-row ring in shared memory; one barrier later the ring holds psi for
+// rows r-2..r and the force and collision of row r-1 run on the moments kept
+// in registers. All per-cell arithmetic lives in the shared device functions
+// below (one cell or two), so every kernel gives bitwise the same
+// populations.
 //
-//  - k_step_strip: plain global loads; any box size.
+//  - k_step_strip: plain global loads, one cell per thread; any box size.
 //  - k_step_tma: the nine source rows of every output row (with halo) are
 //    copied into a ring of shared-memory stages by cp.async.bulk, issued
 //    NSTAGE-1 rows ahead by a ninth warp that also computes the two halo
 //    cells, so the eight compute warps are balanced and the bytes in flight
 //    do not depend on occupancy. Needs nx % 16 == 0 and nx >= kBX + 16.
+//  - k_step_tma2: the same staging over 512-column strips with two cells per
+//    thread (march2); one static row chunk per CTA.
+//  - k_step_dyn: march2 over row chunks that the resident CTAs draw from a
+//    device counter (the automatic choice where nx % 16 == 0).
+//  - k_step_batch: march2 over work items (box, strip, row chunk) of many
+//    boxes in one launch (batch.cu).
 #include "lbm_internal.cuh"
 #include "tma.cuh"
 
