@@ -13,11 +13,13 @@
 // each holding f^out at its source cell (the next step pulls f_i(x) from
 // x - e_i).
 //
-// The kernel marches a 256-column strip down a row chunk with plain loads:
-// for each row it pulls both components of the strip's cells (and of one
-// halo column per side), puts psi_m and psi_g into two four-row rings in
+// k_step2_strip marches a 256-column strip down a row chunk with plain
+// loads: for each row it pulls both components of the strip's cells (and of
+// one halo column per side), puts psi_m and psi_g into two four-row rings in
 // shared memory, and one barrier later runs force, collision and store of
-// the previous row from registers.
+// the previous row from registers. k_step2_tma (below) is the same march
+// with the rows staged by cp.async.bulk over row chunks drawn from a device
+// counter; both use the per-cell functions here.
 #include "lbm_internal.cuh"
 #include "tma.cuh"
 
