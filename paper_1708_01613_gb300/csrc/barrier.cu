@@ -499,9 +499,11 @@ __global__ void __launch_bounds__(kThreads) k_stats_partial(long long N, const i
 
 // ---------------------------------------------------------------------------
 // Tiled barrier pipeline (boxes with nx % 32 == 0 and ny % 8 == 0). The box is
-// cut into 32 x 8 tiles. The density pass also writes the initial labels and
-// one gas flag per tile; a tile is active when a gas cell lies within the
-// tile span that R_z can reach. Owners, rupture signs and masks can only be
+// cut into 32 x 8 tiles. The density pass also joins the gas cells inside
+// each tile (a union-find in shared memory: a gas cell's initial label is
+// the smallest index of its piece of the tile) and writes one gas flag per
+// tile; the union phase then joins the pieces across tile borders. A tile is
+// active when a gas cell lies within the tile span that R_z can reach. Owners, rupture signs and masks can only be
 // non-trivial in active tiles (a defined owner needs gas within R_z), so the
 // later kernels skip every tile that is inactive now and was inactive at the
 // previous relabel: its owner/sign/mask are already -1/0/0. A tile that just
