@@ -20,7 +20,7 @@ def make_box(nx, ny, storage, barrier, K, seed):
     return sim
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("graph", [True, False])
 def test_batch_matches_boxes_alone_bitwise(storage, graph):
     K, steps = 3, 11

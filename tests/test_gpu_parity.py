@@ -431,18 +431,22 @@ def test_dynamic_chunks_counter_survives_mixed_variants(storage):
     assert np.array_equal(mixed.read("pops")["pops"], plain.read("pops")["pops"])
 
 
-@pytest.mark.parametrize("storage,nx,ny", [("f32", 4096, 4096), ("f16", 4096, 4096), ("f16", 6144, 3072)])
-def test_whole_wave_chunks_match_plain_kernel(storage, nx, ny):
+@pytest.mark.parametrize("storage,nx,ny,tau", [("f32", 4096, 4096, 1.0), ("f16", 4096, 4096, 1.0),
+                                                ("f16", 6144, 3072, 1.0), ("f16", 4096, 4096, 0.8),
+                                                ("f32", 5120, 2048, 0.8)])
+def test_whole_wave_chunks_match_plain_kernel(storage, nx, ny, tau):
     """Mid-size boxes, where the automatic step draws chunks of the height
     that fills whole waves of resident CTAs (4096^2: 18 rows FP32, 27 rows
-    FP16; 6144 x 3072: 31 rows, ragged last chunk row), give bitwise the
-    plain kernel's populations and masks over steps with relabels."""
+    FP16; 6144 x 3072: 31 rows, ragged last chunk row; with tau != 1 the
+    kernel holds the populations across the barrier, runs fewer CTAs per SM
+    and marches full strips with a runtime width), give bitwise the plain
+    kernel's populations and masks over steps with relabels."""
     import torch
 
     pair = two_bubbles(nx, ny, R=20, gap=3.0)  # a film in the middle of the box
     bub = [b for b in inputs.poisson_disk_bubbles(nx, ny, 60, 8.0, 48.0, 2.0, seed=17)
            if all(math.hypot(b[0] - q[0], b[1] - q[1]) > b[2] + q[2] + 12 for q in pair)] + pair
-    kw = dict(storage=storage, barrier=True, relabel_every=3)
+    kw = dict(storage=storage, barrier=True, relabel_every=3, tau=tau)
     auto = gpu_sim(nx, ny, bubbles=bub, rho_ref=RL, **kw)
     plain = gpu_sim(nx, ny, bubbles=bub, rho_ref=RL, **kw)
     plain.set_step_variant(1)
