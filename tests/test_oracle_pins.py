@@ -148,6 +148,24 @@ def test_rest_state_is_stationary():
 
 
 @pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_uniform_flow_is_stationary(tau):
+    """A uniform density moving at a uniform velocity (populations at the
+    moving equilibrium, Eq. 14) has no psi gradient, hence no force, and the
+    collision returns the same equilibrium: streaming and collision leave it
+    unchanged, and the reported velocity (j + F/2)/rho is the imposed one."""
+    nx, ny, rho, ux, uy = 20, 12, 0.9, 0.03, -0.02
+    feq = O.equilibrium(rho, ux, uy)
+    s = O.OracleSim(O.make_params(nx, ny, tau=tau))
+    s.load_populations(np.broadcast_to(feq[:, None, None], (9, ny, nx)))
+    f0 = s.f.copy()
+    s.step(40)
+    assert np.max(np.abs(s.f - f0)) < 1e-15
+    fl = s.fields()
+    assert np.allclose(fl["ux"], ux, rtol=0, atol=1e-15) and np.allclose(fl["uy"], uy, rtol=0, atol=1e-15)
+    assert np.allclose(fl["rho"], rho, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
 def test_shear_wave_decay_matches_viscosity(tau):
     """G = 0: a shear wave u_y = U sin kx decays as exp(-nu k^2 t) with
     nu = cs2 (tau - 1/2) (Eq. 17)."""
