@@ -28,7 +28,12 @@
  *   nearest-bubble rule     Sec. 2.1.5 (interaction zones, nearest bubble,
  *                           Eq. 38 selection of one bubble's potential)
  *   barrier wall            Sec. 2.1.5, modified Shan-Chen flowchart
- *                           ("neglect effect from other side of barrier wall")
+ *                           ("locate oxide network barrier wall ... on equal
+ *                           velocity cells of each bubble interact domain",
+ *                           "neglect effect from other side of barrier
+ *                           wall") and the text after it: while the wall
+ *                           stands the bubbles never cross it and no
+ *                           coalescence occurs
  *   rupture criterion       Sec. 2.1.5, Eq. 41 (eta_m = 0 when d2p/dn2 = 0)
  *   run termination         Sec. 2.1.4 main flowchart and Sec. 5 (the foam
  *                           run ends when the first cell reaches rupture)
@@ -47,10 +52,17 @@
  *     Sec. 2.1.2); bubbles are 4-connected gas components on the torus,
  *     labelled by the smallest row-major index in the component;
  *   - owner of a liquid cell: the bubble of the nearest gas cell within the
- *     zone radius R_z, ties broken by the smaller label; none beyond R_z;
- *   - a blocked edge (x, x+e_i) has owners that differ, both defined, and
- *     neither end opened; across a blocked edge the force uses psi(x) in
- *     place of psi(x+e_i);
+ *     zone radius R_z; none (-1) beyond R_z; a cell whose nearest gas cells
+ *     belong to two or more bubbles at the same distance is a wall cell
+ *     (owner -2): the wall sits on the cells equidistant from the bubbles,
+ *     so it lies on a film's symmetry plane;
+ *   - a blocked edge (x, x+e_i) has owners that differ, both defined (not
+ *     -1; a wall cell's -2 counts as defined), and neither end opened. The
+ *     other side of the wall is neglected in both halves of the update:
+ *     across a blocked edge the force uses psi(x) in place of psi(x+e_i),
+ *     and the population f_i^out(x) that would stream across the edge is
+ *     reflected back into x as f_opp(i) (halfway bounce-back), so no mass
+ *     crosses the wall;
  *   - "d2p/dn2 = 0": at a cell with a differing-owner neighbour, n is the
  *     first such lattice direction; D2 = p(x+n) - 2 p(x) + p(x-n); the cell
  *     opens (for good) when |D2| <= eps or the sign of D2 differs from the
@@ -80,12 +92,16 @@
 #endif
 
 #define Q 9
+#define OWNER_NONE (-1) /* no bubble within the zone radius */
+#define OWNER_WALL (-2) /* equidistant from two or more bubbles */
 
 static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double WT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
                              1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+/* opposite direction: e_OPP[i] = -e_i */
+static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 
 typedef struct {
   int32_t nx, ny;
@@ -238,9 +254,12 @@ void orc_label(const orc_params *p, const double *rho, int32_t *label) {
 }
 
 /* Interaction zones (Sec. 2.1.5): a gas cell belongs to its own bubble; a
- * liquid cell belongs to the bubble of the gas cell g that minimises
- * (|x-g|^2 on the torus, label(g)) among gas cells with |x-g|^2 <= R_z^2;
- * none (-1) if there is no such cell. Exhaustive search of the window. */
+ * liquid cell belongs to the bubble of the gas cell g nearest to it (|x-g|^2
+ * on the torus) among gas cells with |x-g|^2 <= R_z^2; none (-1) if there is
+ * no such cell; a wall cell (OWNER_WALL) if gas cells of two or more bubbles
+ * are nearest at the same distance (the flowchart places the barrier wall on
+ * the cells where the bubbles' domains are equal). Exhaustive search of the
+ * window. */
 void orc_owner(const orc_params *p, const int32_t *label, int32_t *owner) {
   const int nx = p->nx, ny = p->ny, R = p->zone_radius;
 #pragma omp parallel for schedule(static)
@@ -253,30 +272,35 @@ void orc_owner(const orc_params *p, const int32_t *label, int32_t *owner) {
       }
       int best_d2 = -1;
       int32_t best = -1;
+      int tie = 0; /* another bubble at the best distance */
       for (int dy = -R; dy <= R; ++dy)
         for (int dx = -R; dx <= R; ++dx) {
           int d2 = dx * dx + dy * dy;
           if (d2 > R * R) continue;
           int32_t l = label[(size_t)wrap(y + dy, ny) * nx + wrap(x + dx, nx)];
           if (l < 0) continue;
-          if (best < 0 || d2 < best_d2 || (d2 == best_d2 && l < best)) {
+          if (best < 0 || d2 < best_d2) {
             best_d2 = d2;
             best = l;
+            tie = 0;
+          } else if (d2 == best_d2 && l != best) {
+            tie = 1;
           }
         }
-      owner[c] = best;
+      owner[c] = tie ? OWNER_WALL : best;
     }
 }
 
 /* First lattice direction i (1..8) across which the owner changes between two
- * defined owners, or 0 if x is not on a barrier. */
+ * defined owners (a wall cell's owner counts as defined), or 0 if x is not on
+ * a barrier. */
 static int barrier_direction(const orc_params *p, const int32_t *owner, int x, int y) {
   const int nx = p->nx, ny = p->ny;
   int32_t o = owner[(size_t)y * nx + x];
-  if (o < 0) return 0;
+  if (o == OWNER_NONE) return 0;
   for (int i = 1; i < Q; ++i) {
     int32_t on = owner[(size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx)];
-    if (on >= 0 && on != o) return i;
+    if (on != OWNER_NONE && on != o) return i;
   }
   return 0;
 }
@@ -322,7 +346,9 @@ void orc_rupture(const orc_params *p, const double *rho, const int32_t *owner, i
 }
 
 /* Blocked-edge mask: bit i-1 of mask(x) is set when owner(x) and owner(x+e_i)
- * are both defined and differ, and neither cell is open. */
+ * are both defined (not OWNER_NONE) and differ, and neither cell is open. The
+ * relation is symmetric: bit i-1 of mask(x) equals bit OPP[i]-1 of
+ * mask(x+e_i). */
 void orc_mask(const orc_params *p, const int32_t *owner, const uint8_t *open, uint8_t *mask) {
   const int nx = p->nx, ny = p->ny;
 #pragma omp parallel for schedule(static)
@@ -332,7 +358,8 @@ void orc_mask(const orc_params *p, const int32_t *owner, const uint8_t *open, ui
       uint8_t m = 0;
       for (int i = 1; i < Q; ++i) {
         size_t nb = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
-        if (owner[c] >= 0 && owner[nb] >= 0 && owner[c] != owner[nb] && !open[c] && !open[nb])
+        if (owner[c] != OWNER_NONE && owner[nb] != OWNER_NONE && owner[c] != owner[nb] && !open[c] &&
+            !open[nb])
           m |= (uint8_t)(1u << (i - 1));
       }
       mask[c] = m;
@@ -407,7 +434,8 @@ void orc_init_state(const orc_params *p, orc_state *s, const double *rho_init) {
 /* One time step: barrier pipeline when due, then moments (Eq. 11),
  * pseudopotential (Eq. 30), force (Eq. 22, masked), velocity shift
  * (Eqs. 39-40), equilibrium (Eq. 14), BGK collision (Eq. 18) and streaming
- * (Eq. 19). Returns 1 if the run is halted, else 0. */
+ * (Eq. 19; across a blocked edge the population bounces back into its own
+ * cell in the opposite direction). Returns 1 if the run is halted, else 0. */
 int orc_step(const orc_params *p, orc_state *s) {
   const int nx = p->nx, ny = p->ny;
   const size_t N = (size_t)nx * ny;
@@ -451,8 +479,13 @@ int orc_step(const orc_params *p, orc_state *s) {
         double fi = s->f[i * N + c];
         double fout = fi - (fi - feq[i]) / p->tau;
         if (source) fout += WT[i] * drho;
-        size_t dst = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
-        s->f_next[i * N + dst] = fout;
+        if (barrier && i > 0 && ((s->mask[c] >> (i - 1)) & 1u)) {
+          /* the edge to x+e_i is blocked: bounce back into x */
+          s->f_next[OPP[i] * N + c] = fout;
+        } else {
+          size_t dst = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+          s->f_next[i * N + dst] = fout;
+        }
       }
     }
   memcpy(s->f, s->f_next, Q * N * sizeof(double));
@@ -493,7 +526,7 @@ void orc_fields(const orc_params *p, orc_state *s, double *rho, double *ux, doub
  * incoming populations f of a whole box and a blocked-edge mask (may be NULL),
  * writes the incoming populations of the next step at cells[k] into
  * out[k*9 + i]. Each output is computed from its 5x5 neighbourhood with the
- * same equations as orc_step. */
+ * same equations as orc_step, bounce-back across blocked edges included. */
 void orc_step_cells(const orc_params *p, const double *f, const uint8_t *mask,
                     const int64_t *cells, int64_t ncells, double *out) {
   const int nx = p->nx, ny = p->ny;
@@ -503,8 +536,15 @@ void orc_step_cells(const orc_params *p, const double *f, const uint8_t *mask,
     int64_t c = cells[k];
     int x = (int)(c % nx), y = (int)(c / nx);
     for (int i = 0; i < Q; ++i) {
-      /* the population i arriving at x left the source cell x - e_i */
-      int sx = wrap(x - EX[i], nx), sy = wrap(y - EY[i], ny);
+      /* the population i arriving at x left the source cell x - e_i in
+         direction i, or, if the edge (x, x - e_i) is blocked, left x itself
+         in direction OPP[i] and bounced back */
+      int sx = wrap(x - EX[i], nx), sy = wrap(y - EY[i], ny), d = i;
+      if (mask && i > 0 && ((mask[(size_t)y * nx + x] >> (OPP[i] - 1)) & 1u)) {
+        sx = x;
+        sy = y;
+        d = OPP[i];
+      }
       size_t sc = (size_t)sy * nx + sx;
       double rho_s = 0.0, jx = 0.0, jy = 0.0;
       for (int q = 0; q < Q; ++q) {
@@ -527,8 +567,8 @@ void orc_step_cells(const orc_params *p, const double *f, const uint8_t *mask,
       double ux = (jx + p->tau * Fx) / rho_s, uy = (jy + p->tau * Fy) / rho_s;
       double feq[Q];
       orc_equilibrium(rho_s, ux, uy, feq);
-      double fi = f[i * N + sc];
-      out[k * Q + i] = fi - (fi - feq[i]) / p->tau;
+      double fi = f[d * N + sc];
+      out[k * Q + i] = fi - (fi - feq[d]) / p->tau;
     }
   }
 }
@@ -621,7 +661,8 @@ int32_t orc_stats(const orc_params *p, const int32_t *label, double *gas_fractio
  *   - pressure p = (rho_m + rho_g)/3 + (1/6) sum_{s,s'} G_{ss'} psi_s psi_s'
  *     (Eq. 29 summed over the pairs; with no gas it is Eq. 29);
  *   - bubbles (for the barrier) are the 4-connected regions of melt density
- *     below gas_threshold; the rupture test uses the pressure above.
+ *     below gas_threshold; the rupture test uses the pressure above; both
+ *     components bounce back across a blocked edge.
  * With an empty gas lattice the step is the single-component step.
  * ------------------------------------------------------------------------ */
 typedef struct {
@@ -763,10 +804,16 @@ void orc2_step(const orc2_params *q, orc2_state *s) {
       orc_equilibrium(rm, um_x, um_y, feq_m);
       orc_equilibrium(rg, ug_x, ug_y, feq_g);
       for (int i = 0; i < Q; ++i) {
-        const size_t dst = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
         const double a = s->fm[i * N + c], b = s->fg[i * N + c];
-        s->fm_next[i * N + dst] = a - (a - feq_m[i]) / q->tau_m;
-        s->fg_next[i * N + dst] = b - (b - feq_g[i]) / q->tau_g;
+        /* streaming; across a blocked edge both components bounce back */
+        size_t dst = (size_t)wrap(y + EY[i], ny) * nx + wrap(x + EX[i], nx);
+        int d = i;
+        if (mask && i > 0 && ((mask[c] >> (i - 1)) & 1u)) {
+          dst = c;
+          d = OPP[i];
+        }
+        s->fm_next[d * N + dst] = a - (a - feq_m[i]) / q->tau_m;
+        s->fg_next[d * N + dst] = b - (b - feq_g[i]) / q->tau_g;
       }
     }
   memcpy(s->fm, s->fm_next, Q * N * sizeof(double));

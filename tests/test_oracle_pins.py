@@ -305,16 +305,19 @@ def test_flat_interface_coexistence():
 
 
 def test_laplace_law_droplets():
-    """Static droplets: p_in - p_out is linear in 1/R with a near-zero
-    intercept (Laplace). Droplets are used because small gas bubbles in a
-    closed box at coexistence density dissolve."""
+    """Static droplets: p_in - p_out is linear in 1/R (R^2 >= 0.999) with an
+    intercept within 2 % of dp(R = 10) (Laplace). Droplets are used because
+    small gas bubbles in a closed box at coexistence density dissolve. Radii
+    10, 20, 30, 40 in boxes of 64-160 cells, relaxed for 12000 steps (the
+    fit's intercept is 5 % of dp(10) after 4000 steps, 0.7 % after 8000 and
+    0.05 % after 12000); the GPU sweep takes the survey's 10-60."""
     rl, rg = inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55
     pts = []
-    for R, L in ((10, 96), (14, 96), (18, 128), (24, 128)):
+    for R, L in ((10, 64), (20, 96), (30, 128), (40, 160)):
         P = O.make_params(L, L, G=-5.5)
         s = O.OracleSim(P)
         s.init_density(O.init_bubbles(P, [[L / 2, L / 2, R]], rg, rl, 4.0))  # liquid inside
-        s.step(4000)
+        s.step(12000)
         fl = s.fields()
         A = np.sum((fl["rho"] - rg) / (rl - rg))
         yy, xx = np.mgrid[0:L, 0:L]
@@ -327,7 +330,7 @@ def test_laplace_law_droplets():
     fit = slope * xs + icpt
     r2 = 1 - np.sum((dp - fit) ** 2) / np.sum((dp - dp.mean()) ** 2)
     assert slope > 0 and r2 >= 0.999
-    assert abs(icpt) <= 0.05 * dp[0]
+    assert abs(icpt) <= 0.02 * dp[0]
 
 
 # ----------------------------------------------------------------- barrier pipeline
@@ -374,8 +377,10 @@ def test_labels_owner_mask_brute_force(shape, seed):
             if not ok.any():
                 assert own[y, x] == -1
                 continue
-            cand = sorted(zip(d2[ok], lab[gy[ok], gx[ok]]))
-            assert own[y, x] == cand[0][1]
+            near = set(lab[gy[ok], gx[ok]][d2[ok] == d2[ok].min()].tolist())
+            # one nearest bubble owns the cell; equidistant bubbles put it on the wall
+            assert own[y, x] == (near.pop() if len(near) == 1 else -2)
+    assert (own == -2).any()  # the random boxes do exercise the wall rule
     op = (rng.random((ny, nx)) < 0.2).astype(np.uint8)
     m = O.mask(P, own, op)
     ex, ey, _ = O.lattice()
@@ -383,10 +388,73 @@ def test_labels_owner_mask_brute_force(shape, seed):
         for x in range(nx):
             for i in range(1, 9):
                 yy, xx = (y + ey[i]) % ny, (x + ex[i]) % nx
-                want = (own[y, x] >= 0 and own[yy, xx] >= 0 and own[y, x] != own[yy, xx]
+                want = (own[y, x] != -1 and own[yy, xx] != -1 and own[y, x] != own[yy, xx]
                         and not op[y, x] and not op[yy, xx])
                 assert bool((m[y, x] >> (i - 1)) & 1) == want
                 assert bool((m[y, x] >> (i - 1)) & 1) == bool((m[yy, xx] >> (OPP[i] - 1)) & 1)
+
+
+def test_wall_sits_on_the_symmetry_plane_of_a_film():
+    """Two vertical gas slabs (columns 0 and 6 of a 12-wide torus) leave two
+    5-cell films. Columns 3 and 9 are 3 cells from both slabs: they are wall
+    cells (owner -2), and every edge from them into either side is blocked;
+    the films' other cells belong to the nearer slab. With an even film (slabs
+    at columns 0 and 5: films of 4 and 6 cells) no cell is equidistant and
+    the wall runs between the two middle cells."""
+    ny = 4
+    P = O.make_params(12, ny, barrier=True, zone_radius=3)
+    rho = np.full((ny, 12), 2.3)
+    rho[:, [0, 6]] = 0.1
+    lab = O.label(P, rho)
+    own = O.owner(P, lab)
+    assert np.all(own[:, [1, 2, 11]] == 0) and np.all(own[:, [4, 5, 7, 8]] == 6)
+    assert np.all(own[:, [3, 9]] == -2)
+    m = O.mask(P, own, np.zeros((ny, 12), np.uint8))
+    left = 1 << 2 | 1 << 5 | 1 << 6   # directions 3, 6, 7 (towards -x)
+    right = 1 << 0 | 1 << 4 | 1 << 7  # directions 1, 5, 8 (towards +x)
+    assert np.all(m[:, [3, 9]] == left | right)
+    assert np.all(m[:, [2, 8]] == right) and np.all(m[:, [4, 10]] == left)
+    assert np.all(m[:, [0, 1, 5, 6, 7, 11]] == 0)
+    rho = np.full((ny, 12), 2.3)
+    rho[:, [0, 5]] = 0.1
+    own = O.owner(P, O.label(P, rho))
+    assert not (own == -2).any()
+    assert np.all(own[:, [1, 2]] == 0) and np.all(own[:, [3, 4, 6, 7, 8]] == 5)
+    assert np.all(own[:, [9, 10, 11]] == 0)
+
+
+def test_bounce_back_closed_wall_conserves_mass_on_each_side():
+    """Two gas slabs (tanh profiles, 8 cells wide) span the periodic height;
+    with R_z = 10 their zones meet in both films, so two straight walls (at
+    columns 15|16 and 39|40) cut the torus into two closed halves. The liquid
+    starts slightly denser in one half. A blocked edge reflects the population
+    that would cross it (halfway bounce-back), so each half keeps its mass
+    to rounding over 1000 steps while the walls stand; without the barrier
+    liquid moves from one half into the other."""
+    nx, ny = 48, 8
+    x = np.arange(nx)
+    rl, rg = inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55
+    side_b = (x >= 16) & (x < 40)
+    d = np.minimum(np.abs(x % 24 - 3.5), 24 - np.abs(x % 24 - 3.5)) - 4.0  # distance to a slab surface
+    liq = np.where(side_b, rl + 0.01, rl - 0.01)
+    rho = 0.5 * (liq + rg) + 0.5 * (liq - rg) * np.tanh(d / 2.0)
+    rho = np.ascontiguousarray(np.broadcast_to(rho, (ny, nx)), dtype=np.float64)
+    drift = {}
+    for barrier in (True, False):
+        P = O.make_params(nx, ny, G=-5.5, barrier=barrier, zone_radius=10, rupture_eps=-1.0)
+        s = O.OracleSim(P)
+        s.init_density(rho)
+        mb0 = s.f.sum(0)[:, side_b].sum()
+        worst = 0.0
+        for _ in range(20):
+            s.step(50)
+            if barrier:  # the walls stand where the zones meet
+                assert np.all(s.mask[:, [15, 16, 39, 40]] != 0)
+                assert not np.any(s.mask[:, :14]) and not np.any(s.mask[:, 18:37]) and not np.any(s.mask[:, 42:])
+            worst = max(worst, abs(s.f.sum(0)[:, side_b].sum() - mb0) / mb0)
+        drift[barrier] = worst
+    assert drift[True] < 1e-12
+    assert drift[False] > 1e-3
 
 
 def test_rupture_rule_on_hand_cases():
@@ -490,9 +558,9 @@ def test_two_bubbles_first_rupture_hand_check():
                 own = s.owner
                 o = own[y, x]
                 dirs = [i for i in range(1, 9)
-                        if own[(y + ey[i]) % P.ny, (x + ex[i]) % P.nx] >= 0
+                        if own[(y + ey[i]) % P.ny, (x + ex[i]) % P.nx] != -1
                         and own[(y + ey[i]) % P.ny, (x + ex[i]) % P.nx] != o]
-                assert o >= 0 and dirs
+                assert o != -1 and dirs
                 i = dirs[0]
                 d2 = (p(rho[(y + ey[i]) % P.ny, (x + ex[i]) % P.nx]) - 2 * p(rho[y, x])
                       + p(rho[(y - ey[i]) % P.ny, (x - ex[i]) % P.nx]))
@@ -509,18 +577,93 @@ def test_two_bubbles_first_rupture_hand_check():
     assert done == t_open and s2.halted
 
 
-def test_step_cells_matches_full_step():
-    rho = inputs.noise_density(32, 24, seed=7)
-    P = O.make_params(32, 24, G=-5.5)
-    s = O.OracleSim(P)
-    s.init_density(rho)
-    s.step(300)  # some structure
+def _merged_components(old, new):
+    """Components of the labelling `new` that hold gas cells of two or more
+    components of `old` (coalescence events between the two labellings)."""
+    both = (old >= 0) & (new >= 0)
+    pairs = np.unique(np.stack([new[both], old[both]]), axis=1)
+    roots, counts = np.unique(pairs[0], return_counts=True)
+    return int(np.sum(counts >= 2))
+
+
+def _watch_two_bubbles(gap, steps, every=100, **kw):
+    """Run the two-bubble case and return (step of the first coalescence
+    event or None, bubble count at each check, steps run)."""
+    P, s = _two_bubbles(gap, **kw)
+    old = s.labels_now()
+    counts = []
+    while s.t < steps:
+        s.step(every)
+        new = s.labels_now()
+        counts.append(O.stats(P, new)["n_bubbles"])
+        if _merged_components(old, new):
+            return s.t, counts, s
+        old = new
+        if counts[-1] < 2:
+            break
+    return None, counts, s
+
+
+def test_barrier_without_rupture_stops_coalescence():
+    """Survey pin 9(ii), the paper's statement that while the oxide-network
+    wall stands the bubbles never cross it and do not coalesce (Sec. 2.1.5,
+    text after the modified Shan-Chen flowchart). Barrier on with rupture
+    disabled (eps < 0), K = 1: no coalescence event in 20000 steps for films
+    of 2 and 3 cells between R = 20 bubbles, while plain Shan-Chen merges the
+    3-cell film within a few hundred steps. With the 2-cell film both bubbles
+    are still there after 20000 steps, with a blocked-edge wall between them.
+    (With the 3-cell film one bubble later dissolves into the other through
+    the liquid around the wall, Ostwald ripening in the closed box, which
+    plain Shan-Chen shows too for a 6-cell film: a bubble vanishes, none
+    merge, and the count stays 2 for the first 10000 steps.)"""
+    t_plain, _, _ = _watch_two_bubbles(3.0, 2000)
+    assert t_plain is not None and t_plain <= 1000
+    t2, counts2, s2 = _watch_two_bubbles(2.0, 20000, barrier=True, rupture_eps=-1.0)
+    assert t2 is None and s2.t == 20000 and counts2[-1] == 2 and min(counts2) == 2
+    assert s2.mask.any() and s2.opened_total == 0
+    t3, counts3, s3 = _watch_two_bubbles(3.0, 20000, barrier=True, rupture_eps=-1.0)
+    assert t3 is None and min(counts3[:100]) == 2
+
+
+def test_rupture_lets_the_bubbles_merge_later_than_without_barrier():
+    """Survey pin 9(iii): with the barrier and the rupture criterion of Eq. 41
+    (default eps), a film cell opens, the wall is removed there and the two
+    bubbles coalesce (a true merge event: one component covers both), later
+    than without the barrier. T_m itself has no value in the paper to pin
+    (its Tab. 4 time is in SI units without a lattice mapping)."""
+    t_off, _, _ = _watch_two_bubbles(3.0, 2000, every=50)
+    t_m, _, s = _watch_two_bubbles(3.0, 20000, every=50, barrier=True)
+    assert t_off is not None and t_m is not None
+    assert t_m > t_off and s.opened_total > 0
+
+
+@pytest.mark.parametrize("barrier", [False, True])
+def test_step_cells_matches_full_step(barrier):
+    """orc_step_cells (a pull over each cell's 5x5 neighbourhood) against the
+    full step (collide, then push each population to its destination), two
+    separately written codes of the same update. With the barrier the full
+    step has just relabelled two bubbles whose zones meet, so the mask it
+    applies is a real symmetric wall with blocked cells among the checked
+    ones: both the force substitution and the bounce-back are compared."""
+    if barrier:
+        P, s = _two_bubbles(3.0, barrier=True, relabel_every=1)
+        s.step(40)
+    else:
+        P = O.make_params(32, 24, G=-5.5)
+        s = O.OracleSim(P)
+        s.init_density(inputs.noise_density(32, 24, seed=7))
+        s.step(300)  # some structure
     f0 = s.f.copy()
+    s.step(1)  # relabels first when the barrier is on: s.mask is the mask of this step
+    m = s.mask.copy() if barrier else None
     rng = np.random.default_rng(0)
-    m = (rng.random((24, 32)) < 0.1).astype(np.uint8) * 0  # plain: no mask
-    cells = rng.choice(32 * 24, 50, replace=False)
+    N = P.nx * P.ny
+    cells = rng.choice(N, 200, replace=False)
+    if barrier:
+        blocked = np.flatnonzero(m)
+        assert blocked.size > 10
+        cells = np.unique(np.concatenate([cells, blocked, (blocked + 1) % N, (blocked + P.nx) % N]))
     out = O.step_cells(P, f0, cells, m)
-    s.step(1)
     full = s.f.reshape(9, -1)[:, cells].T
     assert np.max(np.abs(out - full)) < 1e-15
 
