@@ -10,7 +10,12 @@
  * equilibrium u_eq = (j + tau F)/rho (Sec. 2.1.5, Eqs. 39-40; Eq. 14) and
  * BGK collision (Eq. 18). Every K steps it runs the film-barrier pipeline of
  * Sec. 2.1.5: gas labelling, nearest-bubble interaction zones, the
- * d2p/dn2 = 0 rupture test (Eq. 41) and the blocked-edge mask.
+ * d2p/dn2 = 0 rupture test (Eq. 41) and the blocked-edge mask. The wall is
+ * a barrier in both halves of the update: across a blocked edge the force
+ * uses psi(x) in place of psi(x + e_i), and the population that would
+ * stream across it is reflected back into its own cell in the opposite
+ * direction (halfway bounce-back), so no mass crosses the wall and bubbles
+ * on its two sides do not coalesce until the rupture test opens it.
  *
  * Conventions
  *  - Box: nx by ny cells, periodic on all sides, row-major, x fastest.
@@ -65,8 +70,12 @@ enum {
   LBM_FIELD_UY = 1u << 2,    /* float32: (j_y + F_y / 2) / rho */
   LBM_FIELD_P = 1u << 3,     /* float32: p = rho/3 + G psi^2 / 6 (Eq. 29) */
   LBM_FIELD_LABEL = 1u << 4, /* int32: bubble label (min row-major index) or -1 */
-  LBM_FIELD_OWNER = 1u << 5, /* int32: interaction-zone owner or -1 (barrier on) */
-  LBM_FIELD_MASK = 1u << 6,  /* uint8: bit i-1 set = edge (x, x+e_i) blocked */
+  LBM_FIELD_OWNER = 1u << 5, /* int32 (barrier on): label of the nearest bubble
+                                within R_z; -1 none; -2 a wall cell, equidistant
+                                from two or more bubbles */
+  LBM_FIELD_MASK = 1u << 6,  /* uint8: bit i-1 set = edge (x, x+e_i) blocked:
+                                owners of both ends differ, neither is -1,
+                                neither end is open (symmetric) */
   LBM_FIELD_OPEN = 1u << 7,  /* uint8: 1 = cell has ruptured (barrier on) */
   LBM_FIELD_POPS = 1u << 8,  /* float32 [9][ny][nx] ([18][ny][nx] with two
                                 components, melt then gas): incoming f_i of

@@ -221,6 +221,20 @@ int relabel(lbm_handle* h) {
   return LBM_OK;
 }
 
+// Bounce-back across the blocked edges on the buffer the step just wrote
+// (pops(1 - cur)), over the latest relabel's tile list where the box uses the
+// tiled pipeline.
+cudaError_t bounce_after_step(lbm_handle* h) {
+  const lbm_config& c = h->cfg;
+  const bool two = h->comps() == 2;
+  if (handle_relabel_tiled(h)) {
+    int totals[3];
+    relabel_entry_sizes(c.nx, c.ny, &totals[0], &totals[1], &totals[2]);
+    return launch_bounce_boxes(c.storage, two, h->rbox(), h->rentries(), 1, totals[2], h->cur ^ 1, h->stream);
+  }
+  return launch_bounce(c.storage, two, h->pops(1 - h->cur), h->mask(), c.nx, c.ny, h->stream);
+}
+
 int read_opened(lbm_handle* h, int* out) {
   CUDA_TRY(h, cudaMemcpyAsync(out, h->flags() + FLAG_OPENED, sizeof(int), cudaMemcpyDeviceToHost,
                               h->stream));
@@ -495,6 +509,10 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     if (growing) {
       CUDA_TRY(h, launch_growth(c.storage, p.dst, h->gas_list(), h->flags() + FLAG_GAS, (long long)h->N(),
                                 h->growth_rate, h->growth_budget, h->released(), (int)(h->t & 1), h->stream));
+      h->launches += 1;
+    }
+    if (c.barrier) {  // populations that would cross a blocked edge bounce back
+      CUDA_TRY(h, bounce_after_step(h));
       h->launches += 1;
     }
     h->cur ^= 1;

@@ -1,20 +1,24 @@
 // Film-barrier pipeline of the extended Shan-Chen model (arXiv 1708.01613,
 // Sec. 2.1.5) and the auxiliary kernels: density, gas labelling, interaction
-// zones, rupture test (Eq. 41), blocked-edge mask, diagnostics fields,
-// initialisation, FP64 mass and bubble statistics.
+// zones, rupture test (Eq. 41), blocked-edge mask, the bounce-back across
+// blocked edges after each step, diagnostics fields, initialisation, FP64
+// mass and bubble statistics.
 //
 // Readings used (the paper is silent on them):
 //  - gas cell: rho < threshold (default ln 2, the critical density of
 //    Sec. 2.1.2); bubbles are 4-connected gas components on the torus,
 //    labelled by the smallest row-major index in the component;
-//  - owner of a liquid cell: the bubble of the nearest gas cell within R_z,
-//    ties broken by the smaller label (the nearest-bubble rule of Sec. 2.1.5,
-//    which is where the largest |xi_k| of Eq. 38 sits);
+//  - owner of a liquid cell: the bubble of the nearest gas cell within R_z
+//    (the nearest-bubble rule of Sec. 2.1.5, which is where the largest
+//    |xi_k| of Eq. 38 sits); -1 if there is none; -2 (a wall cell) if gas
+//    cells of two or more bubbles are nearest at the same distance (the
+//    flowchart places the barrier wall where the bubbles' domains are equal);
 //  - rupture: at a cell with a differing-owner neighbour, n = the first such
 //    lattice direction, D2 = p(x+n) - 2 p(x) + p(x-n) with p of Eq. 29; the
 //    cell opens for good when |D2| <= eps or sign(D2) differs from the sign
 //    stored at the previous relabel;
-//  - blocked edge: owners differ, both defined, neither end open.
+//  - blocked edge: owners differ, both defined (not -1; the wall's -2 is
+//    defined), neither end open.
 #include <math.h>
 
 #include "lbm_internal.cuh"
@@ -32,7 +36,8 @@ __device__ __forceinline__ int wrapi(int a, int n) {
 
 inline unsigned blocks_for(long long n, int threads = kThreads) {
   long long b = (n + threads - 1) / threads;
-  if (b > 152LL * 64) b = 152LL * 64;
+  const long long cap = device_sm_count() * 64LL;
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (unsigned)b;
 }
@@ -117,7 +122,7 @@ __global__ void k_label_flatten(long long N, int32_t* L, int* flags) {
   if (fail) atomicOr(flags + FLAG_TIMEOUT, 1);
 }
 
-// --- interaction zones: nearest gas cell within R, ties to the smaller label ---
+// --- interaction zones: nearest gas cell within R; equidistant bubbles: wall (-2) ---
 __global__ void k_owner(int nx, int ny, int R, const int32_t* __restrict__ L, int32_t* __restrict__ own) {
   const long long N = (long long)nx * ny;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
@@ -129,6 +134,7 @@ __global__ void k_owner(int nx, int ny, int R, const int32_t* __restrict__ L, in
     }
     const int x = (int)(c % nx), y = (int)(c / nx);
     int best = -1, bd = 0x7fffffff;
+    bool tie = false;
     for (int dy = -R; dy <= R; ++dy) {
       const long long row = (long long)wrapi(y + dy, ny) * nx;
       for (int dx = -R; dx <= R; ++dx) {
@@ -136,14 +142,42 @@ __global__ void k_owner(int nx, int ny, int R, const int32_t* __restrict__ L, in
         if (d2 > R * R || d2 > bd) continue;
         const int l = __ldg(L + row + wrapi(x + dx, nx));
         if (l < 0) continue;
-        if (d2 < bd || l < best) {
+        if (d2 < bd) {
           bd = d2;
           best = l;
+          tie = false;
+        } else if (l != best) {
+          tie = true;
         }
       }
     }
-    own[c] = best;
+    own[c] = tie ? -2 : best;
   }
+}
+
+// Owner of a liquid cell from a window of labels in shared memory (row0 at
+// the cell, row stride W): the label of the nearest labelled cell within R,
+// -1 if none, -2 if two different labels are nearest at the same distance.
+__device__ __forceinline__ int window_owner(const int* row0, int W, int R) {
+  int best = -1, bd = 0x7fffffff;
+  bool tie = false;
+  for (int dy = -R; dy <= R; ++dy) {
+    const int* rowp = row0 + dy * W;
+    for (int dx = -R; dx <= R; ++dx) {
+      const int d2 = dx * dx + dy * dy;
+      if (d2 > R * R || d2 > bd) continue;
+      const int l = rowp[dx];
+      if (l < 0) continue;
+      if (d2 < bd) {
+        bd = d2;
+        best = l;
+        tie = false;
+      } else if (l != best) {
+        tie = true;
+      }
+    }
+  }
+  return tie ? -2 : best;
 }
 
 // Tiled owner search: a 32 x 8 tile stages the labels of its window (tile
@@ -176,20 +210,7 @@ __global__ void __launch_bounds__(kOTX * kOTY) k_owner_tiled(int nx, int ny, int
     if (lc >= 0) {
       result = lc;
     } else {
-      int bd = 0x7fffffff;
-      for (int dy = -R; dy <= R; ++dy) {
-        const int* rowp = row0 + dy * W;
-        for (int dx = -R; dx <= R; ++dx) {
-          const int d2 = dx * dx + dy * dy;
-          if (d2 > R * R || d2 > bd) continue;
-          const int l = rowp[dx];
-          if (l < 0) continue;
-          if (d2 < bd || l < result) {
-            bd = d2;
-            result = l;
-          }
-        }
-      }
+      result = window_owner(row0, W, R);
     }
   }
   own[(long long)y * nx + x] = result;
@@ -210,11 +231,11 @@ __global__ void k_rupture(int nx, int ny, float G, float rho0, float eps,
     const int o = own[c];
     const int x = (int)(c % nx), y = (int)(c / nx);
     int dir = 0;
-    if (o >= 0) {
+    if (o != -1) {
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const int on = own[(long long)wrapi(y + cy(i), ny) * nx + wrapi(x + cx(i), nx)];
-        if (dir == 0 && on >= 0 && on != o) dir = i;
+        if (dir == 0 && on != -1 && on != o) dir = i;
       }
     }
     if (dir == 0) {
@@ -251,12 +272,12 @@ __global__ void k_mask(int nx, int ny, const int32_t* __restrict__ own, const ui
     const int o = own[c];
     const int x = (int)(c % nx), y = (int)(c / nx);
     unsigned m = 0;
-    if (o >= 0 && !open[c]) {
+    if (o != -1 && !open[c]) {
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const long long nb = (long long)wrapi(y + cy(i), ny) * nx + wrapi(x + cx(i), nx);
         const int on = own[nb];
-        if (on >= 0 && on != o && !open[nb]) m |= 1u << (i - 1);
+        if (on != -1 && on != o && !open[nb]) m |= 1u << (i - 1);
       }
     }
     mask[c] = (uint8_t)m;
@@ -416,7 +437,9 @@ __global__ void __launch_bounds__(kThreads) k_bubbles_rho(const lbm_bubble* __re
 }
 
 // --- fixed-order FP64 reductions ---
-constexpr int kRedBlocks = 152 * 4;
+// A fixed number of block partials (not tied to the device's SM count), so the
+// summation order, and with it every reduced value, is the same on any GPU.
+constexpr int kRedBlocks = 608;
 
 template <int NV>
 __device__ void block_reduce_store(double (&v)[NV], double* __restrict__ out) {
@@ -513,7 +536,8 @@ __global__ void __launch_bounds__(kThreads) k_stats_partial(long long N, const i
 // of one): each box's CTAs follow those of the boxes before it in the entry
 // list (RelabelEntry prefix sums), and a CTA finds its box by binary search.
 constexpr int kTX = kRelabelTileX, kTY = kRelabelTileY;
-constexpr int kListCtas = 152 * 8;  // CTAs per box for the tile-list phases, at most
+// CTAs per box for the tile-list phases, at most: eight per SM
+inline int list_ctas() { return device_sm_count() * 8; }
 
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -795,16 +819,19 @@ __global__ void __launch_bounds__(kTX * kTY) kb_flatten(const RelabelBox* __rest
   if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
 }
 
-// Nearest labelled cell within radius R of the window position row0 (window
-// width W), ties to the smaller label; -1 if none. Shells of equal squared
+// Owner from the labels within radius R of the window position row0 (window
+// width W): the label of the nearest labelled cell, -1 if none, -2 if two
+// different labels are nearest at the same distance. Shells of equal squared
 // distance are scanned in increasing order and the first shell holding a
-// label decides: the unsigned minimum of the labels in it (-1 is the
-// largest unsigned value) is the minimum of (d^2, label). With R known at
-// compile time every offset is one shared load and one min.
+// label decides: the unsigned minimum of its labels (-1 is the largest
+// unsigned value) and the signed maximum (-1 is the smallest) are that
+// shell's smallest and largest label, equal unless two bubbles tie. With R
+// known at compile time every offset is one shared load, one min and one max.
 template <int R>
 __device__ __forceinline__ int nearest_label(const int* row0) {
   constexpr int W = kTX + 2 * R;
-  unsigned best = 0xffffffffu;
+  unsigned lo = 0xffffffffu;
+  int hi = -1;
 #pragma unroll
   for (int S = 1; S <= R * R; ++S) {
     bool any = false;
@@ -813,12 +840,14 @@ __device__ __forceinline__ int nearest_label(const int* row0) {
 #pragma unroll
       for (int dx = -R; dx <= R; ++dx)
         if (dx * dx + dy * dy == S) {
-          best = min(best, (unsigned)row0[dy * W + dx]);
+          const int l = row0[dy * W + dx];
+          lo = min(lo, (unsigned)l);
+          hi = max(hi, l);
           any = true;
         }
-    if (any && best != 0xffffffffu) break;
+    if (any && lo != 0xffffffffu) break;
   }
-  return (int)best;
+  return lo == 0xffffffffu ? -1 : (hi != (int)lo ? -2 : (int)lo);
 }
 
 __global__ void __launch_bounds__(kTX * kTY) kb_owner(const RelabelBox* __restrict__ boxes,
@@ -850,20 +879,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_owner(const RelabelBox* __restri
     if (result < 0 && R == 4) {  // the default zone radius
       result = nearest_label<4>(row0);
     } else if (result < 0) {
-      int bd = 0x7fffffff;
-      for (int dy = -R; dy <= R; ++dy) {
-        const int* rowp = row0 + dy * W;
-        for (int dx = -R; dx <= R; ++dx) {
-          const int d2 = dx * dx + dy * dy;
-          if (d2 > R * R || d2 > bd) continue;
-          const int l = rowp[dx];
-          if (l < 0) continue;
-          if (d2 < bd || l < result) {
-            bd = d2;
-            result = l;
-          }
-        }
-      }
+      result = window_owner(row0, W, R);
     }
     B.owner[c] = result;
   }
@@ -883,11 +899,11 @@ __global__ void __launch_bounds__(kTX * kTY) kb_rupture(const RelabelBox* __rest
     const size_t c = (size_t)y * nx + x;
     const int o = act ? own[c] : -1;
     int dir = 0;
-    if (o >= 0) {
+    if (o != -1) {
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const int on = own[(size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx)];
-        if (dir == 0 && on >= 0 && on != o) dir = i;
+        if (dir == 0 && on != -1 && on != o) dir = i;
       }
     }
     int opened = 0;
@@ -934,16 +950,82 @@ __global__ void __launch_bounds__(kTX * kTY) kb_mask(const RelabelBox* __restric
     const size_t c = (size_t)y * nx + x;
     unsigned msk = 0;
     const int o = act ? B.owner[c] : -1;
-    if (o >= 0 && !B.open[c]) {
+    if (o != -1 && !B.open[c]) {
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const size_t nb = (size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx);
         const int on = B.owner[nb];
-        if (on >= 0 && on != o && !B.open[nb]) msk |= 1u << (i - 1);
+        if (on != -1 && on != o && !B.open[nb]) msk |= 1u << (i - 1);
       }
     }
     B.mask[c] = (uint8_t)msk;
     if (threadIdx.x == 0 && threadIdx.y == 0) B.tile_prev[t] = (uint8_t)act;
+  }
+}
+
+// --- halfway bounce-back across blocked edges (the barrier of Sec. 2.1.5) ---
+// The step kernels store every outgoing population in its own slot: slot
+// (plane i, x) holds f_i^out(x), which the next step pulls into x + e_i. For
+// a blocked edge (x, x + e_i) the wall sends it back instead: f_i^out(x)
+// returns to x as population opp(i), which the next step pulls from
+// x - e_opp(i) = x + e_i in plane opp(i), and f_opp(i)^out(x + e_i) returns to
+// x + e_i as population i, pulled from slot (plane i, x). So after the step
+// the two slots of every blocked edge trade their values. The mask is
+// symmetric; each edge is handled once, from its end whose direction is
+// 1, 2, 5 or 6 (mask bits 0, 1, 4, 5), and every slot belongs to one edge
+// only, so no two threads touch the same slot. T is the raw storage word
+// (4 or 2 bytes: the values move bit for bit); TWO: a second lattice follows
+// the first nine planes.
+constexpr unsigned kCanonBits = 0x33u;
+
+template <typename T, bool TWO>
+__device__ __forceinline__ void bounce_cell(T* __restrict__ pops, size_t N, int x, int y, int nx, int ny,
+                                            unsigned m) {
+  m &= kCanonBits;
+  if (!m) return;
+  const size_t c = (size_t)y * nx + x;
+#pragma unroll
+  for (int i = 1; i <= 6; ++i) {
+    if (i == 3 || i == 4 || !((m >> (i - 1)) & 1u)) continue;
+    const size_t a = (size_t)i * N + c;
+    const size_t b = (size_t)opp(i) * N + (size_t)wrap1(y + cy(i), ny) * nx + wrap1(x + cx(i), nx);
+    const T va = pops[a], vb = pops[b];
+    pops[a] = vb;
+    pops[b] = va;
+    if (TWO) {
+      const size_t a2 = a + Q * N, b2 = b + Q * N;
+      const T wa = pops[a2], wb = pops[b2];
+      pops[a2] = wb;
+      pops[b2] = wa;
+    }
+  }
+}
+
+// Every cell of a box (boxes that do not use the tiled pipeline).
+template <typename T, bool TWO>
+__global__ void k_bounce(T* __restrict__ pops, const uint8_t* __restrict__ mask, int nx, int ny) {
+  const long long N = (long long)nx * ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const unsigned m = mask[c];
+    if (m & kCanonBits) bounce_cell<T, TWO>(pops, (size_t)N, (int)(c % nx), (int)(c / nx), nx, ny, m);
+  }
+}
+
+// Tiled boxes: only the tiles of the latest relabel's work list can hold a
+// blocked edge. Buffer B.pops[B.cur ^ q] of every box in the entry list.
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(kTX * kTY) kb_bounce(const RelabelBox* __restrict__ boxes,
+                                                       const RelabelEntry* __restrict__ e, int m, int q) {
+  const ListWalk lw = list_walk(boxes, e, m);
+  const RelabelBox& B = *lw.B;
+  T* pops = static_cast<T*>(const_cast<void*>(B.pops[B.cur ^ q]));
+  const size_t N = (size_t)B.nx * B.ny;
+  for (int w = lw.first; w < lw.n; w += lw.stride) {
+    const int t = B.tile_list[w];
+    const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    const unsigned msk = B.mask[(size_t)y * B.nx + x];
+    if (msk & kCanonBits) bounce_cell<T, TWO>(pops, N, x, y, B.nx, B.ny, msk);
   }
 }
 
@@ -1111,7 +1193,8 @@ void relabel_entry_sizes(int nx, int ny, int* tiles, int* scan, int* list) {
   const int t = relabel_tile_count(nx, ny);
   *tiles = t;
   *scan = (t + kThreads - 1) / kThreads;
-  *list = t < kListCtas ? t : kListCtas;
+  const int cap = list_ctas();
+  *list = t < cap ? t : cap;
 }
 
 cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const RelabelEntry* entries, int m,
@@ -1140,6 +1223,34 @@ cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const Rel
   if (two) kb_rupture<true><<<totals[2], block, 0, s>>>(boxes, entries, m);
   else kb_rupture<false><<<totals[2], block, 0, s>>>(boxes, entries, m);
   kb_mask<<<totals[2], block, 0, s>>>(boxes, entries, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bounce(int storage, bool two, void* pops, const uint8_t* mask, int nx, int ny, cudaStream_t s) {
+  const unsigned b = blocks_for((long long)nx * ny);
+  if (two) {
+    if (storage != LBM_F32) return cudaErrorInvalidValue;
+    k_bounce<uint32_t, true><<<b, kThreads, 0, s>>>(static_cast<uint32_t*>(pops), mask, nx, ny);
+  } else if (storage == LBM_F32) {
+    k_bounce<uint32_t, false><<<b, kThreads, 0, s>>>(static_cast<uint32_t*>(pops), mask, nx, ny);
+  } else {
+    k_bounce<uint16_t, false><<<b, kThreads, 0, s>>>(static_cast<uint16_t*>(pops), mask, nx, ny);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bounce_boxes(int storage, bool two, const RelabelBox* boxes, const RelabelEntry* entries, int m,
+                                int total_list, int q, cudaStream_t s) {
+  if (m <= 0 || total_list <= 0) return cudaSuccess;
+  const dim3 block(kTX, kTY);
+  if (two) {
+    if (storage != LBM_F32) return cudaErrorInvalidValue;
+    kb_bounce<uint32_t, true><<<total_list, block, 0, s>>>(boxes, entries, m, q);
+  } else if (storage == LBM_F32) {
+    kb_bounce<uint32_t, false><<<total_list, block, 0, s>>>(boxes, entries, m, q);
+  } else {
+    kb_bounce<uint16_t, false><<<total_list, block, 0, s>>>(boxes, entries, m, q);
+  }
   return cudaGetLastError();
 }
 

@@ -3,7 +3,8 @@
 // A batch advances several independent boxes together: every step is one
 // persistent launch of the two-cell staged kernel over a list of work items
 // (box, column strip, row chunk) that covers all active boxes, preceded, when
-// a relabel is due, by each box's barrier pipeline. Blocks of K steps (K =
+// a relabel is due, by each box's barrier pipeline and followed, with the
+// barrier, by the bounce-back across the boxes' blocked edges. Blocks of K steps (K =
 // relabel period) are captured once as CUDA graphs and replayed. The strip
 // width and chunk height of the work items are picked by lbm_batch_tune,
 // which times the candidates on the batch itself. Per-cell arithmetic is the
@@ -55,6 +56,12 @@ struct lbm_batch {
   std::map<int, Group> groups;            // by residue of the step count
   std::vector<int> untiled;               // boxes relabelled one by one
   int64_t relabel_launches = 0;           // per relabel period
+  // bounce-back after each step: tiled boxes together (entries d_bent, in
+  // stepping order), untiled boxes one by one
+  RelabelEntry* d_bent = nullptr;
+  std::vector<int> bounce_first;          // tiled boxes among the first k stepping boxes
+  std::vector<int> bounce_ctas;           // list CTAs of the first k tiled boxes
+  int64_t bounce_launches = 0;            // per step
   int strip = 512, rows = 0;
   int use_graph = 1;
   int dirty = 1;               // descriptors/items must be re-uploaded
@@ -198,18 +205,34 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
   b->groups.clear();
   b->untiled.clear();
   b->relabel_launches = 0;
-  std::vector<RelabelEntry> ents;
+  b->bounce_first.assign(1, 0);
+  b->bounce_ctas.assign(1, 0);
+  b->bounce_launches = 0;
+  std::vector<RelabelEntry> ents, bents;
   if (b->masked) {
     std::vector<int> ord = order;
     if (ord.empty())
       for (int i = 0; i < b->n; ++i)
         if (b->active[i]) ord.push_back(i);
     const int r = b->h[0]->cfg.relabel_every;
+    for (int i : ord) {  // bounce-back entries: the tiled boxes in stepping order
+      const bool tiled = handle_relabel_tiled(b->h[i]);
+      if (tiled) {
+        int t0, t1, t2;
+        relabel_entry_sizes(b->h[i]->cfg.nx, b->h[i]->cfg.ny, &t0, &t1, &t2);
+        bents.push_back({i, 0, 0, b->bounce_ctas.back()});
+        b->bounce_ctas.push_back(b->bounce_ctas.back() + t2);
+      }
+      b->bounce_first.push_back(b->bounce_first.back() + (tiled ? 1 : 0));
+    }
+    bents.push_back({-1, 0, 0, b->bounce_ctas.back()});
+    b->bounce_launches = (bents.size() > 1 ? 1 : 0);
     for (int i : ord) {
       lbm_handle* h = b->h[i];
       if (!handle_relabel_tiled(h)) {
         b->untiled.push_back(i);
         b->relabel_launches += 7;
+        b->bounce_launches += 1;
         continue;
       }
       // due at batch count T when T + (t_i - t_batch) is a multiple of r
@@ -236,6 +259,8 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
     if (!ents.empty())
       BCUDA(b, cudaMemcpyAsync(b->d_rent, ents.data(), sizeof(RelabelEntry) * ents.size(), cudaMemcpyHostToDevice,
                                b->stream));
+    BCUDA(b, cudaMemcpyAsync(b->d_bent, bents.data(), sizeof(RelabelEntry) * bents.size(), cudaMemcpyHostToDevice,
+                             b->stream));
   }
   BCUDA(b, cudaStreamSynchronize(b->stream));
   b->par = 0;
@@ -277,6 +302,28 @@ int enqueue_relabel(lbm_batch* b, int parity, int64_t j, int live, Stepping step
   return LBM_OK;
 }
 
+// Bounce-back across blocked edges after the batched step of parity
+// `parity`: the first `first` boxes of the stepping order (all of them when
+// first < 0), on the buffers that step wrote.
+template <class Stepping>
+int enqueue_bounce(lbm_batch* b, int parity, int first, Stepping stepping) {
+  const int total = (int)b->bounce_first.size() - 1;
+  const int k = b->bounce_first[first < 0 || first > total ? total : first];
+  if (k > 0) {
+    BCUDA(b, launch_bounce_boxes(b->storage, false, b->d_rboxes, b->d_bent, k, b->bounce_ctas[k], parity ^ 1,
+                                 b->stream));
+    b->launches += 1;
+  }
+  for (int i : b->untiled) {
+    if (!stepping(i)) continue;
+    lbm_handle* h = b->h[i];
+    BCUDA(b, launch_bounce(b->storage, false, h->pops(b->base_cur[i] ^ parity ^ 1), h->mask(), h->cfg.nx,
+                           h->cfg.ny, b->stream));
+    b->launches += 1;
+  }
+  return LBM_OK;
+}
+
 // Host bookkeeping after `n` steps of every active box.
 void advance(lbm_batch* b, int64_t n) {
   b->t += n;
@@ -297,6 +344,7 @@ int enqueue_step(lbm_batch* b, int parity, int64_t j) {
   BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items, b->nitems,
                              b->d_counter, parity, b->stream));
   b->launches += 1;
+  if (b->masked && (rc = enqueue_bounce(b, parity, -1, [&](int i) { return b->active[i] != 0; }))) return rc;
   return LBM_OK;
 }
 
@@ -350,7 +398,8 @@ size_t lbm_batch_workspace_bytes(lbm_handle* const* handles, int32_t n) {
     if (!handles[i]) return 0;
   const int mi = max_items_for(handles, n);
   return align_up(sizeof(BatchInst) * (size_t)n) + align_up(sizeof(BatchItem) * (size_t)mi) + kAlign +
-         align_up(sizeof(RelabelBox) * (size_t)n) + align_up(sizeof(RelabelEntry) * (2 * (size_t)n + 1));
+         align_up(sizeof(RelabelBox) * (size_t)n) + align_up(sizeof(RelabelEntry) * (2 * (size_t)n + 1)) +
+         align_up(sizeof(RelabelEntry) * ((size_t)n + 1));
 }
 
 int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, size_t bytes, lbm_batch** out) {
@@ -402,6 +451,8 @@ int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, s
   b->d_rboxes = reinterpret_cast<RelabelBox*>(reinterpret_cast<char*>(b->d_counter) + kAlign);
   b->d_rent = reinterpret_cast<RelabelEntry*>(reinterpret_cast<char*>(b->d_rboxes) +
                                               align_up(sizeof(RelabelBox) * (size_t)n));
+  b->d_bent = reinterpret_cast<RelabelEntry*>(reinterpret_cast<char*>(b->d_rent) +
+                                              align_up(sizeof(RelabelEntry) * (2 * (size_t)n + 1)));
   // default tiles: full-width strips, chunks giving ~4 items per resident CTA
   long long cells = 0;
   for (int i = 0; i < n; ++i) cells += (long long)handles[i]->cfg.nx * handles[i]->cfg.ny;
@@ -472,7 +523,8 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     const int p = b->par;
     if (!b->graph[p] && (rc = build_graph(b, p))) return rc;
     BCUDA(b, cudaGraphLaunch(b->graph[p], b->stream));
-    b->launches += b->K + b->relabel_launches;  // every group relabels once per period
+    // every group relabels once per period; a bounce-back follows every step
+    b->launches += b->K * (1 + b->bounce_launches) + b->relabel_launches;
     advance(b, b->K);
     left -= b->K;
   }
@@ -542,6 +594,7 @@ int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n) {
     BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items,
                                prefix[live], b->d_counter, parity, b->stream));
     b->launches += 1;
+    if (b->masked && (rc = enqueue_bounce(b, parity, (int)live, [&](int i) { return nsteps[i] > j; }))) return rc;
   }
   for (int i = 0; i < n; ++i) {
     b->h[i]->t += nsteps[i];

@@ -101,7 +101,7 @@ __global__ void k_nucleate(typename Store<S>::T* __restrict__ pops, const lbm_bu
 
 unsigned grid_for(long long n) {
   long long b = (n + kThreadsG - 1) / kThreadsG;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > device_sm_count() * 8LL) b = device_sm_count() * 8LL;
   return (unsigned)(b < 1 ? 1 : b);
 }
 
@@ -117,7 +117,7 @@ cudaError_t launch_gas_census(const float* rho, long long N, float threshold, in
 
 cudaError_t launch_growth(int storage, void* pops, const int32_t* list, const int* count, long long N,
                           double rate, double budget, double* released, int parity, cudaStream_t s) {
-  const unsigned g = 152 * 4;
+  const unsigned g = (unsigned)device_sm_count() * 4;
   switch (storage) {
     case LBM_F32:
       k_growth<LBM_F32><<<g, kThreadsG, 0, s>>>(static_cast<float*>(pops), list, count, N, rate, budget, released,

@@ -20,6 +20,8 @@ __host__ __device__ constexpr int cx(int i) {
 __host__ __device__ constexpr int cy(int i) {
   return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
 }
+// Opposite direction: e_opp(i) = -e_i.
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5); }
 __host__ __device__ constexpr double wq(int i) {
   return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
@@ -170,6 +172,10 @@ struct BatchItem {
   int inst, x0, width, y0, y1;
 };
 
+// Streaming multiprocessors of the current device (queried once per device;
+// 152 on a GB300 if the query fails). Grids that are sized per SM use it.
+int device_sm_count();
+
 // Launch of the fused step (step.cu). Returns a cudaError_t.
 cudaError_t launch_step(int storage, const StepParams& p, cudaStream_t s);
 // Launch geometry the fused step uses for a box (for tests/benchmarks).
@@ -270,6 +276,18 @@ struct RelabelBox {
 struct RelabelEntry {
   int box, off_tiles, off_scan, off_list;
 };
+
+// Halfway bounce-back across the blocked edges of the mask (the barrier of
+// Sec. 2.1.5), run on the buffer a step has just written (after the growth
+// source, if any): the two slots of each blocked edge trade values, so the
+// next step's pull returns every population that would cross the wall to
+// its own cell in the opposite direction. `two`: 18 planes (two lattices).
+// launch_bounce scans every cell; launch_bounce_boxes walks the tile list of
+// the latest tiled relabel of each box in the entry list, on buffer
+// pops[cur ^ q] (total_list = the entries' list-CTA total).
+cudaError_t launch_bounce(int storage, bool two, void* pops, const uint8_t* mask, int nx, int ny, cudaStream_t s);
+cudaError_t launch_bounce_boxes(int storage, bool two, const RelabelBox* boxes, const RelabelEntry* entries, int m,
+                                int total_list, int q, cudaStream_t s);
 
 // CTAs a box takes in each kind of phase.
 void relabel_entry_sizes(int nx, int ny, int* tiles, int* scan, int* list);

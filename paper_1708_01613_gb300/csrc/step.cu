@@ -825,15 +825,7 @@ bool tma_ok(int nx) {
   return nx % 16 == 0 && nx >= TmaGeom<S>::WIN;
 }
 
-int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      n = 152;
-  }
-  return n;
-}
+int sm_count() { return device_sm_count(); }
 
 // Rows per chunk so that all CTAs are resident at once (one wave).
 void tma_geometry(int nx, int ny, int resident_per_sm, int* gx, int* gy, int* rows) {
@@ -976,9 +968,21 @@ cudaError_t launch_typed(const StepParams& p, cudaStream_t s) {
 
 }  // namespace
 
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk, int* block) {
   const int gx = (nx + kBX - 1) / kBX;
-  const int target = 152 * 6;  // CTAs: a few per SM
+  const int target = device_sm_count() * 6;  // CTAs: a few per SM
   int gy = (target + gx - 1) / gx;
   if (gy > ny) gy = ny;
   if (gy < 1) gy = 1;

@@ -8,7 +8,8 @@
 //   f_s,i  <- f_s,i - (f_s,i - f^eq_i(rho_s, u_s)) / tau_s
 //
 // with psi_s = rho0 (1 - exp(-rho_s/rho0)) (Eq. 30), G_mg = G_gm, and the
-// barrier substitution psi~ = psi_s'(x) across a blocked edge. FP32 storage;
+// barrier substitution psi~ = psi_s'(x) across a blocked edge (where both
+// components' populations bounce back: launch_bounce after the step). FP32 storage;
 // buffer layout: 18 planes, the nine melt planes then the nine gas planes,
 // each holding f^out at its source cell (the next step pulls f_i(x) from
 // x - e_i).
@@ -528,7 +529,7 @@ cudaError_t launch_step2(const Step2Params& p, cudaStream_t s) {
     return one ? launch_step2_tma<false, true>(p, s) : launch_step2_tma<false, false>(p, s);
   }
   const int gx = (p.nx + kBX2C - 1) / kBX2C;
-  int g = (152 * 4 + gx - 1) / gx;  // a few CTAs per SM
+  int g = (device_sm_count() * 4 + gx - 1) / gx;  // a few CTAs per SM
   if (g > p.ny) g = p.ny;
   if (g < 1) g = 1;
   Step2Params q = p;
@@ -547,7 +548,7 @@ cudaError_t launch_step2(const Step2Params& p, cudaStream_t s) {
 cudaError_t launch_fields2(const Step2Params& p, float* rho_m, float* rho_g, float* ux, float* uy, float* pr,
                            cudaStream_t s) {
   long long b = (p.N + 255) / 256;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > device_sm_count() * 8LL) b = device_sm_count() * 8LL;
   k_fields2<<<(unsigned)b, 256, 0, s>>>(p, rho_m, rho_g, ux, uy, pr);
   return cudaGetLastError();
 }

@@ -30,6 +30,8 @@ def test_clock_summary(tmp_path):
 def test_traffic_is_reported_only_for_the_captured_sources_and_size(monkeypatch):
     rec = json.load(open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")))
     n = rec["cells"]
+    # sources as they were when the record was taken
+    monkeypatch.setattr(bench, "sources_sha256", lambda kind: rec["sources_sha256"][kind])
     for key in ("f32", "f16", "two_component"):
         assert bench.kernel_traffic(key, n) == rec[key]["bytes_per_launch_full"]
         assert bench.kernel_traffic(key, n // 4) is None  # another box size

@@ -85,11 +85,14 @@ def _bits_equal_except_near(a, b, ok_mask):
 
 
 @pytest.mark.parametrize("nx,ny", [(160, 80), (164, 84)])
-def test_barrier_parity_two_bubbles_fp32(nx, ny):
+@pytest.mark.parametrize("gap", [6.0, 3.0])
+def test_barrier_parity_two_bubbles_fp32(nx, ny, gap):
     """Barrier on (K = 1): populations within 1e-5 and the owner map and
     blocked-edge mask bit-exact at steps 1, 10, 100 (160 x 80 runs the tiled
-    relabel pipeline, 164 x 84 the untiled one)."""
-    b = two_bubbles(nx, ny, gap=6.0)
+    relabel pipeline, 164 x 84 the untiled one). The 3-cell film has wall
+    cells (owner -2) on its symmetry plane; populations bounce back across
+    every blocked edge."""
+    b = two_bubbles(nx, ny, gap=gap)
     P = O.make_params(nx, ny, barrier=True)
     rho0 = O.init_bubbles(P, b, RL, RG, 4.0)
     sim = gpu_sim(nx, ny, bubbles=b, barrier=True)
@@ -108,6 +111,8 @@ def test_barrier_parity_two_bubbles_fp32(nx, ny):
         assert np.array_equal(got["mask"], ref.mask)
         assert np.array_equal(got["open"], ref.open)
     assert np.count_nonzero(ref.mask) > 0
+    if gap == 3.0:
+        assert np.any(ref.owner == -2)
 
 
 def test_barrier_relabel_period_k():
@@ -246,8 +251,9 @@ def test_full_size_8192_sampled(storage):
     """The benchmark workload (8192^2, 400 bubbles, barrier on, K = 10) in the
     benchmark's launch configuration: one step checked at 4096 sampled cells
     against the oracle evaluated one cell at a time from the GPU's own input
-    state and mask; labels checked as a valid min-index labelling; owners
-    checked at sampled liquid cells by exhaustive window search."""
+    state and mask (force substitution and bounce-back across blocked edges);
+    labels checked as a valid min-index labelling; owners checked at sampled
+    liquid cells by exhaustive window search."""
     n = 8192
     bub = inputs.poisson_disk_bubbles(n, n, 400, 8.0, 64.0, 2.0, seed=21)
     P = O.make_params(n, n, barrier=True, relabel_every=10)
@@ -281,15 +287,18 @@ def test_full_size_8192_sampled(storage):
         if gas[y, x]:
             assert own[y, x] == lab[y, x]
             continue
-        best = None
+        near, best = set(), None
         for dy in range(-R, R + 1):
             for dx in range(-R, R + 1):
-                if dx * dx + dy * dy > R * R:
-                    continue
+                d2 = dx * dx + dy * dy
                 l = lab[(y + dy) % n, (x + dx) % n]
-                if l >= 0 and (best is None or (dx * dx + dy * dy, l) < best):
-                    best = (dx * dx + dy * dy, l)
-        assert own[y, x] == (best[1] if best else -1)
+                if d2 > R * R or l < 0 or (best is not None and d2 > best):
+                    continue
+                if best is None or d2 < best:
+                    near, best = set(), d2
+                near.add(int(l))
+        # nearest bubble, none, or a wall cell (-2) between equidistant bubbles
+        assert own[y, x] == (-1 if not near else (near.pop() if len(near) == 1 else -2))
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
