@@ -41,12 +41,12 @@ def watch_gpu(steps, every, **cfg):
     sim.init_bubbles(BUB, RL, RG, 4.0)
     old = labels_of(sim.read("rho")["rho"])
     counts = []
-    while sim.steps_done() < steps:
+    while sim.steps_done < steps:
         sim.step(every)
         new = labels_of(sim.read("rho")["rho"])
         counts.append(len(np.unique(new[new >= 0])))
         if merged_components(old, new):
-            return sim.steps_done(), counts, sim
+            return sim.steps_done, counts, sim
         old = new
         if counts[-1] < 2:
             break
