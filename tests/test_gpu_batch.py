@@ -122,3 +122,48 @@ def test_step_each_multi_rate_bitwise(storage):
         assert np.array_equal(s.read("pops")["pops"], r.read("pops")["pops"]), (s.nx, s.ny)
         assert np.array_equal(s.read("mask")["mask"], r.read("mask")["mask"])
     b.close()
+
+
+ORACLE_SIZES = [(160, 80), (256, 128), (192, 96), (96, 64)]
+
+
+@pytest.mark.parametrize("storage,K,steps", [("f32", 3, 30), ("f16", 10, 50)])
+def test_batch_matches_oracle(storage, K, steps):
+    """A batch of four boxes of mixed size (barrier on, bubbles 2 cells
+    apart, so walls and rupture are active) against one FP64 oracle run per
+    box: FP32 populations within 1e-5, FP16 deviation storage within 2e-3 on
+    rho; blocked-edge masks equal for FP32."""
+    import oracle as O
+
+    boxes, refs = [], []
+    for i, (nx, ny) in enumerate(ORACLE_SIZES):
+        R = 0.2 * ny
+        bub = [[nx / 2 - R - 1.0, ny / 2, R], [nx / 2 + R + 1.0, ny / 2, R]]
+        P = O.make_params(nx, ny, barrier=True, relabel_every=K)
+        rho0 = O.init_bubbles(P, bub, RL, RG, 4.0)
+        ref = O.OracleSim(P)
+        ref.init_density(rho0)
+        refs.append(ref)
+        sim = Simulation(make_config(nx, ny, storage=storage, barrier=True, relabel_every=K,
+                                     rho_ref=float(np.mean(rho0))))
+        sim.init_density(rho0)
+        boxes.append(sim)
+    b = Batch(boxes)
+    b.step(steps)
+    b.sync()
+    b.close()
+    for s, ref in zip(boxes, refs):
+        ref.step(steps)
+        if storage == "f32":
+            got = s.read("pops", "mask")
+            err = float(np.max(np.abs(got["pops"] - ref.f)) / np.max(np.abs(ref.f)))
+            assert np.array_equal(got["mask"], ref.mask) and ref.opened_total >= 0
+            tol = 1e-5
+        else:
+            rho = ref.fields()["rho"]
+            err = float(np.max(np.abs(s.read("rho")["rho"] - rho)) / np.max(np.abs(rho)))
+            tol = 2e-3
+        print(f"batch {storage} K={K} {s.nx}x{s.ny} step {steps}: rel err {err:.3e}, "
+              f"blocked edges {int(np.count_nonzero(ref.mask))}")
+        assert err < tol, (s.nx, s.ny, err)
+    assert any(np.count_nonzero(r.mask) for r in refs)

@@ -143,8 +143,10 @@ def test_fields_and_labels_parity():
     assert rel_inf(got["rho"], fl["rho"]) < TOL["f32"]
     assert rel_inf(got["p"], fl["p"]) < TOL["f32"]
     umax = max(np.max(np.abs(fl["ux"])), np.max(np.abs(fl["uy"])))
-    assert np.max(np.abs(got["ux"] - fl["ux"])) / umax < 1e-4
-    assert np.max(np.abs(got["uy"] - fl["uy"])) / umax < 1e-4
+    ex = np.max(np.abs(got["ux"] - fl["ux"])) / umax
+    ey = np.max(np.abs(got["uy"] - fl["uy"])) / umax
+    print(f"fields step 50: u rel err {ex:.3e} / {ey:.3e} (max |u| {umax:.3e})")
+    assert ex < 1e-4 and ey < 1e-4
     lab_ref = O.label(P, fl["rho"])
     near = np.abs(fl["rho"] - math.log(2.0)) < 1e-5
     assert _bits_equal_except_near(got["label"], lab_ref, near)
@@ -158,7 +160,9 @@ def test_fields_and_labels_parity():
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_16bit_storage_error(storage):
-    """FP16 deviation storage meets 2e-3 on rho over short horizons; BF16 is
+    """16-bit deviation storage against the oracle over short horizons, with
+    the metrics of the tolerance: rho in the infinity norm relative to
+    max rho, and |u| relative to max |u|. FP16 meets 2e-3 on rho; BF16 is
     reported (8 mantissa bits are not expected to meet it)."""
     nx, ny = 160, 80
     b = two_bubbles(nx, ny, gap=6.0)
@@ -172,8 +176,12 @@ def test_16bit_storage_error(storage):
         sim.step(t - done)
         ref.step(t - done)
         done = t
-        err = rel_inf(sim.read("rho")["rho"], ref.fields()["rho"])
-        print(f"{storage} step {t}: rho rel err {err:.3e}")
+        got = sim.read("rho", "ux", "uy")
+        fl = ref.fields()
+        err = rel_inf(got["rho"], fl["rho"])
+        u_ref = np.hypot(fl["ux"], fl["uy"])
+        u_err = float(np.max(np.abs(np.hypot(got["ux"], got["uy"]) - u_ref)) / np.max(u_ref))
+        print(f"{storage} step {t}: rho rel err {err:.3e}, |u| rel err {u_err:.3e} (max |u| {np.max(u_ref):.3e})")
         if storage == "f16":
             assert err < TOL["f16"], (t, err)
 
@@ -568,7 +576,7 @@ def test_config_1024_clustered_foam(K):
     ref = O.OracleSim(P)
     ref.init_density(rho0)
     sims = {st: gpu_sim(n, n, rho0, storage=st, barrier=True, relabel_every=K) for st in ("f32", "f16")}
-    for steps in (1, 49):
+    for steps in (1, 9, 40):
         ref.step(steps)
         for s in sims.values():
             s.step(steps)
@@ -581,6 +589,8 @@ def test_config_1024_clustered_foam(K):
         print(f"1024^2 K={K} step {ref._s.t}: f32 pops {err:.3e}, f16 rho inf {inf16:.3e} rms {rms16:.3e}")
         assert err < TOL["f32"]
         assert rms16 < TOL["f16"] and inf16 < 5e-2
+        if ref.t <= 10:  # the short horizon of the FP16 tolerance
+            assert inf16 < TOL["f16"], (ref.t, inf16)
         diff = got["mask"] != ref.mask
         if diff.any():
             from scipy.ndimage import binary_dilation

@@ -100,3 +100,33 @@ def test_request_larger_than_budget_is_refused():
     r = requests()[3]
     with pytest.raises(ValueError):
         FoamServer(memory_budget_bytes=footprint_bytes(r) - 1).run([r])
+
+
+@pytest.mark.gpu
+def test_served_results_match_oracle():
+    """A served mix (FP32 and FP16 deviation storage, barrier on, K = 4,
+    staggered arrivals, queueing under a memory budget) against one FP64
+    oracle run per request, from the same initial density: FP32 populations
+    within 1e-5, FP16 within 2e-3 on rho."""
+    import oracle as O
+
+    reqs = requests()
+    budget = sorted(footprint_bytes(r) for r in reqs)[-1] + sorted(footprint_bytes(r) for r in reqs)[-2]
+    server = FoamServer(memory_budget_bytes=budget, max_boxes=4, quantum_updates=2e6, keep_pops=True)
+    served = {r.rid: r for r in server.run(reqs)}
+    for r in reqs:
+        P = O.make_params(r.nx, r.ny, barrier=True, relabel_every=4)
+        ref = O.OracleSim(P)
+        ref.init_density(O.init_bubbles(P, r.bubbles, r.rho_l, r.rho_g, 4.0))
+        ref.step(r.steps)
+        got = served[r.rid]
+        if r.storage == "f32":
+            err = float(np.max(np.abs(got.pops - ref.f)) / np.max(np.abs(ref.f)))
+            tol = 1e-5
+        else:
+            f16 = got.pops.astype(np.float64)
+            rho = ref.f.sum(0)
+            err = float(np.max(np.abs(f16.sum(0) - rho)) / np.max(np.abs(rho)))
+            tol = 2e-3
+        print(f"served {r.rid} {r.nx}x{r.ny} {r.storage} {r.steps} steps: rel err {err:.3e}")
+        assert err < tol, (r.rid, err)

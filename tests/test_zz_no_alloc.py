@@ -21,30 +21,54 @@ from paper_1708_01613_gb300 import lbm as L
 pytestmark = pytest.mark.gpu
 
 
-def test_mass_noalloc_matches_workspace_mass_twice():
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_mass_noalloc_matches_workspace_mass_twice(storage):
+    """512 x 300 cells (three 65,536-cell reduction blocks) of populations
+    from a stepped box. The 16-bit buffer handed to lbm_mass_noalloc holds
+    the deviations g = f - w_i rho_ref rounded to the storage type (the
+    conversion lbm_load_populations applies), so lbm_mass of a box loaded with
+    the same populations sums the same stored values."""
     import torch
 
-    nx, ny = 300, 70
+    nx, ny = 512, 300
     rho = inputs.noise_density(nx, ny, seed=11)
-    sim = Simulation(make_config(nx, ny))
+    rho_ref = float(np.mean(rho))
+    sim = Simulation(make_config(nx, ny, storage=storage, rho_ref=rho_ref))
     sim.init_density(rho)
     sim.step(25)
+    f = sim.read("pops", device=True)["pops"]  # FP32 [9][ny][nx] on the device
+    sim.load_populations(f)
     ref = sim.mass()  # the existing entry point (workspace scratch)
-    pops = sim.read("pops", device=True)["pops"]  # FP32 [9][ny][nx] on the device
-    out = torch.full((1,), float("nan"), dtype=torch.float64, device=pops.device)
+    if storage == "f32":
+        buf = f.contiguous()
+    else:
+        _, _, w = inputs_lattice_weights()
+        wref = torch.tensor([np.float32(wi * rho_ref) for wi in w], dtype=torch.float32, device=f.device)
+        dt = torch.float16 if storage == "f16" else torch.bfloat16
+        buf = (f - wref[:, None, None]).to(dt).contiguous()
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device=f.device)
     lib = L.load_library()
     err = C.create_string_buffer(256)
-    stream = torch.cuda.current_stream(pops.device)
+    stream = torch.cuda.current_stream(f.device)
     for _ in range(2):
         out.fill_(float("nan"))
-        rc = lib.lbm_mass_noalloc(C.c_void_p(pops.data_ptr()), nx, ny, L.STORAGE["f32"], 1.0,
+        rc = lib.lbm_mass_noalloc(C.c_void_p(buf.data_ptr()), nx, ny, L.STORAGE[storage], rho_ref,
                                   C.c_void_p(stream.cuda_stream), C.c_void_p(out.data_ptr()), err, 256)
         assert rc == L.LBM_OK, err.value
         stream.synchronize()
         got = float(out.item())
-        # same FP32 values summed in FP64 in another order
+        # the same stored values summed in FP64 in another order
         assert got == pytest.approx(ref, rel=1e-12, abs=0.0)
-    assert ref == pytest.approx(float(np.sum(rho)), rel=1e-5)
+    assert ref == pytest.approx(float(np.sum(rho)), rel=1e-5 if storage == "f32" else 2e-3)
+
+
+def inputs_lattice_weights():
+    """D2Q9 directions and weights (Eqs. 15-16) as the lattice tables of the
+    test suite give them."""
+    ex = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    ey = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    w = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    return ex, ey, w
 
 
 def test_mass_noalloc_rejects_oversize_and_bad_arguments():
