@@ -309,6 +309,44 @@ def test_full_size_8192_sampled(storage):
         assert own[y, x] == (-1 if not near else (near.pop() if len(near) == 1 else -2))
 
 
+def test_full_box_8192_crop_against_full_oracle():
+    """The benchmark workload (8192^2, 400 bubbles, barrier on, K = 10) run by
+    the oracle on the whole periodic box for 20 steps (two relabels), and the
+    GPU compared with it on a 512^2 crop (a crop of a periodic run is not
+    periodic, so the oracle cannot run the crop alone): FP32 populations
+    within 1e-5, blocked-edge mask and owners equal; FP16 deviation storage
+    within 2e-3 on rho."""
+    n, steps = 8192, 20
+    bub = inputs.poisson_disk_bubbles(n, n, 400, 8.0, 64.0, 2.0, seed=21)
+    P = O.make_params(n, n, barrier=True, relabel_every=10)
+    rho0 = O.init_bubbles(P, bub, RL, RG, 4.0)
+    ref = O.OracleSim(P)
+    ref.init_density(rho0)
+    ref.step(steps)
+    # a crop holding blocked edges if the box has any (the densest 512^2 window)
+    m = (ref.mask != 0).astype(np.int64)
+    tiles = m.reshape(16, 512, 16, 512).sum(axis=(1, 3))
+    ty, tx = np.unravel_index(int(np.argmax(tiles)), tiles.shape)
+    ys, xs = slice(512 * ty, 512 * ty + 512), slice(512 * tx, 512 * tx + 512)
+    rho_ref = ref.f[:, ys, xs].sum(0)
+    for storage in ("f32", "f16"):
+        sim = gpu_sim(n, n, rho0, storage=storage, barrier=True, relabel_every=10, rho_ref=float(RL))
+        sim.step(steps)
+        if storage == "f32":
+            got = sim.read("pops", "mask", "owner")
+            err = rel_inf(got["pops"][:, ys, xs], ref.f[:, ys, xs])
+            assert np.array_equal(got["mask"][ys, xs], ref.mask[ys, xs])
+            assert np.array_equal(got["owner"][ys, xs], ref.owner[ys, xs])
+            tol = TOL["f32"]
+        else:
+            err = rel_inf(sim.read("rho")["rho"][ys, xs], rho_ref)
+            tol = TOL["f16"]
+        print(f"8192^2 {storage} step {steps}, crop ({ty}, {tx}) with {int(tiles[ty, tx])} blocked cells: "
+              f"rel err {err:.3e}")
+        assert err < tol
+        del sim
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("nx,ny,barrier", [(528, 70, False), (272, 9, False), (320, 80, True), (544, 80, True)])
 @pytest.mark.parametrize("tau", [1.0, 0.8])
