@@ -79,7 +79,7 @@ Layout layout_for(const lbm_config& c) {
     L.sgn = take(N);
     L.ntiles = relabel_tile_count(c.nx, c.ny);
     L.tiles = take(3 * (size_t)L.ntiles);  // gas, active, previous active
-    L.tile_list = take(4 * (size_t)L.ntiles);
+    L.tile_list = take(8 * (size_t)L.ntiles);  // work list, then the tiles with a blocked edge
     L.rbox = take(sizeof(RelabelBox) + 2 * sizeof(RelabelEntry));
   }
   if (c.growth) L.gas_list = take(4 * N);
@@ -298,6 +298,7 @@ RelabelBox handle_relabel_box(lbm_handle* h) {
   b.tile_active = h->tiles(1);
   b.tile_prev = h->tiles(2);
   b.tile_list = reinterpret_cast<int*>(h->ws + h->L.tile_list);
+  b.film_list = b.tile_list + h->L.ntiles;
   b.flags = h->flags();
   b.pr = h->pr();
   b.G_mg = (float)c.G_mg;

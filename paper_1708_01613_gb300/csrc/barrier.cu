@@ -536,6 +536,9 @@ __global__ void __launch_bounds__(kThreads) k_stats_partial(long long N, const i
 // of one): each box's CTAs follow those of the boxes before it in the entry
 // list (RelabelEntry prefix sums), and a CTA finds its box by binary search.
 constexpr int kTX = kRelabelTileX, kTY = kRelabelTileY;
+// Mask bits of the directions 1, 2, 5, 6: each blocked edge is seen from the
+// one end where its direction is among these.
+constexpr unsigned kCanonBits = 0x33u;
 // CTAs per box for the tile-list phases, at most: eight per SM
 inline int list_ctas() { return device_sm_count() * 8; }
 
@@ -657,7 +660,10 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
   B.label[c] = lab;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     B.tile_gas[t] = (uint8_t)(any != 0);
-    if (t == 0) B.flags[FLAG_TILES] = 0;  // the tile list is rebuilt by the next phase
+    if (t == 0) {  // the tile lists are rebuilt by the next phase and the mask phase
+      B.flags[FLAG_TILES] = 0;
+      B.flags[FLAG_FILM] = 0;
+    }
   }
 }
 
@@ -734,7 +740,10 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
   *reinterpret_cast<int2*>(B.label + c) = make_int2(laba, labb);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     B.tile_gas[t] = (uint8_t)(any != 0);
-    if (t == 0) B.flags[FLAG_TILES] = 0;  // the tile list is rebuilt by the next phase
+    if (t == 0) {  // the tile lists are rebuilt by the next phase and the mask phase
+      B.flags[FLAG_TILES] = 0;
+      B.flags[FLAG_FILM] = 0;
+    }
   }
 }
 
@@ -959,7 +968,12 @@ __global__ void __launch_bounds__(kTX * kTY) kb_mask(const RelabelBox* __restric
       }
     }
     B.mask[c] = (uint8_t)msk;
-    if (threadIdx.x == 0 && threadIdx.y == 0) B.tile_prev[t] = (uint8_t)act;
+    // tiles holding a blocked edge go to the bounce-back's list
+    const int film = __syncthreads_or((msk & kCanonBits) != 0);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      B.tile_prev[t] = (uint8_t)act;
+      if (film) B.film_list[atomicAdd(B.flags + FLAG_FILM, 1)] = t;
+    }
   }
 }
 
@@ -976,8 +990,6 @@ __global__ void __launch_bounds__(kTX * kTY) kb_mask(const RelabelBox* __restric
 // only, so no two threads touch the same slot. T is the raw storage word
 // (4 or 2 bytes: the values move bit for bit); TWO: a second lattice follows
 // the first nine planes.
-constexpr unsigned kCanonBits = 0x33u;
-
 template <typename T, bool TWO>
 __device__ __forceinline__ void bounce_cell(T* __restrict__ pops, size_t N, int x, int y, int nx, int ny,
                                             unsigned m) {
@@ -1012,8 +1024,9 @@ __global__ void k_bounce(T* __restrict__ pops, const uint8_t* __restrict__ mask,
   }
 }
 
-// Tiled boxes: only the tiles of the latest relabel's work list can hold a
-// blocked edge. Buffer B.pops[B.cur ^ q] of every box in the entry list.
+// Tiled boxes: the mask phase of the latest relabel listed the tiles that
+// hold a blocked edge (a short list: film tiles only). Buffer
+// B.pops[B.cur ^ q] of every box in the entry list.
 template <typename T, bool TWO>
 __global__ void __launch_bounds__(kTX * kTY) kb_bounce(const RelabelBox* __restrict__ boxes,
                                                        const RelabelEntry* __restrict__ e, int m, int q) {
@@ -1021,8 +1034,9 @@ __global__ void __launch_bounds__(kTX * kTY) kb_bounce(const RelabelBox* __restr
   const RelabelBox& B = *lw.B;
   T* pops = static_cast<T*>(const_cast<void*>(B.pops[B.cur ^ q]));
   const size_t N = (size_t)B.nx * B.ny;
-  for (int w = lw.first; w < lw.n; w += lw.stride) {
-    const int t = B.tile_list[w];
+  const int nfilm = B.flags[FLAG_FILM];
+  for (int w = lw.first; w < nfilm; w += lw.stride) {
+    const int t = B.film_list[w];
     const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
     const unsigned msk = B.mask[(size_t)y * B.nx + x];
     if (msk & kCanonBits) bounce_cell<T, TWO>(pops, N, x, y, B.nx, B.ny, msk);

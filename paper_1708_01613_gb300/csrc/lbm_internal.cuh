@@ -38,6 +38,7 @@ enum Flag : int {
   FLAG_GAS = 4,       // gas points in the growth list
   FLAG_ITEM = 5,      // work-item counter of the dynamically scheduled step (0 between launches)
   FLAG_DONE = 6,      // CTAs of that launch that have finished (0 between launches)
+  FLAG_FILM = 7,      // tiles in the list of tiles holding a blocked edge
   FLAG_HIST = 64,     // 64 histogram counters
   FLAG_COUNT = 128
 };
@@ -261,6 +262,7 @@ struct RelabelBox {
   uint8_t* tile_active;
   uint8_t* tile_prev;
   int* tile_list;
+  int* film_list;  // tiles of the work list holding a blocked edge (bounce-back)
   int* flags;
   float* pr;  // two components: mixture pressure written by the density
               // phase and used by the rupture test (nullptr: one component)
@@ -282,9 +284,10 @@ struct RelabelEntry {
 // source, if any): the two slots of each blocked edge trade values, so the
 // next step's pull returns every population that would cross the wall to
 // its own cell in the opposite direction. `two`: 18 planes (two lattices).
-// launch_bounce scans every cell; launch_bounce_boxes walks the tile list of
-// the latest tiled relabel of each box in the entry list, on buffer
-// pops[cur ^ q] (total_list = the entries' list-CTA total).
+// launch_bounce scans every cell; launch_bounce_boxes visits the tiles that
+// the latest tiled relabel of each box in the entry list found holding a
+// blocked edge, on buffer pops[cur ^ q] (total_list = the entries' list-CTA
+// total).
 cudaError_t launch_bounce(int storage, bool two, void* pops, const uint8_t* mask, int nx, int ny, cudaStream_t s);
 cudaError_t launch_bounce_boxes(int storage, bool two, const RelabelBox* boxes, const RelabelEntry* entries, int m,
                                 int total_list, int q, cudaStream_t s);
