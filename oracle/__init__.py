@@ -59,7 +59,7 @@ class _State(C.Structure):
                 ("owner", C.c_void_p), ("sgn", C.c_void_p), ("open", C.c_void_p),
                 ("mask", C.c_void_p), ("t", C.c_int64), ("opened_total", C.c_int64),
                 ("opened_last", C.c_int32), ("halted", C.c_int32), ("gas", C.c_void_p),
-                ("n_gas", C.c_int64), ("injected", C.c_double)]
+                ("n_gas", C.c_int64), ("injected", C.c_double), ("merges_total", C.c_int64)]
 
 
 class Params2(C.Structure):
@@ -111,6 +111,7 @@ def lib():
                                         C.c_double, vp]),
             "orc_stats": (C.c_int32, [P, vp, vp, vp, vp, vp, vp, C.c_int32, C.c_double,
                                       C.c_double]),
+            "orc_merges": (C.c_int32, [P, vp, vp]),
         }
         P2 = C.POINTER(Params2)
         S2 = C.POINTER(_State2)
@@ -226,6 +227,14 @@ def init_bubbles(params: Params, bubbles, rho_l: float, rho_g: float, width: flo
     return out
 
 
+def merges(params: Params, before: np.ndarray, now: np.ndarray) -> int:
+    """Components of the labelling `now` holding gas of two or more
+    components of `before` (coalescence events)."""
+    before = np.ascontiguousarray(before, dtype=np.int32)
+    now = np.ascontiguousarray(now, dtype=np.int32)
+    return int(lib().orc_merges(C.byref(params), _p(before), _p(now)))
+
+
 def step_cells(params: Params, f: np.ndarray, cells, mask_arr: np.ndarray | None = None):
     """Next-step incoming populations at ``cells`` (flat indices) -> (len, 9)."""
     f = np.ascontiguousarray(f, dtype=np.float64)
@@ -275,7 +284,8 @@ class OracleSim:
                          jy=_p(self.jy), psi=_p(self.psi), Fx=_p(self.Fx), Fy=_p(self.Fy),
                          label=_p(self.label), owner=_p(self.owner), sgn=_p(self.sgn),
                          open=_p(self.open), mask=_p(self.mask), t=0, opened_total=0,
-                         opened_last=0, halted=0, gas=_p(self.gas), n_gas=0, injected=0.0)
+                         opened_last=0, halted=0, gas=_p(self.gas), n_gas=0, injected=0.0,
+                         merges_total=0)
 
     def init_density(self, rho: np.ndarray) -> None:
         rho = np.ascontiguousarray(rho, dtype=np.float64)
@@ -319,6 +329,11 @@ class OracleSim:
     @property
     def opened_last(self) -> int:
         return int(self._s.opened_last)
+
+    @property
+    def merges_total(self) -> int:
+        """Coalescence events counted by the relabels so far."""
+        return int(self._s.merges_total)
 
     def fields(self):
         ny, nx = self.params.ny, self.params.nx

@@ -37,6 +37,9 @@
  *   rupture criterion       Sec. 2.1.5, Eq. 41 (eta_m = 0 when d2p/dn2 = 0)
  *   run termination         Sec. 2.1.4 main flowchart and Sec. 5 (the foam
  *                           run ends when the first cell reaches rupture)
+ *   bubble statistics       Sec. 5, Tab. 5 (counts, sizes) and the merging
+ *                           runs of Sec. 4: areas, equivalent diameters and
+ *                           coalescence events between relabels
  *   nucleation and growth   Sec. 2.1.3 (gas nuclei at random sites; every
  *                           step the released gas is added to the gas
  *                           points, dp/dt = A (dn/dt) / N, Eq. 34) and the
@@ -132,6 +135,7 @@ typedef struct {
   uint8_t *gas;            /* [ny][nx] gas points of the latest census */
   int64_t n_gas;           /* their number */
   double injected;         /* gas mass released so far */
+  int64_t merges_total;    /* coalescence events over all relabels so far */
 } orc_state;
 
 static inline int wrap(int a, int n) {
@@ -366,10 +370,44 @@ void orc_mask(const orc_params *p, const int32_t *owner, const uint8_t *open, ui
     }
 }
 
+/* Coalescence events between two labellings of the same box (bubble
+ * statistics, Sec. 5 and the merging runs of Sec. 4): the number of
+ * components of `now` that hold gas cells of two or more components of
+ * `before`. A bubble that grows, shrinks, moves or splits is no event; a
+ * triple merge within the interval is one event. Cells that are gas in only
+ * one of the two labellings do not link components. */
+int32_t orc_merges(const orc_params *p, const int32_t *before, const int32_t *now) {
+  const size_t N = (size_t)p->nx * p->ny;
+  /* first[r]: an old label seen in new component r (-1: none yet);
+     merged[r]: component r already counted */
+  int32_t *first = (int32_t *)malloc(N * sizeof(int32_t));
+  uint8_t *merged = (uint8_t *)calloc(N, 1);
+  for (size_t c = 0; c < N; ++c) first[c] = -1;
+  int32_t events = 0;
+  for (size_t c = 0; c < N; ++c) {
+    const int32_t r = now[c], o = before[c];
+    if (r < 0 || o < 0) continue;
+    if (first[r] < 0) {
+      first[r] = o;
+    } else if (first[r] != o && !merged[r]) {
+      merged[r] = 1;
+      events += 1;
+    }
+  }
+  free(first);
+  free(merged);
+  return events;
+}
+
 /* The barrier pipeline on the populations of the current step. */
 void orc_relabel(const orc_params *p, orc_state *s) {
+  const size_t N = (size_t)p->nx * p->ny;
+  int32_t *before = (int32_t *)malloc(N * sizeof(int32_t));
+  memcpy(before, s->label, N * sizeof(int32_t));
   orc_moments(p, s->f, s->rho, NULL, NULL);
   orc_label(p, s->rho, s->label);
+  s->merges_total += orc_merges(p, before, s->label);
+  free(before);
   orc_owner(p, s->label, s->owner);
   int32_t opened = 0;
   orc_rupture(p, s->rho, s->owner, s->sgn, s->open, &opened);
@@ -429,6 +467,7 @@ void orc_init_state(const orc_params *p, orc_state *s, const double *rho_init) {
   if (s->gas) memset(s->gas, 0, N);
   s->n_gas = 0;
   s->injected = 0.0;
+  s->merges_total = 0;
 }
 
 /* One time step: barrier pipeline when due, then moments (Eq. 11),

@@ -604,6 +604,51 @@ def _watch_two_bubbles(gap, steps, every=100, **kw):
     return None, counts, s
 
 
+def test_merge_events_hand_cases():
+    """Coalescence events between two labellings (components of the later one
+    holding gas of two or more earlier components): a merge of two is one
+    event, of three is one, two separate merges are two; growth, shrinking,
+    a split, a vanished or a new bubble are none."""
+    P = O.make_params(12, 3)
+
+    def lab(*groups):
+        a = np.full((3, 12), -1, np.int32)
+        for cells in groups:
+            idx = np.asarray(cells)
+            a.flat[idx] = idx.min()
+        return a
+
+    A, B, C, D = [0, 1], [3, 4], [6, 7], [9, 10]
+    assert O.merges(P, lab(A, B), lab(A + [2] + B)) == 1
+    assert O.merges(P, lab(A, B, C), lab(A + [2] + B + [5] + C)) == 1
+    assert O.merges(P, lab(A, B, C, D), lab(A + [2] + B, C + [8] + D)) == 2
+    assert O.merges(P, lab(A, B), lab(A, B)) == 0
+    assert O.merges(P, lab(A, B), lab(A + [2, 14], [4])) == 0  # growth and shrinking
+    assert O.merges(P, lab([0, 1, 2, 3]), lab([0, 1], [3])) == 0  # a split
+    assert O.merges(P, lab(A, B), lab(A, [27, 28])) == 0  # one vanished, one new
+    assert O.merges(P, lab(), lab(A)) == 0
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_merge_events_brute_force(seed):
+    """Random gas maps at two times on a 24 x 16 torus, labelled by the
+    oracle: the event count equals a set-based count of new components whose
+    cells carry two or more distinct old labels."""
+    rng = np.random.default_rng(seed)
+    P = O.make_params(24, 16)
+    g0 = rng.random((16, 24)) < 0.45
+    g1 = g0 | (rng.random((16, 24)) < 0.15)
+    g1 &= rng.random((16, 24)) > 0.05
+    l0 = O.label(P, np.where(g0, 0.1, 2.3))
+    l1 = O.label(P, np.where(g1, 0.1, 2.3))
+    want = 0
+    for r in np.unique(l1[l1 >= 0]):
+        olds = set(l0[(l1 == r) & (l0 >= 0)].tolist())
+        want += len(olds) >= 2
+    assert want > 0
+    assert O.merges(P, l0, l1) == want
+
+
 def test_barrier_without_rupture_stops_coalescence():
     """Survey pin 9(ii), the paper's statement that while the oxide-network
     wall stands the bubbles never cross it and do not coalesce (Sec. 2.1.5,
@@ -620,9 +665,9 @@ def test_barrier_without_rupture_stops_coalescence():
     assert t_plain is not None and t_plain <= 1000
     t2, counts2, s2 = _watch_two_bubbles(2.0, 20000, barrier=True, rupture_eps=-1.0)
     assert t2 is None and s2.t == 20000 and counts2[-1] == 2 and min(counts2) == 2
-    assert s2.mask.any() and s2.opened_total == 0
+    assert s2.mask.any() and s2.opened_total == 0 and s2.merges_total == 0
     t3, counts3, s3 = _watch_two_bubbles(3.0, 20000, barrier=True, rupture_eps=-1.0)
-    assert t3 is None and min(counts3[:100]) == 2
+    assert t3 is None and min(counts3[:100]) == 2 and s3.merges_total == 0
 
 
 def test_rupture_lets_the_bubbles_merge_later_than_without_barrier():
@@ -635,6 +680,7 @@ def test_rupture_lets_the_bubbles_merge_later_than_without_barrier():
     t_m, _, s = _watch_two_bubbles(3.0, 20000, every=50, barrier=True)
     assert t_off is not None and t_m is not None
     assert t_m > t_off and s.opened_total > 0
+    assert s.merges_total == 1  # the relabels counted the one coalescence
 
 
 @pytest.mark.parametrize("barrier", [False, True])
