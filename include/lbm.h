@@ -131,6 +131,13 @@ typedef struct {
   double gas_fraction;     /* gas cells / all cells */
   double mean_eq_diameter; /* mean of 2 sqrt(A / pi) over bubbles */
   double mass;             /* FP64 sum of rho */
+  int64_t n_merges;        /* coalescence events since the last init, counted
+                              by every relabel (barrier on; 0 otherwise): the
+                              components of a relabel's labelling that hold
+                              gas cells of two or more components of the
+                              previous relabel's (Sec. 4 merging runs, Sec. 5
+                              statistics); a triple merge between two
+                              relabels is one event */
 } lbm_stats;
 
 typedef struct lbm_handle lbm_handle;
@@ -243,6 +250,15 @@ int lbm_growth_released(lbm_handle* h, double* out);
  * bins over [dmin, dmax) (outliers clamped to the end bins). Synchronises. */
 int lbm_bubble_stats(lbm_handle* h, lbm_stats* out, double* hist, int32_t nbins, double dmin,
                      double dmax);
+
+/* Bubbles of the current density (labels recomputed, as in
+ * lbm_bubble_stats; Sec. 5, Tab. 5 bubble sizes): *n_out = their number;
+ * labels[k] (the smallest row-major index of bubble k) and areas[k] (its
+ * cell count, as a double) in increasing label order, host arrays of
+ * `capacity` entries. If the bubbles outnumber capacity, *n_out is still set
+ * and LBM_EINVAL is returned (call again with room); capacity 0 only counts.
+ * Uses the idle population buffer as scratch. Synchronises. */
+int lbm_bubble_areas(lbm_handle* h, int32_t capacity, int32_t* labels, double* areas, int32_t* n_out);
 
 /* Synchronises the stream and reports device-side faults. */
 int lbm_sync(lbm_handle* h);

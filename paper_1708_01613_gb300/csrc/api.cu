@@ -12,7 +12,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "handle.cuh"
 
@@ -178,6 +180,7 @@ int reset_state(lbm_handle* h) {
     CUDA_TRY(h, cudaMemsetAsync(h->open(), 0, h->N(), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->sgn(), 0, h->N(), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->owner(), 0xff, 4 * h->N(), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->label(), 0xff, 4 * h->N(), h->stream));  // no earlier bubbles
     CUDA_TRY(h, cudaMemsetAsync(h->tiles(0), 0, 3 * (size_t)h->L.ntiles, h->stream));
   }
   CUDA_TRY(h, cudaMemsetAsync(h->released(), 0, 2 * sizeof(double), h->stream));
@@ -208,16 +211,16 @@ int relabel(lbm_handle* h) {
     relabel_entry_sizes(c.nx, c.ny, &totals[0], &totals[1], &totals[2]);
     CUDA_TRY(h, launch_relabel_boxes(c.storage, h->rbox(), h->rentries(), 1, totals, h->cur, h->stream,
                                      h->comps() == 2));
-    h->launches += 7;
+    h->launches += kRelabelLaunches;
     return LBM_OK;
   }
   CUDA_TRY(h, launch_density(fp, h->rho(), h->stream));
-  CUDA_TRY(h, launch_labels(fp, h->rho(), (float)c.gas_threshold, h->label(), h->flags(), h->stream));
+  CUDA_TRY(h, launch_labels(fp, h->rho(), (float)c.gas_threshold, h->label(), h->flags(), h->stream, h->owner()));
   CUDA_TRY(h, launch_owner(c.nx, c.ny, c.zone_radius, h->label(), h->owner(), h->stream));
   CUDA_TRY(h, launch_rupture(c.nx, c.ny, (float)c.G, (float)c.rho0, (float)c.rupture_eps, h->rho(),
                              h->owner(), h->sgn(), h->open(), h->flags(), h->stream));
   CUDA_TRY(h, launch_mask(c.nx, c.ny, h->owner(), h->open(), h->mask(), h->stream));
-  h->launches += 7;
+  h->launches += kRelabelLaunches;
   return LBM_OK;
 }
 
@@ -584,11 +587,14 @@ int lbm_read_fields(lbm_handle* h, uint32_t fields, void* dst, size_t dst_bytes,
         if (!dst_is_device) CUDA_TRY(h, cudaMemcpyAsync(out, stage, nb, d2x, h->stream));
         break;
       }
-      case LBM_FIELD_LABEL:
-        CUDA_TRY(h, launch_labels(fp, h->rho(), (float)h->cfg.gas_threshold, h->label(), h->flags(),
-                                  h->stream));
-        CUDA_TRY(h, cudaMemcpyAsync(out, h->label(), nb, d2x, h->stream));
+      case LBM_FIELD_LABEL: {
+        // into scratch: the relabel pipeline's own labels stay those of the
+        // last relabel (the coalescence count compares the next one with them)
+        int32_t* lab = dst_is_device ? reinterpret_cast<int32_t*>(out) : reinterpret_cast<int32_t*>(stage);
+        CUDA_TRY(h, launch_labels(fp, h->rho(), (float)h->cfg.gas_threshold, lab, h->flags(), h->stream));
+        if (!dst_is_device) CUDA_TRY(h, cudaMemcpyAsync(out, stage, nb, d2x, h->stream));
         break;
+      }
       case LBM_FIELD_OWNER:
       case LBM_FIELD_MASK:
       case LBM_FIELD_OPEN: {
@@ -699,18 +705,22 @@ int lbm_bubble_stats(lbm_handle* h, lbm_stats* out, double* hist, int32_t nbins,
   int rc = select_device(h);
   if (rc) return rc;
   const FieldParams fp = field_params(h);
-  int32_t* area = static_cast<int32_t*>(h->pops(1 - h->cur));
+  // labels and areas in the idle population buffer (>= 18 bytes per cell)
+  int32_t* lab = static_cast<int32_t*>(h->pops(1 - h->cur));
+  int32_t* area = lab + h->N();
   CUDA_TRY(h, launch_density(fp, h->rho(), h->stream));
-  CUDA_TRY(h, launch_labels(fp, h->rho(), (float)h->cfg.gas_threshold, h->label(), h->flags(), h->stream));
-  CUDA_TRY(h, launch_stats(h->cfg.nx, h->cfg.ny, h->label(), area, h->partials(), h->L.nparts, h->scalars(),
+  CUDA_TRY(h, launch_labels(fp, h->rho(), (float)h->cfg.gas_threshold, lab, h->flags(), h->stream));
+  CUDA_TRY(h, launch_stats(h->cfg.nx, h->cfg.ny, lab, area, h->partials(), h->L.nparts, h->scalars(),
                            h->flags() + FLAG_HIST, hist ? nbins : 0, hist ? dmin : 1.0, hist ? dmax : 2.0,
                            h->stream));
   double sc[3];
   int hc[kMaxHistBins];
-  int opened = 0;
+  int opened = 0, merges = 0;
   CUDA_TRY(h, cudaMemcpyAsync(sc, h->scalars(), sizeof(sc), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(hc, h->flags() + FLAG_HIST, sizeof(hc), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(&opened, h->flags() + FLAG_OPENED, sizeof(int), cudaMemcpyDeviceToHost,
+                              h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(&merges, h->flags() + FLAG_MERGES, sizeof(int), cudaMemcpyDeviceToHost,
                               h->stream));
   if ((rc = check_flags(h))) return rc;
   double mass = 0.0;
@@ -722,8 +732,46 @@ int lbm_bubble_stats(lbm_handle* h, lbm_stats* out, double* hist, int32_t nbins,
   out->gas_fraction = sc[1] / (double)h->N();
   out->mean_eq_diameter = sc[0] > 0 ? sc[2] / sc[0] : 0.0;
   out->mass = mass;
+  out->n_merges = merges;
   if (hist)
     for (int b = 0; b < nbins; ++b) hist[b] = hc[b];
+  return LBM_OK;
+}
+
+int lbm_bubble_areas(lbm_handle* h, int32_t capacity, int32_t* labels, double* areas, int32_t* n_out) {
+  if (!h) return LBM_EINVAL;
+  if (!n_out || capacity < 0 || (capacity > 0 && (!labels || !areas)))
+    return fail(h, LBM_EINVAL, "need n_out, and labels and areas for capacity > 0");
+  int rc = select_device(h);
+  if (rc) return rc;
+  const FieldParams fp = field_params(h);
+  const size_t N = h->N();
+  // scratch in the idle population buffer: labels, areas, (root, area) list
+  // (bubbles <= N / 2: each needs a liquid neighbour or covers the box)
+  int32_t* lab = static_cast<int32_t*>(h->pops(1 - h->cur));
+  int32_t* area = lab + N;
+  int32_t* list = area + N;
+  int* count = h->flags() + FLAG_HIST;  // the histogram slots serve as scratch here
+  CUDA_TRY(h, launch_density(fp, h->rho(), h->stream));
+  CUDA_TRY(h, launch_labels(fp, h->rho(), (float)h->cfg.gas_threshold, lab, h->flags(), h->stream));
+  CUDA_TRY(h, launch_bubble_list(h->cfg.nx, h->cfg.ny, lab, area, list, count, h->stream));
+  int n = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&n, count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  if ((rc = check_flags(h))) return rc;
+  *n_out = n;
+  if (n > capacity) return fail(h, LBM_EINVAL, "%d bubbles, capacity %d", n, capacity);
+  std::vector<int32_t> pairs(2 * (size_t)n);
+  if (n) {
+    CUDA_TRY(h, cudaMemcpyAsync(pairs.data(), list, sizeof(int32_t) * 2 * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return pairs[2 * a] < pairs[2 * b]; });
+  for (int k = 0; k < n; ++k) {
+    labels[k] = pairs[2 * order[k]];
+    areas[k] = (double)pairs[2 * order[k] + 1];
+  }
   return LBM_OK;
 }
 

@@ -69,6 +69,45 @@ __global__ void k_label_init(const float* __restrict__ rho, long long N, float t
     L[c] = rho[c] < th ? (int32_t)c : -1;
 }
 
+// Relabel variant of k_label_init: each new gas cell first parks its label of
+// the previous relabel in keep[c] (INT_MAX where it was liquid) for the
+// coalescence count; keep is the owner array, which the owner phase
+// rewrites afterwards.
+__global__ void k_label_init_keep(const float* __restrict__ rho, long long N, float th, int32_t* L,
+                                  int32_t* __restrict__ keep) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const bool gas = rho[c] < th;
+    if (gas) {
+      const int32_t o = L[c];
+      keep[c] = o >= 0 ? o : 0x7fffffff;
+    }
+    L[c] = gas ? (int32_t)c : -1;
+  }
+}
+
+// Coalescence events (components of the new labelling holding gas of two or
+// more components of the previous one). keep[r] of a new root r collects the
+// first earlier label seen in its component (the root starts with its own);
+// a member with another earlier label marks the component (-3), and the one
+// that marks it first counts it, so every merged component counts once.
+__device__ __forceinline__ int merge_vote(int32_t* keep, int r, int o) {
+  if (o == 0x7fffffff) return 0;
+  const int prev = atomicCAS(keep + r, 0x7fffffff, o);
+  if (prev == 0x7fffffff || prev == o || prev == -3) return 0;
+  return atomicExch(keep + r, -3) != -3;
+}
+
+__global__ void k_merge_count(long long N, const int32_t* __restrict__ L, int32_t* keep, int* flags) {
+  int n = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int r = L[c];
+    if (r >= 0 && r != c) n += merge_vote(keep, r, keep[c]);
+  }
+  if (n) atomicAdd(flags + FLAG_MERGES, n);
+}
+
 __device__ int find_root(const int32_t* L, int a, int* fail) {
   for (int it = 0; it < kUnionIters; ++it) {
     const int p = L[a];
@@ -491,6 +530,26 @@ __global__ void k_area(long long N, const int32_t* __restrict__ L, int32_t* __re
   }
 }
 
+// Roots with their areas appended to list (warp-aggregated slots).
+__global__ void k_bubble_list(long long N, const int32_t* __restrict__ L, const int32_t* __restrict__ area,
+                              int32_t* __restrict__ list, int* count) {
+  for (long long c0 = blockIdx.x * (long long)blockDim.x; c0 < N; c0 += (long long)gridDim.x * blockDim.x) {
+    const long long c = c0 + threadIdx.x;
+    const bool root = c < N && L[c] == c;
+    const unsigned b = __ballot_sync(0xffffffffu, root);
+    if (!b) continue;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(b) - 1) base = atomicAdd(count, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+    if (root) {
+      const int k = base + __popc(b & ((1u << lane) - 1u));
+      list[2 * k] = (int32_t)c;
+      list[2 * k + 1] = area[c];
+    }
+  }
+}
+
 // partial sums: [0] bubbles, [1] gas cells, [2] sum of equivalent diameters;
 // histogram counts are integers, accumulated exactly with atomics
 constexpr int kMaxBins = 64;
@@ -657,6 +716,10 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
     if (gas) lab = tile_root_index(sp, li, x - threadIdx.x, y - threadIdx.y, nx, &fail);
     if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
   }
+  if (gas) {  // the label of the previous relabel, for the coalescence count
+    const int32_t o = B.label[c];
+    B.owner[c] = o >= 0 ? o : 0x7fffffff;
+  }
   B.label[c] = lab;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     B.tile_gas[t] = (uint8_t)(any != 0);
@@ -736,6 +799,11 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
     if (ga) laba = tile_root_index(sp, la, x0, y0, nx, &fail);
     if (gb) labb = tile_root_index(sp, lb, x0, y0, nx, &fail);
     if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
+  }
+  if (ga || gb) {  // labels of the previous relabel, for the coalescence count
+    const int2 o = *reinterpret_cast<const int2*>(B.label + c);
+    if (ga) B.owner[c] = o.x >= 0 ? o.x : 0x7fffffff;
+    if (gb) B.owner[c + 1] = o.y >= 0 ? o.y : 0x7fffffff;
   }
   *reinterpret_cast<int2*>(B.label + c) = make_int2(laba, labb);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -826,6 +894,25 @@ __global__ void __launch_bounds__(kTX * kTY) kb_flatten(const RelabelBox* __rest
     if (L[c] >= 0) L[c] = find_root(L, c, &fail);
   }
   if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
+}
+
+// Coalescence events of the relabel (merge_vote), over the listed tiles
+// with gas; runs between the flatten and the owner phase, whose owner array
+// holds the earlier labels the density phase parked there.
+__global__ void __launch_bounds__(kTX * kTY) kb_merge(const RelabelBox* __restrict__ boxes,
+                                                      const RelabelEntry* __restrict__ e, int m) {
+  const ListWalk lw = list_walk(boxes, e, m);
+  const RelabelBox& B = *lw.B;
+  int n = 0;
+  for (int w = lw.first; w < lw.n; w += lw.stride) {
+    const int t = B.tile_list[w];
+    if (!B.tile_gas[t]) continue;
+    const int c = ((t / B.ntx) * kTY + threadIdx.y) * B.nx + (t % B.ntx) * kTX + threadIdx.x;
+    const int r = B.label[c];
+    if (r >= 0 && r != c) n += merge_vote(B.owner, r, B.owner[c]);
+  }
+  n = __syncthreads_count(n);
+  if (n && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(B.flags + FLAG_MERGES, n);
 }
 
 // Owner from the labels within radius R of the window position row0 (window
@@ -1067,11 +1154,13 @@ cudaError_t launch_density(const FieldParams& fp, float* rho, cudaStream_t s) {
 }
 
 cudaError_t launch_labels(const FieldParams& fp, const float* rho, float threshold, int32_t* label,
-                          int* flags, cudaStream_t s) {
+                          int* flags, cudaStream_t s, int32_t* keep) {
   const unsigned b = blocks_for(fp.N);
-  k_label_init<<<b, kThreads, 0, s>>>(rho, fp.N, threshold, label);
+  if (keep) k_label_init_keep<<<b, kThreads, 0, s>>>(rho, fp.N, threshold, label, keep);
+  else k_label_init<<<b, kThreads, 0, s>>>(rho, fp.N, threshold, label);
   k_label_union<<<b, kThreads, 0, s>>>(fp.nx, fp.ny, label, flags);
   k_label_flatten<<<b, kThreads, 0, s>>>(fp.N, label, flags);
+  if (keep) k_merge_count<<<b, kThreads, 0, s>>>(fp.N, label, keep, flags);
   return cudaGetLastError();
 }
 
@@ -1199,6 +1288,17 @@ cudaError_t launch_stats(int nx, int ny, const int32_t* label, int32_t* area, do
   return cudaGetLastError();
 }
 
+cudaError_t launch_bubble_list(int nx, int ny, const int32_t* label, int32_t* area, int32_t* list, int* count,
+                               cudaStream_t s) {
+  const long long N = (long long)nx * ny;
+  cudaError_t e = cudaMemsetAsync(area, 0, sizeof(int32_t) * N, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_area<<<blocks_for(N), kThreads, 0, s>>>(N, label, area);
+  k_bubble_list<<<blocks_for(N), kThreads, 0, s>>>(N, label, area, list, count);
+  return cudaGetLastError();
+}
+
 bool relabel_tiled_ok(int nx, int ny, int R) { return nx % kTX == 0 && ny % kTY == 0 && R <= kOMaxR; }
 
 int relabel_tile_count(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY); }
@@ -1233,6 +1333,7 @@ cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const Rel
   kb_active<<<totals[1], kThreads, 0, s>>>(boxes, entries, m);
   kb_union<<<totals[2], block, 0, s>>>(boxes, entries, m);
   kb_flatten<<<totals[2], block, 0, s>>>(boxes, entries, m);
+  kb_merge<<<totals[2], block, 0, s>>>(boxes, entries, m);
   kb_owner<<<totals[2], block, 0, s>>>(boxes, entries, m);
   if (two) kb_rupture<true><<<totals[2], block, 0, s>>>(boxes, entries, m);
   else kb_rupture<false><<<totals[2], block, 0, s>>>(boxes, entries, m);

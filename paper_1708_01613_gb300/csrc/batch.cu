@@ -231,7 +231,7 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
       lbm_handle* h = b->h[i];
       if (!handle_relabel_tiled(h)) {
         b->untiled.push_back(i);
-        b->relabel_launches += 7;
+        b->relabel_launches += kRelabelLaunches;
         b->bounce_launches += 1;
         continue;
       }
@@ -252,7 +252,7 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
         g.tot.push_back(acc);
       }
       ents.push_back({-1, acc[0], acc[1], acc[2]});
-      b->relabel_launches += 7;
+      b->relabel_launches += kRelabelLaunches;
     }
     BCUDA(b, cudaMemcpyAsync(b->d_rboxes, rboxes.data(), sizeof(RelabelBox) * b->n, cudaMemcpyHostToDevice,
                              b->stream));
@@ -283,7 +283,7 @@ int enqueue_relabel(lbm_batch* b, int parity, int64_t j, int live, Stepping step
     if (m > 0) {
       BCUDA(b, launch_relabel_boxes(b->storage, b->d_rboxes, b->d_rent + g.start, m, g.tot[m].data(), parity,
                                     b->stream));
-      b->launches += 7;
+      b->launches += kRelabelLaunches;
     }
   }
   for (int i : b->untiled) {
@@ -297,7 +297,7 @@ int enqueue_relabel(lbm_batch* b, int parity, int64_t j, int live, Stepping step
     h->stream = hs;
     h->cur = saved;
     if (rc) return bfail(b, rc, "relabel of box %d: %s", i, h->err);
-    b->launches += 7;
+    b->launches += kRelabelLaunches;
   }
   return LBM_OK;
 }

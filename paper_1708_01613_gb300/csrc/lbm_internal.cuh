@@ -39,6 +39,7 @@ enum Flag : int {
   FLAG_ITEM = 5,      // work-item counter of the dynamically scheduled step (0 between launches)
   FLAG_DONE = 6,      // CTAs of that launch that have finished (0 between launches)
   FLAG_FILM = 7,      // tiles in the list of tiles holding a blocked edge
+  FLAG_MERGES = 8,    // coalescence events counted by the relabels since the last init
   FLAG_HIST = 64,     // 64 histogram counters
   FLAG_COUNT = 128
 };
@@ -218,8 +219,17 @@ struct FieldParams {
 };
 
 cudaError_t launch_density(const FieldParams& fp, float* rho, cudaStream_t s);
+// Gas labels (4-connected, smallest index) of rho into label. With keep (the
+// relabel pipeline: the owner array), each new gas cell first parks its
+// label of the previous relabel there and the coalescence events are added
+// to flags[FLAG_MERGES]; keep = nullptr for diagnostics.
 cudaError_t launch_labels(const FieldParams& fp, const float* rho, float threshold, int32_t* label,
-                          int* flags, cudaStream_t s);
+                          int* flags, cudaStream_t s, int32_t* keep = nullptr);
+// Per-bubble areas of a label array: roots (label[c] == c) with their cell
+// counts appended to list (pairs root, area) in any order; the count goes to
+// *count (device). area: N int32 scratch.
+cudaError_t launch_bubble_list(int nx, int ny, const int32_t* label, int32_t* area, int32_t* list, int* count,
+                               cudaStream_t s);
 cudaError_t launch_owner(int nx, int ny, int R, const int32_t* label, int32_t* owner, cudaStream_t s);
 cudaError_t launch_rupture(int nx, int ny, float G, float rho0, float eps, const float* rho,
                            const int32_t* owner, int8_t* sgn, uint8_t* open, int* flags,
@@ -247,6 +257,9 @@ constexpr int kMaxHistBins = 64;
 bool relabel_tiled_ok(int nx, int ny, int R);
 int relabel_tile_count(int nx, int ny);
 constexpr int kRelabelTileX = 32, kRelabelTileY = 8;  // tile of the pipeline
+// Launches of one relabel: density, tile scan (tiled) or label init (untiled),
+// union, flatten, coalescence count, owner, rupture, mask.
+constexpr int kRelabelLaunches = 8;
 
 // A box as the pipeline sees it (device memory). Populations are read from
 // pops[cur ^ parity], parity being the launch argument.

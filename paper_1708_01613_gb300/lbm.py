@@ -53,7 +53,7 @@ class lbm_bubble(C.Structure):
 class lbm_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("n_bubbles", C.c_int32), ("reserved", C.c_int32),
                 ("n_open", C.c_int64), ("gas_fraction", C.c_double),
-                ("mean_eq_diameter", C.c_double), ("mass", C.c_double)]
+                ("mean_eq_diameter", C.c_double), ("mass", C.c_double), ("n_merges", C.c_int64)]
 
 
 # Every entry point of include/lbm.h with its ctypes signature.
@@ -78,6 +78,7 @@ SIGNATURES = {
     "lbm_growth_released": (C.c_int, [_vp, C.POINTER(C.c_double)]),
     "lbm_bubble_stats": (C.c_int, [_vp, C.POINTER(lbm_stats), _vp, C.c_int32, C.c_double,
                                    C.c_double]),
+    "lbm_bubble_areas": (C.c_int, [_vp, C.c_int32, _vp, _vp, C.POINTER(C.c_int32)]),
     "lbm_sync": (C.c_int, [_vp]),
     "lbm_last_error": (C.c_char_p, [_vp]),
     "lbm_destroy": (None, [_vp]),
@@ -331,7 +332,24 @@ class Simulation:
                    int(nbins), float(dmin), float(dmax))
         return {"step": st.step, "n_bubbles": st.n_bubbles, "n_open": st.n_open,
                 "gas_fraction": st.gas_fraction, "mean_diameter": st.mean_eq_diameter,
-                "mass": st.mass, "hist": hist[:nbins].copy()}
+                "mass": st.mass, "n_merges": st.n_merges, "hist": hist[:nbins].copy()}
+
+    def bubble_areas(self):
+        """(labels, areas) of the bubbles of the current density, in
+        increasing label order (labels int32, areas float64 cell counts)."""
+        n = C.c_int32(0)
+        lib = load_library()
+        import torch
+
+        with torch.cuda.device(self.device):
+            rc = lib.lbm_bubble_areas(self.handle, 0, None, None, C.byref(n))
+        if rc not in (LBM_OK, LBM_EINVAL):
+            _check(rc, self.handle)
+        labels = np.zeros(max(n.value, 1), np.int32)
+        areas = np.zeros(max(n.value, 1), np.float64)
+        self._call("lbm_bubble_areas", int(len(labels)), C.c_void_p(labels.ctypes.data),
+                   C.c_void_p(areas.ctypes.data), C.byref(n))
+        return labels[:n.value].copy(), areas[:n.value].copy()
 
     def sync(self) -> None:
         self._call("lbm_sync")

@@ -94,3 +94,25 @@ def test_gpu_rupture_merge_step_matches_oracle(K):
     assert t_gpu is not None and t_orc is not None and t_plain is not None
     assert t_gpu > t_plain
     assert abs(t_gpu - t_orc) <= 0.1 * t_orc
+
+
+def test_gpu_coalescence_events_and_areas():
+    """The relabels' coalescence count and the per-bubble areas through the
+    C ABI: one event when the 2-cell film ruptures and the pair merges (none
+    without rupture), and the bubbles' labels and areas of the initial
+    density equal the oracle's labelling of the same density."""
+    bub2 = [[NX / 2 - R - 1.0, NY / 2, R], [NX / 2 + R + 1.0, NY / 2, R]]
+    for eps, want in ((1e-6, 1), (-1.0, 0)):
+        sim = Simulation(make_config(NX, NY, barrier=True, rho_ref=float(RL), rupture_eps=eps))
+        sim.init_bubbles(bub2, RL, RG, 4.0)
+        if eps > 0:
+            labels, areas = sim.bubble_areas()
+            rho0 = O.init_bubbles(O.make_params(NX, NY), bub2, RL, RG, 4.0)
+            so = O.stats(O.make_params(NX, NY), labels_of(rho0))
+            lo = labels_of(rho0)
+            assert np.array_equal(labels, np.unique(lo[lo >= 0]))
+            assert np.array_equal(areas, so["areas"])
+        sim.step(600)
+        st = sim.stats()
+        print(f"eps {eps}: bubbles {st['n_bubbles']}, coalescence events {st['n_merges']}")
+        assert st["n_merges"] == want
