@@ -516,7 +516,7 @@ def run_batched(args, dev, world, rank):
     bat.close()
     del bat, bat_boxes
     torch.cuda.empty_cache()
-    return {"workload": "64 boxes, sides 256-2048 log-uniform (multiples of 64), 5-200 Poisson-disk bubbles, "
+    return {"workload": "64 boxes, sides 256-2048 log-uniform (any integer), 5-200 Poisson-disk bubbles, "
                         "1k-20k steps each (log-uniform), FP16-deviation storage, barrier on (K=10, R_z=4)",
             "step_scale": scale, "cell_updates": updates,
             "value": round(world * updates / t_bat / 1e6, 1), "unit": "MLUPS",

@@ -273,13 +273,15 @@ void lbm_destroy(lbm_handle* h);
  * Batches: many boxes advanced together. Not in the paper; it serves runs
  * of many independent foam simulations on one GPU. Every step of a batch is
  * one persistent launch of the two-cell staged kernel over a list of work
- * items (box, column strip, row chunk) of all active boxes, preceded, when a
- * relabel is due, by each box's barrier pipeline; blocks of steps are
- * captured as CUDA graphs and replayed. Each box evolves bitwise as it would
- * when stepped alone with lbm_step.
+ * items (box, column strip, row chunk) of all active boxes with nx % 16 == 0
+ * (rows the bulk copies can stage), plus one plain-load step per other box,
+ * preceded, when a relabel is due, by each box's barrier pipeline and
+ * followed, with the barrier, by the bounce-back across blocked edges;
+ * blocks of steps are captured as CUDA graphs and replayed. Each box evolves
+ * bitwise as it would when stepped alone with lbm_step.
  *
  * Rules: all boxes share storage, barrier setting and relabel period, are
- * on one device, have nx % 16 == 0, and do not stop on rupture. Boxes may be
+ * on one device, and do not stop on rupture. Boxes may be
  * at different step counts (each relabels when its own count is due). The batch works on a stream of its own (created by
  * lbm_batch_create; the legacy default stream cannot be captured into a
  * graph), ordered by events after earlier work on the first box's stream,

@@ -16,7 +16,7 @@ Workload recipes (lattice units, periodic boxes):
   edge gap drawn from U[gap_lo, gap_hi] in a random direction, and is
   rejected if its gap to any other bubble is below ``gap_lo``;
 * batched instances and serving requests: sides, bubble counts and step
-  counts drawn log-uniformly, sides rounded to a multiple of 64.
+  counts drawn log-uniformly (sides rounded to the nearest integer).
 
 The liquid and gas densities used to initialise bubbles are plain numbers
 here (``RHO_LIQ_G55``, ``RHO_GAS_G55``); the tests check them against the
@@ -131,8 +131,9 @@ def clustered_bubbles(nx: int, ny: int, n: int, rmin: float, rmax: float,
     return np.asarray(out, dtype=np.float64).reshape(-1, 3)
 
 
-def log_uniform_sides(count: int, lo: int, hi: int, seed: int, multiple: int = 64) -> list[int]:
-    """``count`` box sides drawn log-uniformly in [lo, hi], rounded to ``multiple``."""
+def log_uniform_sides(count: int, lo: int, hi: int, seed: int, multiple: int = 1) -> list[int]:
+    """``count`` box sides drawn log-uniformly in [lo, hi], rounded to ``multiple``
+    (1: any integer side)."""
     s = _Stream(seed)
     out = []
     for _ in range(count):
@@ -148,7 +149,7 @@ def batch_instances(count: int = 64, side_lo: int = 256, side_hi: int = 2048,
     s = _Stream(seed)
     out = []
     for i in range(count):
-        side = int(min(side_hi, max(side_lo, 64 * round(s.log_uniform(side_lo, side_hi) / 64))))
+        side = int(min(side_hi, max(side_lo, round(s.log_uniform(side_lo, side_hi)))))
         nb = int(round(s.log_uniform(bub_lo, bub_hi)))
         steps = int(round(s.log_uniform(steps_lo, steps_hi)))
         # keep the bubble area below ~35 % of the box
@@ -189,7 +190,7 @@ def serving_requests(count: int = 2000, rate_per_s: float = 10.0, side_lo: int =
     out = []
     for i in range(count):
         t += -math.log(1.0 - s.uniform()) / rate_per_s
-        side = int(min(side_hi, max(side_lo, 64 * round(s.log_uniform(side_lo, side_hi) / 64))))
+        side = int(min(side_hi, max(side_lo, round(s.log_uniform(side_lo, side_hi)))))
         nb = int(round(s.log_uniform(bub_lo, bub_hi)))
         steps = int(round(s.log_uniform(steps_lo, steps_hi)))
         fp16 = s.uniform() < fp16_fraction

@@ -55,17 +55,19 @@ struct lbm_batch {
   };
   std::map<int, Group> groups;            // by residue of the step count
   std::vector<int> untiled;               // boxes relabelled one by one
-  int64_t relabel_launches = 0;           // per relabel period
+  std::vector<char> lone;                 // boxes the staged kernel cannot take (rows
+                                          // not 16-byte multiples): stepped by the
+                                          // plain-load kernel in the same sequence
   // bounce-back after each step: tiled boxes together (entries d_bent, in
   // stepping order), untiled boxes one by one
   RelabelEntry* d_bent = nullptr;
   std::vector<int> bounce_first;          // tiled boxes among the first k stepping boxes
   std::vector<int> bounce_ctas;           // list CTAs of the first k tiled boxes
-  int64_t bounce_launches = 0;            // per step
   int strip = 512, rows = 0;
   int use_graph = 1;
   int dirty = 1;               // descriptors/items must be re-uploaded
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // K-step block starting at parity 0 / 1
+  int64_t graph_launches[2] = {0, 0};             // kernels in each graph
   int64_t launches = 0;
   char err[320] = {0};
 };
@@ -124,7 +126,7 @@ void build_items(lbm_batch* b, bool spread) {
   auto count = [&](int rows) {
     long long c = 0;
     for (int i = 0; i < b->n; ++i)
-      if (b->active[i])
+      if (b->active[i] && !b->lone[i])
         c += (long long)((b->h[i]->cfg.nx + b->strip - 1) / b->strip) * ((b->h[i]->cfg.ny + rows - 1) / rows);
     return c;
   };
@@ -142,7 +144,7 @@ void build_items(lbm_batch* b, bool spread) {
     rows_all = lo;
   }
   for (int i = 0; i < b->n; ++i) {
-    if (!b->active[i]) continue;
+    if (!b->active[i] || b->lone[i]) continue;
     const int nx = b->h[i]->cfg.nx, ny = b->h[i]->cfg.ny;
     const int strips = (nx + b->strip - 1) / b->strip;
     const int rows = spread ? std::max(1, std::min(rows_all, (strips * ny + kMinItems - 1) / kMinItems)) : rows_all;
@@ -204,10 +206,8 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
   BCUDA(b, cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), b->stream));  // item counters (step parity)
   b->groups.clear();
   b->untiled.clear();
-  b->relabel_launches = 0;
   b->bounce_first.assign(1, 0);
   b->bounce_ctas.assign(1, 0);
-  b->bounce_launches = 0;
   std::vector<RelabelEntry> ents, bents;
   if (b->masked) {
     std::vector<int> ord = order;
@@ -226,13 +226,10 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
       b->bounce_first.push_back(b->bounce_first.back() + (tiled ? 1 : 0));
     }
     bents.push_back({-1, 0, 0, b->bounce_ctas.back()});
-    b->bounce_launches = (bents.size() > 1 ? 1 : 0);
     for (int i : ord) {
       lbm_handle* h = b->h[i];
       if (!handle_relabel_tiled(h)) {
         b->untiled.push_back(i);
-        b->relabel_launches += kRelabelLaunches;
-        b->bounce_launches += 1;
         continue;
       }
       // due at batch count T when T + (t_i - t_batch) is a multiple of r
@@ -252,7 +249,6 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
         g.tot.push_back(acc);
       }
       ents.push_back({-1, acc[0], acc[1], acc[2]});
-      b->relabel_launches += kRelabelLaunches;
     }
     BCUDA(b, cudaMemcpyAsync(b->d_rboxes, rboxes.data(), sizeof(RelabelBox) * b->n, cudaMemcpyHostToDevice,
                              b->stream));
@@ -302,6 +298,22 @@ int enqueue_relabel(lbm_batch* b, int parity, int64_t j, int live, Stepping step
   return LBM_OK;
 }
 
+// The boxes outside the item list (lone) that step now: one plain-load step
+// each, on the buffers of parity `parity`, on the batch stream.
+template <class Stepping>
+int enqueue_lone(lbm_batch* b, int parity, Stepping stepping) {
+  for (int i = 0; i < b->n; ++i) {
+    if (!b->lone[i] || !stepping(i)) continue;
+    lbm_handle* h = b->h[i];
+    StepParams p = handle_step_params(h);
+    p.src = h->pops(b->base_cur[i] ^ parity);
+    p.dst = h->pops(b->base_cur[i] ^ parity ^ 1);
+    BCUDA(b, launch_step(b->storage, p, b->stream));
+    b->launches += 1;
+  }
+  return LBM_OK;
+}
+
 // Bounce-back across blocked edges after the batched step of parity
 // `parity`: the first `first` boxes of the stepping order (all of them when
 // first < 0), on the buffers that step wrote.
@@ -341,9 +353,12 @@ int enqueue_step(lbm_batch* b, int parity, int64_t j) {
   int rc;
   if (b->masked && (rc = enqueue_relabel(b, parity, j, -1, [&](int i) { return b->active[i] != 0; })))
     return rc;
-  BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items, b->nitems,
-                             b->d_counter, parity, b->stream));
-  b->launches += 1;
+  if (b->nitems) {
+    BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items, b->nitems,
+                               b->d_counter, parity, b->stream));
+    b->launches += 1;
+  }
+  if ((rc = enqueue_lone(b, parity, [&](int i) { return b->active[i] != 0; }))) return rc;
   if (b->masked && (rc = enqueue_bounce(b, parity, -1, [&](int i) { return b->active[i] != 0; }))) return rc;
   return LBM_OK;
 }
@@ -355,6 +370,7 @@ int build_graph(lbm_batch* b, int start_parity) {
   int rc = LBM_OK;
   for (int j = 0; j < b->K && rc == LBM_OK; ++j) rc = enqueue_step(b, start_parity ^ (j & 1), j);
   const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  b->graph_launches[start_parity] = b->launches - saved;
   b->launches = saved;  // counted again at every replay
   if (rc) {
     if (g) cudaGraphDestroy(g);
@@ -417,7 +433,6 @@ int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, s
     if (h->cfg.barrier && h->cfg.relabel_every != h0->cfg.relabel_every) return LBM_EINVAL;
     if (h->cfg.stop_on_first_rupture || h->cfg.growth || h->cfg.components != 1) return LBM_ENOTSUP;
     if (h->device != h0->device || h->halted) return LBM_EINVAL;
-    if (h->cfg.nx % 16 != 0) return LBM_ENOTSUP;  // bulk copies need 16-byte rows
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_ENOMEM;
@@ -425,6 +440,8 @@ int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, s
   b->h.assign(handles, handles + n);
   b->active.assign(n, 1);
   b->base_cur.assign(n, 0);
+  b->lone.assign(n, 0);
+  for (int i = 0; i < n; ++i) b->lone[i] = !step_tma2_allowed(handles[i]->cfg.storage, handles[i]->cfg.nx);
   b->storage = h0->cfg.storage;
   b->masked = h0->cfg.barrier;
   // graph block: one relabel period with the barrier, else 16 steps
@@ -523,8 +540,7 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     const int p = b->par;
     if (!b->graph[p] && (rc = build_graph(b, p))) return rc;
     BCUDA(b, cudaGraphLaunch(b->graph[p], b->stream));
-    // every group relabels once per period; a bounce-back follows every step
-    b->launches += b->K * (1 + b->bounce_launches) + b->relabel_launches;
+    b->launches += b->graph_launches[p];
     advance(b, b->K);
     left -= b->K;
   }
@@ -591,9 +607,12 @@ int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n) {
       }
       if ((rc = enqueue_relabel(b, parity, j, gl, [&](int i) { return nsteps[i] > j; }))) return rc;
     }
-    BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items,
-                               prefix[live], b->d_counter, parity, b->stream));
-    b->launches += 1;
+    if (prefix[live]) {
+      BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items,
+                                 prefix[live], b->d_counter, parity, b->stream));
+      b->launches += 1;
+    }
+    if ((rc = enqueue_lone(b, parity, [&](int i) { return nsteps[i] > j; }))) return rc;
     if (b->masked && (rc = enqueue_bounce(b, parity, (int)live, [&](int i) { return nsteps[i] > j; }))) return rc;
   }
   for (int i = 0; i < n; ++i) {
