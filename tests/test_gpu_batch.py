@@ -113,13 +113,13 @@ def test_step_each_multi_rate_bitwise(storage):
     boxes = [make_box(nx, ny, storage, True, K, 300 + i) for i, (nx, ny) in enumerate(SIZES)]
     ref = [make_box(nx, ny, storage, True, K, 300 + i) for i, (nx, ny) in enumerate(SIZES)]
     b = Batch(boxes)
-    plan = [[7, 0, 3, 12, 1], [2, 5, 5, 0, 9]]
+    plan = [[7, 0, 3, 12, 1, 5, 2], [2, 5, 5, 0, 9, 1, 6]]
     b.step_each(plan[0])
     b.step(4)
     b.set_active(3, False)
     b.step_each(plan[1])
     with pytest.raises(LbmError):
-        b.step_each([1, 1, 1, 1, 1])  # box 3 is switched off
+        b.step_each([1] * len(SIZES))  # box 3 is switched off
     b.sync()
     total = [p0 + 4 + p1 for p0, p1 in zip(*plan)]
     assert b.steps_done == 12 + 4 + 9
