@@ -188,9 +188,12 @@ int64_t lbm_kernel_launches(const lbm_handle* h);
 /* Selects the fused-step kernel: 0 = automatic, 1 = plain-load kernel (any
  * box), 2 = TMA-staged kernel with one cell per thread (nx % 16 == 0 and
  * nx >= 272), 3 = TMA-staged kernel with two cells per thread, one row
- * chunk per CTA (nx % 16 == 0), 4 = the same with row chunks drawn by the
- * CTAs from a counter (nx % 16 == 0). Automatic picks 4 where the box
- * allows (3 when the box has no more chunks than CTAs fit the GPU), else 1. A variant the box does not allow returns LBM_ENOTSUP. All
+ * chunk per CTA (nx >= 16), 4 = the same with row chunks drawn by the
+ * CTAs from a counter (nx >= 16). Variants 3 and 4 bulk-copy whole rows
+ * when nx % 16 == 0, else each row's 16-byte-aligned interior, with the
+ * unaligned head, tail and wrapped halo loaded plainly. Automatic picks 4
+ * where the box allows (3 when the box has no more chunks than CTAs fit the
+ * GPU), else 1. A variant the box does not allow returns LBM_ENOTSUP. All
  * variants compute the same operations in the same order and give bitwise
  * the same populations. The same handle must not be stepped by two streams
  * at once (variant 4 keeps its chunk counter in the handle's workspace). */

@@ -535,8 +535,9 @@ int lbm_set_step_variant(lbm_handle* h, int variant) {
   if (variant < 0 || variant > 4) return fail(h, LBM_EINVAL, "variant must be 0, 1, 2, 3 or 4");
   if (variant == 2 && !step_tma_allowed(h->cfg.storage, h->cfg.nx))
     return fail(h, LBM_ENOTSUP, "TMA-staged step needs nx %% 16 == 0 and nx >= 272");
-  if ((variant == 3 || variant == 4) && !step_tma2_allowed(h->cfg.storage, h->cfg.nx))
-    return fail(h, LBM_ENOTSUP, "two-cell staged step needs nx %% 16 == 0");
+  if ((variant == 3 || variant == 4) && !step_tma2_allowed(h->cfg.storage, h->cfg.nx) &&
+      !step_tma2_unaligned_allowed(h->cfg.nx))
+    return fail(h, LBM_ENOTSUP, "two-cell staged step needs nx >= 16");
   h->variant = variant;
   return LBM_OK;
 }

@@ -42,6 +42,7 @@ struct lbm_batch {
   int* d_counter = nullptr;
   int max_items = 0;
   int nitems = 0;
+  int nitems_a = 0;            // items of boxes with 16-byte rows come first; then the others
   std::vector<BatchItem> items;
   // barrier pipeline: tiled boxes relabel together, one launch per phase for
   // all boxes due at the same step; boxes are grouped by the residue of their
@@ -55,9 +56,11 @@ struct lbm_batch {
   };
   std::map<int, Group> groups;            // by residue of the step count
   std::vector<int> untiled;               // boxes relabelled one by one
-  std::vector<char> lone;                 // boxes the staged kernel cannot take (rows
-                                          // not 16-byte multiples): stepped by the
-                                          // plain-load kernel in the same sequence
+  std::vector<char> lone;                 // boxes narrower than the staged kernel takes
+                                          // (< 16 columns): stepped by the plain-load
+                                          // kernel in the same sequence
+  std::vector<char> unal;                 // rows not 16-byte multiples: the staged
+                                          // kernel's variant for them (own launch)
   // bounce-back after each step: tiled boxes together (entries d_bent, in
   // stepping order), untiled boxes one by one
   RelabelEntry* d_bent = nullptr;
@@ -163,7 +166,11 @@ void build_items(lbm_batch* b, bool spread) {
   std::stable_sort(b->items.begin(), b->items.end(), [](const BatchItem& a, const BatchItem& c) {
     return (long long)a.width * (a.y1 - a.y0) > (long long)c.width * (c.y1 - c.y0);
   });
+  // boxes with 16-byte rows first (one launch), then the others (another)
+  std::stable_partition(b->items.begin(), b->items.end(), [&](const BatchItem& it) { return !b->unal[it.inst]; });
   b->nitems = (int)b->items.size();
+  b->nitems_a = 0;
+  for (const BatchItem& it : b->items) b->nitems_a += !b->unal[it.inst];
 }
 
 // Re-uploads descriptors and items (host-synchronous copies). Boxes may be
@@ -203,7 +210,7 @@ int upload(lbm_batch* b, const std::vector<int>& order = {}) {
   if (b->nitems)
     BCUDA(b, cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(BatchItem) * b->nitems, cudaMemcpyHostToDevice,
                              b->stream));
-  BCUDA(b, cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), b->stream));  // item counters (step parity)
+  BCUDA(b, cudaMemsetAsync(b->d_counter, 0, 4 * sizeof(int), b->stream));  // item counters (kind, step parity)
   b->groups.clear();
   b->untiled.clear();
   b->bounce_first.assign(1, 0);
@@ -298,6 +305,22 @@ int enqueue_relabel(lbm_batch* b, int parity, int64_t j, int live, Stepping step
   return LBM_OK;
 }
 
+// The batched kernels of one step: the items of boxes with 16-byte rows
+// (counters 0, 1) and those of the other boxes (counters 2, 3).
+int enqueue_items(lbm_batch* b, int parity, const BatchItem* items_a, int na, const BatchItem* items_u, int nu) {
+  if (na > 0) {
+    BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, false, b->d_insts, items_a, na,
+                               b->d_counter, parity, b->stream));
+    b->launches += 1;
+  }
+  if (nu > 0) {
+    BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, true, b->d_insts, items_u, nu,
+                               b->d_counter + 2, parity, b->stream));
+    b->launches += 1;
+  }
+  return LBM_OK;
+}
+
 // The boxes outside the item list (lone) that step now: one plain-load step
 // each, on the buffers of parity `parity`, on the batch stream.
 template <class Stepping>
@@ -353,11 +376,9 @@ int enqueue_step(lbm_batch* b, int parity, int64_t j) {
   int rc;
   if (b->masked && (rc = enqueue_relabel(b, parity, j, -1, [&](int i) { return b->active[i] != 0; })))
     return rc;
-  if (b->nitems) {
-    BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items, b->nitems,
-                               b->d_counter, parity, b->stream));
-    b->launches += 1;
-  }
+  if ((rc = enqueue_items(b, parity, b->d_items, b->nitems_a, b->d_items + b->nitems_a,
+                          b->nitems - b->nitems_a)))
+    return rc;
   if ((rc = enqueue_lone(b, parity, [&](int i) { return b->active[i] != 0; }))) return rc;
   if (b->masked && (rc = enqueue_bounce(b, parity, -1, [&](int i) { return b->active[i] != 0; }))) return rc;
   return LBM_OK;
@@ -441,7 +462,12 @@ int lbm_batch_create(lbm_handle* const* handles, int32_t n, void* d_workspace, s
   b->active.assign(n, 1);
   b->base_cur.assign(n, 0);
   b->lone.assign(n, 0);
-  for (int i = 0; i < n; ++i) b->lone[i] = !step_tma2_allowed(handles[i]->cfg.storage, handles[i]->cfg.nx);
+  b->unal.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const int nx = handles[i]->cfg.nx;
+    b->unal[i] = !step_tma2_allowed(handles[i]->cfg.storage, nx) && step_tma2_unaligned_allowed(nx);
+    b->lone[i] = !step_tma2_allowed(handles[i]->cfg.storage, nx) && !b->unal[i];
+  }
   b->storage = h0->cfg.storage;
   b->masked = h0->cfg.barrier;
   // graph block: one relabel period with the barrier, else 16 steps
@@ -580,15 +606,24 @@ int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n) {
   rc = upload(b, order);
   b->active = keep;
   if (rc) return rc;
-  std::vector<BatchItem> sorted;
-  std::vector<int> prefix(order.size() + 1, 0);  // items of the first k boxes
-  for (size_t k = 0; k < order.size(); ++k) {
-    for (const BatchItem& it : b->items)
-      if (it.inst == order[k]) sorted.push_back(it);
-    prefix[k + 1] = (int)sorted.size();
+  // items of each kind (16-byte rows or not) in stepping order; the boxes
+  // still stepping at step j own a prefix of each
+  std::vector<BatchItem> sorted[2];
+  std::vector<int> prefix[2];
+  for (int kind = 0; kind < 2; ++kind) {
+    prefix[kind].assign(order.size() + 1, 0);
+    for (size_t k = 0; k < order.size(); ++k) {
+      if ((b->unal[order[k]] != 0) == (kind == 1))
+        for (const BatchItem& it : b->items)
+          if (it.inst == order[k]) sorted[kind].push_back(it);
+      prefix[kind][k + 1] = (int)sorted[kind].size();
+    }
   }
-  BCUDA(b, cudaMemcpyAsync(b->d_items, sorted.data(), sizeof(BatchItem) * sorted.size(), cudaMemcpyHostToDevice,
-                           b->stream));
+  const size_t na_all = sorted[0].size();
+  sorted[0].insert(sorted[0].end(), sorted[1].begin(), sorted[1].end());
+  if (!sorted[0].empty())
+    BCUDA(b, cudaMemcpyAsync(b->d_items, sorted[0].data(), sizeof(BatchItem) * sorted[0].size(),
+                             cudaMemcpyHostToDevice, b->stream));
   std::map<int, int> glive;  // members of each barrier group still stepping
   for (const auto& kv : b->groups) glive[kv.first] = (int)kv.second.members.size();
   size_t live = order.size();
@@ -607,11 +642,8 @@ int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n) {
       }
       if ((rc = enqueue_relabel(b, parity, j, gl, [&](int i) { return nsteps[i] > j; }))) return rc;
     }
-    if (prefix[live]) {
-      BCUDA(b, launch_step_batch(b->storage, b->masked != 0, b->tau_one != 0, b->d_insts, b->d_items,
-                                 prefix[live], b->d_counter, parity, b->stream));
-      b->launches += 1;
-    }
+    if ((rc = enqueue_items(b, parity, b->d_items, prefix[0][live], b->d_items + na_all, prefix[1][live])))
+      return rc;
     if ((rc = enqueue_lone(b, parity, [&](int i) { return nsteps[i] > j; }))) return rc;
     if (b->masked && (rc = enqueue_bounce(b, parity, (int)live, [&](int i) { return nsteps[i] > j; }))) return rc;
   }

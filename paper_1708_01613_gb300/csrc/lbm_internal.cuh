@@ -188,12 +188,17 @@ bool step_tma_allowed(int storage, int nx);
 // many boxes); one persistent grid drawing items from counters[parity] and
 // zeroing counters[parity ^ 1]. Both counters must be zero before the
 // first launch and consecutive launches must alternate parity.
-cudaError_t launch_step_batch(int storage, bool masked, bool tau_one, const BatchInst* insts, const BatchItem* items,
-                              int nitems, int* counters, int parity, cudaStream_t s);
+// unal: the items' boxes have rows that do not start on 16-byte boundaries
+// (the staging variant that bulk-copies aligned interiors and plain-loads
+// the rest); one launch takes items of one kind.
+cudaError_t launch_step_batch(int storage, bool masked, bool tau_one, bool unal, const BatchInst* insts,
+                              const BatchItem* items, int nitems, int* counters, int parity, cudaStream_t s);
 // CTAs of the batched kernel that fit the GPU at once.
 int batch_resident_ctas(int storage, bool masked, bool tau_one);
-// Whether the two-cell staged step kernel can run on a box of width nx.
+// Whether the two-cell staged step kernel can run on a box of width nx with
+// whole rows bulk-copied (nx % 16 == 0), or in its variant for other widths.
 bool step_tma2_allowed(int storage, int nx);
+bool step_tma2_unaligned_allowed(int nx);
 
 // Barrier / field / reduction kernels (barrier.cu).
 struct Workspace {

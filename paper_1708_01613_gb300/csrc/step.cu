@@ -502,48 +502,131 @@ __device__ __forceinline__ void copy_row_wrapped3(T* dst, const T* row, int star
   }
 }
 
+// Rows that do not start on 16-byte boundaries (nx % 16 != 0, variant UNAL
+// of the two-cell march): a staged row keeps window element e at slot
+// position e + off, where off = (global index of window element 0) mod M
+// (M = elements per 16 bytes), so the row's 16-byte-aligned interior can be
+// bulk-copied to an aligned slot position; its head and tail (fewer than M
+// elements each) and any halo that wraps around the periodic row are loaded
+// by the helper lanes with plain loads. A row slot holds M more elements.
+template <typename T>
+struct URow {
+  int off;  // slot position of window element 0
+  int hA;   // window elements [0, hA) and [hB, len) come by plain loads,
+  int hB;   // [hA, hB) by one bulk copy
+};
+
+template <typename T>
+__device__ __forceinline__ URow<T> urow(long long gbase, int c0, int len, int nx) {
+  constexpr int M = 16 / (int)sizeof(T);
+  URow<T> u;
+  u.off = (int)((gbase + c0 + M) & (M - 1));  // gbase + c0 >= -M
+  const int a = c0 > 0 ? c0 : 0, b = c0 + len < nx ? c0 + len : nx;  // columns inside the row
+  long long iA = (gbase + a + M - 1) / M * M, iB = (gbase + b) / M * M;
+  if (iA >= iB) iA = iB = gbase + b;  // no aligned interior: all plain
+  u.hA = (int)(iA - gbase) - c0;
+  u.hB = (int)(iB - gbase) - c0;
+  return u;
+}
+
+// Plain loads of the elements kk = j, j + step, ... of a row's plain part.
+template <typename T>
+__device__ __forceinline__ void urow_plain(T* dst, const T* row, const URow<T>& u, int c0, int len, int nx, int j,
+                                           int step) {
+  const int np = u.hA + (len - u.hB);
+  for (int kk = j; kk < np; kk += step) {
+    const int e = kk < u.hA ? kk : u.hB + (kk - u.hA);
+    int c = (c0 + e) % nx;
+    c = c < 0 ? c + nx : c;
+    dst[e + u.off] = row[c];
+  }
+}
+
 // One stage of the two-cell march: for output row r = y0 - 1 + k, plane i's
 // source row r - c_iy, columns x0 - PAD .. x0 + width + PAD (wrapped), and the
 // mask row r, columns x0 .. x0 + width. Slots have a fixed stride.
-template <int S, bool MASKED, int NSTAGE>
+template <int S, bool MASKED, int NSTAGE, bool UNAL = false>
 __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename Store<S>::T* src,
                                              unsigned char* stages, uint64_t* bars, unsigned gk, int k, int y0,
                                              int x0, int width, int lane) {
   using G = TmaGeom2<S>;
   using T = typename G::T;
-  constexpr uint32_t SLOT_BYTES = Q * G::ROW_BYTES + (MASKED ? kBX2 : 0);
+  constexpr int RB = G::ROW_BYTES + (UNAL ? 16 : 0);  // plane row stride in a slot
+  constexpr uint32_t SLOT_BYTES = Q * RB + (MASKED ? kBX2 + (UNAL ? 16 : 0) : 0);
   const int len = width + 2 * G::PAD;
-  const uint32_t bytes = (uint32_t)(Q * len * G::E + (MASKED ? width : 0));
   const int slot = (int)(gk % NSTAGE);
   unsigned char* st = stages + (size_t)slot * SLOT_BYTES;
   uint64_t* bar = bars + slot;
   const int r = y0 - 1 + k;
   const int ny = p.ny, nx = p.nx;
-  if (lane < Q + (MASKED ? 1 : 0)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(bar, bytes);
-  __syncwarp();
-  if (lane < Q) {
-    const int i = lane;
-    const int ciy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+  if (UNAL || lane < Q + (MASKED ? 1 : 0)) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (!UNAL) {
+    const uint32_t bytes = (uint32_t)(Q * len * G::E + (MASKED ? width : 0));
+    if (lane == 0) mbar_expect_tx(bar, bytes);
+    __syncwarp();
+    if (lane < Q) {
+      const int i = lane;
+      const int ciy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+      int g = r - ciy;
+      g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
+      g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
+      const T* row = src + (size_t)i * p.N + (size_t)g * nx;
+      copy_row_wrapped3<T>(reinterpret_cast<T*>(st + i * RB), row, x0 - G::PAD, len, nx, bar);
+    } else if (MASKED && lane == Q) {
+      const int g = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+      copy_row_wrapped3<uint8_t>(st + Q * RB, p.mask + (size_t)g * nx, x0, width, nx, bar);
+    }
+    return;
+  }
+  // UNAL: row q (planes 0..8, then the mask) is served by lanes 3q .. 3q + 2
+  const int q = lane / 3, j = lane - 3 * q;
+  uint32_t bytes = 0;
+  const void* bsrc = nullptr;
+  void* bdst = nullptr;
+  if (q < Q) {
+    const int ciy = (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
     int g = r - ciy;
     g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
     g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
-    const T* row = src + (size_t)i * p.N + (size_t)g * nx;
-    copy_row_wrapped3<T>(reinterpret_cast<T*>(st + i * G::ROW_BYTES), row, x0 - G::PAD, len, nx, bar);
-  } else if (MASKED && lane == Q) {
+    const T* row = src + (size_t)q * p.N + (size_t)g * nx;
+    T* dst = reinterpret_cast<T*>(st + q * RB);
+    const int c0 = x0 - G::PAD;
+    const URow<T> u = urow<T>((long long)g * nx, c0, len, nx);
+    urow_plain<T>(dst, row, u, c0, len, nx, j, 3);
+    if (j == 0 && u.hB > u.hA) {
+      bytes = (uint32_t)((u.hB - u.hA) * G::E);
+      bsrc = row + (c0 + u.hA);
+      bdst = dst + u.hA + u.off;
+    }
+  } else if (MASKED && q == Q) {
     const int g = r < 0 ? r + ny : (r >= ny ? r - ny : r);
-    copy_row_wrapped3<uint8_t>(st + Q * G::ROW_BYTES, p.mask + (size_t)g * nx, x0, width, nx, bar);
+    const uint8_t* row = p.mask + (size_t)g * nx;
+    uint8_t* dst = st + Q * RB;
+    const URow<uint8_t> u = urow<uint8_t>((long long)g * nx, x0, width, nx);
+    urow_plain<uint8_t>(dst, row, u, x0, width, nx, j, 3);
+    if (j == 0 && u.hB > u.hA) {
+      bytes = (uint32_t)(u.hB - u.hA);
+      bsrc = row + (x0 + u.hA);
+      bdst = dst + u.hA + u.off;
+    }
   }
+  const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+  __syncwarp();  // the plain stores above are ordered before the arrive (release)
+  if (lane == 0) mbar_expect_tx(bar, total);
+  __syncwarp();
+  if (bytes) bulk_g2s(bdst, bsrc, bytes, bar);
 }
 
-template <int S, bool MASKED, int NSTAGE>
+template <int S, bool MASKED, int NSTAGE, bool UNAL = false>
 constexpr size_t tma2_smem_bytes_c() {
-  return (size_t)NSTAGE * (Q * TmaGeom2<S>::ROW_BYTES + (MASKED ? kBX2 : 0)) + 4 * (kBX2 + 4) * 4 + NSTAGE * 8 + 16;
+  return (size_t)NSTAGE * (Q * (TmaGeom2<S>::ROW_BYTES + (UNAL ? 16 : 0)) + (MASKED ? kBX2 + (UNAL ? 16 : 0) : 0)) +
+         4 * (kBX2 + 4) * 4 + NSTAGE * 8 + 16;
 }
 
-template <int S, bool MASKED, int NSTAGE>
+template <int S, bool MASKED, int NSTAGE, bool UNAL = false>
 struct Tma2Smem {
-  static constexpr int SLOT_BYTES = Q * TmaGeom2<S>::ROW_BYTES + (MASKED ? kBX2 : 0);
+  static constexpr int RB = TmaGeom2<S>::ROW_BYTES + (UNAL ? 16 : 0);  // plane row stride
+  static constexpr int SLOT_BYTES = Q * RB + (MASKED ? kBX2 + (UNAL ? 16 : 0) : 0);
   static constexpr int RW = kBX2 + 4;  // ring row: cell column c at index c + 2, halos at 1 and width + 2
   unsigned char* stages;
   float (*ring)[RW];
@@ -558,16 +641,19 @@ struct Tma2Smem {
 };
 
 // The two-cell march of one work item: columns x0 .. x0 + width (a multiple of
-// 16, at most kBX2) and rows y0 .. y1 of one box. `gstage` counts the stages
-// this CTA consumed before (mbarrier phases continue across items). Returns
-// false if a stage wait timed out (the CTA must then leave).
-template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, bool FULL = false>
-__device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MASKED, NSTAGE>& sm, int x0, int width_,
-                                       int y0, int y1, unsigned& gstage, int& bad) {
+// 16, at most kBX2; with UNAL any width, and rows that need not start on
+// 16-byte boundaries) and rows y0 .. y1 of one box. `gstage` counts the
+// stages this CTA consumed before (mbarrier phases continue across items).
+// Returns false if a stage wait timed out (the CTA must then leave).
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, bool FULL = false, bool UNAL = false>
+__device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MASKED, NSTAGE, UNAL>& sm, int x0,
+                                       int width_, int y0, int y1, unsigned& gstage, int& bad) {
   const int width = FULL ? kBX2 : width_;  // FULL: a whole strip (known at compile time)
   using G = TmaGeom2<S>;
   using T = typename G::T;
-  constexpr int SLOT_BYTES = Tma2Smem<S, MASKED, NSTAGE>::SLOT_BYTES;
+  constexpr int SLOT_BYTES = Tma2Smem<S, MASKED, NSTAGE, UNAL>::SLOT_BYTES;
+  constexpr int RB = Tma2Smem<S, MASKED, NSTAGE, UNAL>::RB;
+  constexpr int M = 16 / G::E;  // elements per 16 bytes
   const T* __restrict__ src = static_cast<const T*>(p.src);
   T* __restrict__ dst = static_cast<T*>(p.dst);
   const int nx = p.nx;
@@ -580,11 +666,12 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
 
   if (helper)
     for (int k = 0; k < NSTAGE - 1 && k < nst; ++k)
-      issue_stage2<S, MASKED, NSTAGE>(p, src, sm.stages, sm.bars, g0 + k, k, y0, x0, width, lane);
+      issue_stage2<S, MASKED, NSTAGE, UNAL>(p, src, sm.stages, sm.bars, g0 + k, k, y0, x0, width, lane);
 
   const int hplane = lane & 15;
   const bool hlane = helper && hplane < Q;
   const int hcx = (hplane == 1 || hplane == 5 || hplane == 8) ? 1 : ((hplane == 3 || hplane == 6 || hplane == 7) ? -1 : 0);
+  const int hcy = (hplane == 2 || hplane == 5 || hplane == 6) ? 1 : ((hplane == 4 || hplane == 7 || hplane == 8) ? -1 : 0);
   const int hpos = (lane < 16 ? G::PAD - 1 : G::PAD + width) - hcx;
 
   const int jc = 2 * tid + 2;        // ring index of the first cell of the pair
@@ -600,14 +687,41 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
     float2 f[Q];
     float2 rho = make_float2(1.f, 1.f), jx = make_float2(0.f, 0.f), jy = make_float2(0.f, 0.f);
     unsigned m = 0;
+    // UNAL: slot offsets of the three source rows (r - 1, r, r + 1) and of the mask row
+    int offm = 0, off0 = 0, offp = 0, offk = 0;
+    if (UNAL) {
+      const int r = y0 - 1 + k, ny = p.ny;
+      const int g0r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+      const int gm = g0r == 0 ? ny - 1 : g0r - 1, gp = g0r == ny - 1 ? 0 : g0r + 1;
+      offm = (int)(((long long)gm * nx + x0 - G::PAD + M) & (M - 1));
+      off0 = (int)(((long long)g0r * nx + x0 - G::PAD + M) & (M - 1));
+      offp = (int)(((long long)gp * nx + x0 - G::PAD + M) & (M - 1));
+      offk = (int)(((long long)g0r * nx + x0) & 15);
+    }
     if (active) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = load_pair<S>(st + i * G::ROW_BYTES, pos - cx(i), cx(i));
+      for (int i = 0; i < Q; ++i) {
+        if (UNAL) {
+          const int q = pos - cx(i) + (cy(i) > 0 ? offm : (cy(i) < 0 ? offp : off0));
+          f[i] = load_pair<S>(st + i * RB, q, q & 1);
+        } else {
+          f[i] = load_pair<S>(st + i * RB, pos - cx(i), cx(i));
+        }
+      }
       moments9(f, rho, jx, jy);
       *reinterpret_cast<float2*>(&sm.ring[k & 3][jc]) = psi_of(full_rho<S != LBM_F32>(rho, p), p);
-      if (MASKED) m = *reinterpret_cast<const uint16_t*>(st + Q * G::ROW_BYTES + 2 * tid);
+      if (MASKED) {
+        if (UNAL) {
+          const unsigned char* mr = st + Q * RB + offk + 2 * tid;
+          m = (unsigned)mr[0] | ((unsigned)mr[1] << 8);
+        } else {
+          m = *reinterpret_cast<const uint16_t*>(st + Q * RB + 2 * tid);
+        }
+      }
     } else if (helper) {
-      const float v = hlane ? Store<S>::raw_smem(reinterpret_cast<const T*>(st + hplane * G::ROW_BYTES), hpos) : 0.f;
+      const int ho = UNAL ? (hcy > 0 ? offm : (hcy < 0 ? offp : off0)) : 0;
+      const float v =
+          hlane ? Store<S>::raw_smem(reinterpret_cast<const T*>(st + hplane * RB), hpos + ho) : 0.f;
       const float t1 = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, 1));
       const float t2 = __fadd_rn(t1, __shfl_xor_sync(0xffffffffu, t1, 2));
       const float t3 = __fadd_rn(t2, __shfl_xor_sync(0xffffffffu, t2, 4));
@@ -622,7 +736,8 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
     }
     if (helper) {
       if (k + NSTAGE - 1 < nst)
-        issue_stage2<S, MASKED, NSTAGE>(p, src, sm.stages, sm.bars, gk + NSTAGE - 1, k + NSTAGE - 1, y0, x0, width, lane);
+        issue_stage2<S, MASKED, NSTAGE, UNAL>(p, src, sm.stages, sm.bars, gk + NSTAGE - 1, k + NSTAGE - 1, y0, x0,
+                                              width, lane);
     } else if (k >= 2 && active) {
       const int rc = y0 + k - 2;
       const int srow[3] = {(k - 2) & 3, (k - 1) & 3, k & 3};  // rows rc-1, rc, rc+1
@@ -651,8 +766,20 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
       force_of(sv, psi_c, p.G, Fx, Fy);
       collide<TAU_ONE, S != LBM_F32>(fprev, rho_prev, jx_prev, jy_prev, Fx, Fy, p, bad);
       const size_t base = (size_t)rc * nx + x0 + 2 * tid;
+      if (UNAL && ((base & 1) || 2 * tid + 1 == width)) {
+        // a pair at an odd index cannot take one vector store; with an odd
+        // width the last pair's second cell is the right halo cell (computed
+        // for its psi only) and is not stored
+        const bool second = 2 * tid + 1 < width;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) store_pair<S>(dst, (size_t)i * p.N + base, fprev[i]);
+        for (int i = 0; i < Q; ++i) {
+          Store<S>::store_raw(dst, (size_t)i * p.N + base, fprev[i].x);
+          if (second) Store<S>::store_raw(dst, (size_t)i * p.N + base + 1, fprev[i].y);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) store_pair<S>(dst, (size_t)i * p.N + base, fprev[i]);
+      }
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) fprev[i] = f[i];
@@ -677,8 +804,8 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
   return true;
 }
 
-template <int S, bool MASKED, int NSTAGE>
-__device__ __forceinline__ void march2_init(const Tma2Smem<S, MASKED, NSTAGE>& sm) {
+template <int S, bool MASKED, int NSTAGE, bool UNAL>
+__device__ __forceinline__ void march2_init(const Tma2Smem<S, MASKED, NSTAGE, UNAL>& sm) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) mbar_init(sm.bars + s, 1);
     *sm.abort_flag = 0;
@@ -688,10 +815,10 @@ __device__ __forceinline__ void march2_init(const Tma2Smem<S, MASKED, NSTAGE>& s
 }
 
 // One box, one work item per CTA: strip blockIdx.x (kBX2 columns), row chunk blockIdx.y.
-template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB, bool UNAL>
 __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const Tma2Smem<S, MASKED, NSTAGE> sm(smem);
+  const Tma2Smem<S, MASKED, NSTAGE, UNAL> sm(smem);
   const int x0 = blockIdx.x * kBX2;
   const int y0 = blockIdx.y * p.rows_per_chunk;
   const int y1 = min(y0 + p.rows_per_chunk, p.ny);
@@ -700,8 +827,9 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
   unsigned gstage = 0;
   int bad = 0;
   const int width = min(kBX2, p.nx - x0);
-  const bool ok = width == kBX2 ? march2<S, MASKED, TAU_ONE, NSTAGE, true>(p, sm, x0, width, y0, y1, gstage, bad)
-                                : march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, x0, width, y0, y1, gstage, bad);
+  const bool ok = width == kBX2
+                      ? march2<S, MASKED, TAU_ONE, NSTAGE, true, UNAL>(p, sm, x0, width, y0, y1, gstage, bad)
+                      : march2<S, MASKED, TAU_ONE, NSTAGE, false, UNAL>(p, sm, x0, width, y0, y1, gstage, bad);
   if (!ok) return;
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
 }
@@ -713,11 +841,11 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_tma2(const StepParam
 // one-chunk-per-CTA (8192^2: FP32 0.817 -> 0.757 ms, FP16 0.509 -> 0.481
 // ms). The counters are zero between launches: the last CTA to finish
 // resets them.
-template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB, bool UNAL>
 __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_dyn(const StepParams p, int rows, int gx, int nitems) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int item_sh;
-  const Tma2Smem<S, MASKED, NSTAGE> sm(smem);
+  const Tma2Smem<S, MASKED, NSTAGE, UNAL> sm(smem);
   march2_init(sm);
   int* counter = p.flags + FLAG_ITEM;
   unsigned gstage = 0;
@@ -747,8 +875,8 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_dyn(const StepParams
     // full strips take the compile-time-width march (with tau != 1 the two
     // inlined copies would spill at this kernel's register budget)
     const bool ok = TAU_ONE && width == kBX2
-                        ? march2<S, MASKED, TAU_ONE, NSTAGE, TAU_ONE>(p, sm, x0, width, y0, y1, gstage, bad)
-                        : march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, x0, width, y0, y1, gstage, bad);
+                        ? march2<S, MASKED, TAU_ONE, NSTAGE, TAU_ONE, UNAL>(p, sm, x0, width, y0, y1, gstage, bad)
+                        : march2<S, MASKED, TAU_ONE, NSTAGE, false, UNAL>(p, sm, x0, width, y0, y1, gstage, bad);
     if (!ok) break;  // a stage wait timed out (recorded); no further chunks
   }
   if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
@@ -768,13 +896,13 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_dyn(const StepParams
 // parity, so two counters take turns: this launch draws from
 // counters[parity] and zeroes counters[parity ^ 1] for the next one (which
 // starts only after this one has finished), so no reset is launched.
-template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB>
+template <int S, bool MASKED, bool TAU_ONE, int NSTAGE, int MINB, bool UNAL>
 __global__ void __launch_bounds__(kTmaThreads, MINB)
     k_step_batch(const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
                  int* __restrict__ counters, int parity) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int item_sh;
-  const Tma2Smem<S, MASKED, NSTAGE> sm(smem);
+  const Tma2Smem<S, MASKED, NSTAGE, UNAL> sm(smem);
   march2_init(sm);
   int* counter = counters + parity;
   if (blockIdx.x == 0 && threadIdx.x == 0) counters[parity ^ 1] = 0;
@@ -806,8 +934,10 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
     // full strips take the compile-time-width march (with tau != 1 the two
     // inlined copies would spill at this kernel's register budget)
     const bool ok = TAU_ONE && it.width == kBX2
-                        ? march2<S, MASKED, TAU_ONE, NSTAGE, TAU_ONE>(p, sm, it.x0, it.width, it.y0, it.y1, gstage, bad)
-                        : march2<S, MASKED, TAU_ONE, NSTAGE>(p, sm, it.x0, it.width, it.y0, it.y1, gstage, bad);
+                        ? march2<S, MASKED, TAU_ONE, NSTAGE, TAU_ONE, UNAL>(p, sm, it.x0, it.width, it.y0, it.y1,
+                                                                             gstage, bad)
+                        : march2<S, MASKED, TAU_ONE, NSTAGE, false, UNAL>(p, sm, it.x0, it.width, it.y0, it.y1,
+                                                                         gstage, bad);
     if (!ok) return;
     if (bad) atomicOr(p.flags + FLAG_NUMERIC, 1);
   }
@@ -867,17 +997,21 @@ constexpr int tma2_stages() { return S == LBM_F32 ? 3 : 4; }
 constexpr int kTma2MinBlocks = 4;
 constexpr int kDynRows = 48;  // row chunk of the dynamically scheduled step
 
+// Rows whose starts are 16-byte aligned for every storage (and mask rows):
+// whole rows are bulk-copied. Other boxes of at least 16 columns take the
+// UNAL variant (aligned interiors bulk-copied, heads and tails plain-loaded).
 template <int S>
 bool tma2_ok(int nx) {
   return nx % 16 == 0;
 }
+inline bool tma2_unal_ok(int nx) { return nx >= 16 && nx % 16 != 0; }
 
-template <int S, bool MASKED, bool TAU_ONE>
+template <int S, bool MASKED, bool TAU_ONE, bool UNAL = false>
 cudaError_t launch_tma2(const StepParams& p, cudaStream_t s) {
   constexpr int NS = tma2_stages<S>();
   // the relaxation blend (tau != 1) keeps both population sets live: fewer CTAs
-  auto kern = k_step_tma2<S, MASKED, TAU_ONE, NS, TAU_ONE ? kTma2MinBlocks : 2>;
-  constexpr size_t smem = tma2_smem_bytes_c<S, MASKED, NS>();
+  auto kern = k_step_tma2<S, MASKED, TAU_ONE, NS, TAU_ONE ? kTma2MinBlocks : 2, UNAL>;
+  constexpr size_t smem = tma2_smem_bytes_c<S, MASKED, NS, UNAL>();
   static int resident = 0;  // per instantiation
   if (resident == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -898,11 +1032,11 @@ cudaError_t launch_tma2(const StepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int S, bool MASKED, bool TAU_ONE>
+template <int S, bool MASKED, bool TAU_ONE, bool UNAL = false>
 cudaError_t launch_dyn(const StepParams& p, cudaStream_t s) {
   constexpr int NS = tma2_stages<S>();
-  auto kern = k_step_dyn<S, MASKED, TAU_ONE, NS, TAU_ONE ? kTma2MinBlocks : 2>;
-  constexpr size_t smem = tma2_smem_bytes_c<S, MASKED, NS>();
+  auto kern = k_step_dyn<S, MASKED, TAU_ONE, NS, TAU_ONE ? kTma2MinBlocks : 2, UNAL>;
+  constexpr size_t smem = tma2_smem_bytes_c<S, MASKED, NS, UNAL>();
   static int resident = 0;  // per instantiation: CTAs that fit the GPU at once
   if (resident == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -926,7 +1060,7 @@ cudaError_t launch_dyn(const StepParams& p, cudaStream_t s) {
   // automatic choice: with no more chunks than resident CTAs there is nothing
   // to balance, and the static split saves the counter's round trips (a
   // few microseconds, a large part of a small box's step)
-  if (p.force_generic == 0 && nitems <= resident) return launch_tma2<S, MASKED, TAU_ONE>(p, s);
+  if (p.force_generic == 0 && nitems <= resident) return launch_tma2<S, MASKED, TAU_ONE, UNAL>(p, s);
   const int grid = nitems < resident ? nitems : resident;
   kern<<<grid, kTmaThreads, smem, s>>>(p, rows, gx, nitems);
   return cudaGetLastError();
@@ -952,8 +1086,10 @@ template <int S, bool MASKED, bool TAU_ONE>
 cudaError_t launch_variant(const StepParams& p, cudaStream_t s) {
   const int v = p.force_generic;
   if ((v == 4 || v == 0) && tma2_ok<S>(p.nx)) return launch_dyn<S, MASKED, TAU_ONE>(p, s);
+  if ((v == 4 || v == 0) && tma2_unal_ok(p.nx)) return launch_dyn<S, MASKED, TAU_ONE, true>(p, s);
   if (v == 3) {
     if (tma2_ok<S>(p.nx)) return launch_tma2<S, MASKED, TAU_ONE>(p, s);
+    if (tma2_unal_ok(p.nx)) return launch_tma2<S, MASKED, TAU_ONE, true>(p, s);
   }
   if (v != 1 && tma_ok<S>(p.nx)) return launch_tma<S, MASKED, TAU_ONE>(p, s);
   return launch_strip<S, MASKED, TAU_ONE>(p, s);
@@ -997,15 +1133,15 @@ void step_geometry(int nx, int ny, int* grid_x, int* grid_y, int* rows_per_chunk
 // ---------------------------------------------------------------- batched launch
 namespace {
 
-template <int S, bool MASKED, bool TAU_ONE>
+template <int S, bool MASKED, bool TAU_ONE, bool UNAL>
 struct BatchKernel {
   static constexpr int NS = tma2_stages<S>();
   static constexpr int MINB = TAU_ONE ? kTma2MinBlocks : 2;
-  static constexpr size_t SMEM = tma2_smem_bytes_c<S, MASKED, NS>();
+  static constexpr size_t SMEM = tma2_smem_bytes_c<S, MASKED, NS, UNAL>();
   static int resident() {  // CTAs that fit the GPU at once
     static int r = 0;
     if (r == 0) {
-      auto kern = k_step_batch<S, MASKED, TAU_ONE, NS, MINB>;
+      auto kern = k_step_batch<S, MASKED, TAU_ONE, NS, MINB, UNAL>;
       if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM) != cudaSuccess) return 0;
       int occ = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTmaThreads, SMEM) != cudaSuccess) return 0;
@@ -1019,35 +1155,46 @@ struct BatchKernel {
     if (res == 0) return cudaErrorInvalidConfiguration;
     const int grid = nitems < res ? nitems : res;
     if (grid <= 0) return cudaMemsetAsync(counters, 0, 2 * sizeof(int), s);  // no launch resets them
-    k_step_batch<S, MASKED, TAU_ONE, NS, MINB><<<grid, kTmaThreads, SMEM, s>>>(insts, items, nitems, counters, parity);
+    k_step_batch<S, MASKED, TAU_ONE, NS, MINB, UNAL>
+        <<<grid, kTmaThreads, SMEM, s>>>(insts, items, nitems, counters, parity);
     return cudaGetLastError();
   }
 };
 
-template <int S>
-cudaError_t launch_batch_s(bool masked, bool tau_one, const BatchInst* insts, const BatchItem* items, int nitems,
-                           int* counter, int parity, cudaStream_t s) {
+template <int S, bool UNAL>
+cudaError_t launch_batch_su(bool masked, bool tau_one, const BatchInst* insts, const BatchItem* items, int nitems,
+                            int* counter, int parity, cudaStream_t s) {
   if (masked)
-    return tau_one ? BatchKernel<S, true, true>::launch(insts, items, nitems, counter, parity, s)
-                   : BatchKernel<S, true, false>::launch(insts, items, nitems, counter, parity, s);
-  return tau_one ? BatchKernel<S, false, true>::launch(insts, items, nitems, counter, parity, s)
-                 : BatchKernel<S, false, false>::launch(insts, items, nitems, counter, parity, s);
+    return tau_one ? BatchKernel<S, true, true, UNAL>::launch(insts, items, nitems, counter, parity, s)
+                   : BatchKernel<S, true, false, UNAL>::launch(insts, items, nitems, counter, parity, s);
+  return tau_one ? BatchKernel<S, false, true, UNAL>::launch(insts, items, nitems, counter, parity, s)
+                 : BatchKernel<S, false, false, UNAL>::launch(insts, items, nitems, counter, parity, s);
+}
+
+template <int S>
+cudaError_t launch_batch_s(bool masked, bool tau_one, bool unal, const BatchInst* insts, const BatchItem* items,
+                           int nitems, int* counter, int parity, cudaStream_t s) {
+  return unal ? launch_batch_su<S, true>(masked, tau_one, insts, items, nitems, counter, parity, s)
+              : launch_batch_su<S, false>(masked, tau_one, insts, items, nitems, counter, parity, s);
 }
 
 template <int S>
 int batch_resident_s(bool masked, bool tau_one) {
-  if (masked) return tau_one ? BatchKernel<S, true, true>::resident() : BatchKernel<S, true, false>::resident();
-  return tau_one ? BatchKernel<S, false, true>::resident() : BatchKernel<S, false, false>::resident();
+  if (masked)
+    return tau_one ? BatchKernel<S, true, true, false>::resident() : BatchKernel<S, true, false, false>::resident();
+  return tau_one ? BatchKernel<S, false, true, false>::resident() : BatchKernel<S, false, false, false>::resident();
 }
 
 }  // namespace
 
-cudaError_t launch_step_batch(int storage, bool masked, bool tau_one, const BatchInst* insts, const BatchItem* items,
-                              int nitems, int* counter, int parity, cudaStream_t s) {
+cudaError_t launch_step_batch(int storage, bool masked, bool tau_one, bool unal, const BatchInst* insts,
+                              const BatchItem* items, int nitems, int* counter, int parity, cudaStream_t s) {
   switch (storage) {
-    case LBM_F32: return launch_batch_s<LBM_F32>(masked, tau_one, insts, items, nitems, counter, parity, s);
-    case LBM_F16_DEV: return launch_batch_s<LBM_F16_DEV>(masked, tau_one, insts, items, nitems, counter, parity, s);
-    case LBM_BF16_DEV: return launch_batch_s<LBM_BF16_DEV>(masked, tau_one, insts, items, nitems, counter, parity, s);
+    case LBM_F32: return launch_batch_s<LBM_F32>(masked, tau_one, unal, insts, items, nitems, counter, parity, s);
+    case LBM_F16_DEV:
+      return launch_batch_s<LBM_F16_DEV>(masked, tau_one, unal, insts, items, nitems, counter, parity, s);
+    case LBM_BF16_DEV:
+      return launch_batch_s<LBM_BF16_DEV>(masked, tau_one, unal, insts, items, nitems, counter, parity, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1070,6 +1217,8 @@ bool step_tma2_allowed(int storage, int nx) {
   return storage == LBM_F32 ? tma2_ok<LBM_F32>(nx)
                             : (storage == LBM_F16_DEV ? tma2_ok<LBM_F16_DEV>(nx) : tma2_ok<LBM_BF16_DEV>(nx));
 }
+
+bool step_tma2_unaligned_allowed(int nx) { return tma2_unal_ok(nx); }
 
 cudaError_t launch_step(int storage, const StepParams& p, cudaStream_t s) {
   switch (storage) {

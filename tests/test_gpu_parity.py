@@ -359,19 +359,23 @@ def test_full_box_8192_crop_against_full_oracle():
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("nx,ny,barrier", [(528, 70, False), (272, 9, False), (320, 80, True), (544, 80, True)])
+@pytest.mark.parametrize("nx,ny,barrier", [(528, 70, False), (272, 9, False), (320, 80, True), (544, 80, True),
+                                           (1043, 40, False), (250, 9, False), (337, 80, True), (19, 12, False)])
 @pytest.mark.parametrize("tau", [1.0, 0.8])
 def test_tma_staged_kernel_matches_plain_kernel_bitwise(storage, nx, ny, barrier, tau):
     """The TMA-staged fused steps (one and two cells per thread; ragged last
     strips, periodic wrap, barrier mask staged alongside) give bitwise the
     plain-load kernel's populations, and the FP32 run stays close to the
-    oracle."""
+    oracle. Widths that are not multiples of 16 (1043: a 19-column last strip;
+    250, 337, 19) take the two-cell kernel's variant that bulk-copies the
+    aligned interior of each row and plain-loads the rest, with odd widths and
+    rows that start at odd cell indices."""
     if barrier:
         b = two_bubbles(nx, ny, R=20, gap=3.0)
         rho = O.init_bubbles(O.make_params(nx, ny), b, RL, RG, 4.0)
     else:
         rho = inputs.noise_density(nx, ny, seed=9)
-    variants = (1, 2, 3, 4) if nx >= 528 else (1, 2, 4)
+    variants = (1, 2, 3, 4) if nx >= 528 else (1, 2, 3, 4) if nx % 16 else (1, 2, 4)
     sims = []
     for variant in variants:
         s = gpu_sim(nx, ny, rho, storage=storage, barrier=barrier, rho_ref=float(np.mean(rho)), tau=tau)
@@ -395,13 +399,16 @@ def test_step_variant_selection_errors():
     with pytest.raises(LbmError) as e:
         sim.set_step_variant(2)  # 128 columns is too narrow for the staged kernel
     assert e.value.code == 6
-    sim.set_step_variant(3)  # the two-cell kernel takes any width that is a multiple of 16
+    sim.set_step_variant(3)  # the two-cell kernel takes any width of 16 or more
     odd = gpu_sim(100, 64, inputs.noise_density(100, 64, seed=1))
+    odd.set_step_variant(3)
+    odd.set_step_variant(4)
+    narrow = gpu_sim(12, 64, inputs.noise_density(12, 64, seed=1))
     with pytest.raises(LbmError) as e:
-        odd.set_step_variant(3)
+        narrow.set_step_variant(3)
     assert e.value.code == 6
     with pytest.raises(LbmError) as e:
-        odd.set_step_variant(4)  # dynamic chunks: also the two-cell kernel
+        narrow.set_step_variant(4)  # dynamic chunks: also the two-cell kernel
     assert e.value.code == 6
     sim.set_step_variant(4)
     with pytest.raises(LbmError):
