@@ -504,8 +504,9 @@ __device__ __forceinline__ void copy_row_wrapped3(T* dst, const T* row, int star
 
 // Rows that do not start on 16-byte boundaries (nx % 16 != 0, variant UNAL
 // of the two-cell march): a staged row keeps window element e at slot
-// position e + off, where off = (global index of window element 0) mod M
-// (M = elements per 16 bytes), so the row's 16-byte-aligned interior can be
+// position e + off, where off = (index of window element 0 in the buffer,
+// plane offset i N included) mod M (M = elements per 16 bytes), so the row's
+// 16-byte-aligned interior can be
 // bulk-copied to an aligned slot position; its head and tail (fewer than M
 // elements each) and any halo that wraps around the periodic row are loaded
 // by the helper lanes with plain loads. A row slot holds M more elements.
@@ -516,6 +517,7 @@ struct URow {
   int hB;   // [hA, hB) by one bulk copy
 };
 
+// gbase: buffer index of the row's column 0 (plane offset included).
 template <typename T>
 __device__ __forceinline__ URow<T> urow(long long gbase, int c0, int len, int nx) {
   constexpr int M = 16 / (int)sizeof(T);
@@ -591,7 +593,7 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
     const T* row = src + (size_t)q * p.N + (size_t)g * nx;
     T* dst = reinterpret_cast<T*>(st + q * RB);
     const int c0 = x0 - G::PAD;
-    const URow<T> u = urow<T>((long long)g * nx, c0, len, nx);
+    const URow<T> u = urow<T>((long long)q * p.N + (long long)g * nx, c0, len, nx);
     urow_plain<T>(dst, row, u, c0, len, nx, j, 3);
     if (j == 0 && u.hB > u.hA) {
       bytes = (uint32_t)((u.hB - u.hA) * G::E);
@@ -687,22 +689,25 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
     float2 f[Q];
     float2 rho = make_float2(1.f, 1.f), jx = make_float2(0.f, 0.f), jy = make_float2(0.f, 0.f);
     unsigned m = 0;
-    // UNAL: slot offsets of the three source rows (r - 1, r, r + 1) and of the mask row
-    int offm = 0, off0 = 0, offp = 0, offk = 0;
+    // UNAL: slot offset of plane i's source row is (i N + its row's start
+    // + x0 - PAD) mod M: the rows r - 1, r, r + 1 give three bases, each
+    // plane adds i N; the mask row's offset is taken mod 16
+    int bm = 0, b0 = 0, bp = 0, offk = 0;
     if (UNAL) {
       const int r = y0 - 1 + k, ny = p.ny;
       const int g0r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
       const int gm = g0r == 0 ? ny - 1 : g0r - 1, gp = g0r == ny - 1 ? 0 : g0r + 1;
-      offm = (int)(((long long)gm * nx + x0 - G::PAD + M) & (M - 1));
-      off0 = (int)(((long long)g0r * nx + x0 - G::PAD + M) & (M - 1));
-      offp = (int)(((long long)gp * nx + x0 - G::PAD + M) & (M - 1));
+      bm = (int)(((long long)gm * nx + x0 - G::PAD + M) & (M - 1));
+      b0 = (int)(((long long)g0r * nx + x0 - G::PAD + M) & (M - 1));
+      bp = (int)(((long long)gp * nx + x0 - G::PAD + M) & (M - 1));
       offk = (int)(((long long)g0r * nx + x0) & 15);
     }
     if (active) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         if (UNAL) {
-          const int q = pos - cx(i) + (cy(i) > 0 ? offm : (cy(i) < 0 ? offp : off0));
+          const int off = ((cy(i) > 0 ? bm : (cy(i) < 0 ? bp : b0)) + (int)((i * p.N) & (M - 1))) & (M - 1);
+          const int q = pos - cx(i) + off;
           f[i] = load_pair<S>(st + i * RB, q, q & 1);
         } else {
           f[i] = load_pair<S>(st + i * RB, pos - cx(i), cx(i));
@@ -719,7 +724,8 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
         }
       }
     } else if (helper) {
-      const int ho = UNAL ? (hcy > 0 ? offm : (hcy < 0 ? offp : off0)) : 0;
+      const int ho =
+          UNAL ? ((hcy > 0 ? bm : (hcy < 0 ? bp : b0)) + (int)((hplane * p.N) & (M - 1))) & (M - 1) : 0;
       const float v =
           hlane ? Store<S>::raw_smem(reinterpret_cast<const T*>(st + hplane * RB), hpos + ho) : 0.f;
       const float t1 = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, 1));
@@ -766,15 +772,21 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
       force_of(sv, psi_c, p.G, Fx, Fy);
       collide<TAU_ONE, S != LBM_F32>(fprev, rho_prev, jx_prev, jy_prev, Fx, Fy, p, bad);
       const size_t base = (size_t)rc * nx + x0 + 2 * tid;
-      if (UNAL && ((base & 1) || 2 * tid + 1 == width)) {
-        // a pair at an odd index cannot take one vector store; with an odd
-        // width the last pair's second cell is the right halo cell (computed
-        // for its psi only) and is not stored
+      if (UNAL) {
+        // a pair at an odd buffer index (odd row start, or odd i N) cannot
+        // take one vector store; with an odd width the last pair's second
+        // cell is the right halo cell (computed for its psi only) and is not
+        // stored
         const bool second = 2 * tid + 1 < width;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-          Store<S>::store_raw(dst, (size_t)i * p.N + base, fprev[i].x);
-          if (second) Store<S>::store_raw(dst, (size_t)i * p.N + base + 1, fprev[i].y);
+          const size_t idx = (size_t)i * p.N + base;
+          if ((idx & 1) || !second) {
+            Store<S>::store_raw(dst, idx, fprev[i].x);
+            if (second) Store<S>::store_raw(dst, idx + 1, fprev[i].y);
+          } else {
+            store_pair<S>(dst, idx, fprev[i]);
+          }
         }
       } else {
 #pragma unroll
