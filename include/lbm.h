@@ -111,7 +111,7 @@ typedef struct {
    * density; P and the rupture test use the mixture pressure
    * (rho_m + rho_g)/3 + (G_mm psi_m^2 + 2 G_mg psi_m psi_g + G_gg psi_g^2)/6.
    * Two components need FP32 storage, growth = 0 and, with the barrier,
-   * nx % 32 == 0 and ny % 8 == 0; they cannot join a batch. */
+   * R_z <= 16; they cannot join a batch. */
   int32_t components;            /* 1 (default) or 2 */
   int32_t reserved2;             /* must be 0 */
   double tau_g;                  /* gas relaxation time > 0.5 */

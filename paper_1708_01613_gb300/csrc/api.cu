@@ -49,7 +49,7 @@ bool valid_config(const lbm_config* c, char* why, size_t n) {
     if (!(c->tau_g > 0.5) || !isfinite(c->tau_g)) return snprintf(why, n, "tau_g must be > 0.5"), false;
     if (!isfinite(c->G_mg) || !isfinite(c->G_gg)) return snprintf(why, n, "G_mg, G_gg must be finite"), false;
     if (c->barrier && !relabel_tiled_ok(c->nx, c->ny, c->zone_radius))
-      return snprintf(why, n, "two components with the barrier need nx %% 32 == 0, ny %% 8 == 0, R_z <= 16"), false;
+      return snprintf(why, n, "two components with the barrier need R_z <= 16"), false;
   }
   if (!(c->tau > 0.5) || !isfinite(c->tau)) return snprintf(why, n, "tau must be > 0.5"), false;
   if (!isfinite(c->G)) return snprintf(why, n, "G must be finite"), false;
@@ -308,8 +308,8 @@ RelabelBox handle_relabel_box(lbm_handle* h) {
   b.G_gg = (float)c.G_gg;
   b.nx = c.nx;
   b.ny = c.ny;
-  b.ntx = c.nx / kRelabelTileX;
-  b.nty = c.ny / kRelabelTileY;
+  b.ntx = (c.nx + kRelabelTileX - 1) / kRelabelTileX;
+  b.nty = (c.ny + kRelabelTileY - 1) / kRelabelTileY;
   b.R = c.zone_radius;
   b.cur = 0;
   b.threshold = (float)c.gas_threshold;

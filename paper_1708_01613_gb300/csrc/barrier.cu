@@ -580,8 +580,9 @@ __global__ void __launch_bounds__(kThreads) k_stats_partial(long long N, const i
 }
 
 // ---------------------------------------------------------------------------
-// Tiled barrier pipeline (boxes with nx % 32 == 0 and ny % 8 == 0). The box is
-// cut into 32 x 8 tiles. The density pass also joins the gas cells inside
+// Tiled barrier pipeline. The box is cut into 32 x 8 tiles; where nx or ny is
+// not a multiple of the tile, the last tile column or row is ragged and its
+// threads outside the box take part in the barriers only. The density pass also joins the gas cells inside
 // each tile (a union-find in shared memory: a gas cell's initial label is
 // the smallest index of its piece of the tile) and writes one gas flag per
 // tile; the union phase then joins the pieces across tile borders. A tile is
@@ -673,19 +674,21 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
   const int nx = B.nx, ny = B.ny;
   const size_t N = (size_t)nx * ny;
   const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
-  const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
-  const size_t r0 = (size_t)y * nx, rm = (size_t)wrap1(y - 1, ny) * nx, rp = (size_t)wrap1(y + 1, ny) * nx;
+  const bool in = x < nx && y < ny;  // a ragged tile's threads outside the box only join the barriers
+  const int xi = in ? x : 0, yi = in ? y : 0;
+  const int xm = wrap1(xi - 1, nx), xp = wrap1(xi + 1, nx);
+  const size_t r0 = (size_t)yi * nx, rm = (size_t)wrap1(yi - 1, ny) * nx, rp = (size_t)wrap1(yi + 1, ny) * nx;
   float f[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
-    const int xs = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : x);
+    const int xs = cx(i) > 0 ? xm : (cx(i) < 0 ? xp : xi);
     f[i] = Store<S>::load(p, (size_t)i * N + row + xs, B.wref[i]);
   }
   const float r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-  const size_t c = r0 + x;
-  B.rho[c] = r;
-  if (TWO) {  // two components (FP32): the gas lattice follows the melt's nine planes
+  const size_t c = r0 + xi;
+  if (in) B.rho[c] = r;
+  if (TWO && in) {  // two components (FP32): the gas lattice follows the melt's nine planes
     const float* pg = reinterpret_cast<const float*>(p) + (size_t)Q * N;
     float g = 0.f;
 #pragma unroll
@@ -697,7 +700,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
     const float a = B.rho0 * (1.0f - expf(-r / B.rho0)), b = B.rho0 * (1.0f - expf(-g / B.rho0));
     B.pr[c] = (r + g) * (1.0f / 3.0f) + (B.G * a * a + 2.0f * B.G_mg * a * b + B.G_gg * b * b) * (1.0f / 6.0f);
   }
-  const bool gas = r < B.threshold;
+  const bool gas = in && r < B.threshold;
   // gas cells joined inside the tile here (shared-memory union-find); each
   // starts the global union-find pointing at the smallest index of its piece
   // of the tile, and the union phase joins the pieces across tile borders
@@ -720,7 +723,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_density_label(const RelabelBox* 
     const int32_t o = B.label[c];
     B.owner[c] = o >= 0 ? o : 0x7fffffff;
   }
-  B.label[c] = lab;
+  if (in) B.label[c] = lab;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     B.tile_gas[t] = (uint8_t)(any != 0);
     if (t == 0) {  // the tile lists are rebuilt by the next phase and the mask phase
@@ -751,10 +754,15 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
   const RelabelBox& B = boxes[e[k].box];
   const int t = blockIdx.x - e[k].off_tiles;
   const unsigned short* p = static_cast<const unsigned short*>(B.pops[B.cur ^ parity]);
-  const int nx = B.nx, ny = B.ny;  // nx % 32 == 0: x even, rows start on 4-byte boundaries
+  const int nx = B.nx, ny = B.ny;
   const size_t N = (size_t)nx * ny;
+  // whole tiles: nx % 32 == 0, so x is even and rows start on 4-byte
+  // boundaries (paired 32-bit loads); a box with ragged tiles loads cell by cell
+  const bool whole = nx % kTX == 0 && ny % kTY == 0;
   const int x = (t % B.ntx) * kTX + 2 * threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
-  const size_t r0 = (size_t)y * nx, rm = (size_t)wrap1(y - 1, ny) * nx, rp = (size_t)wrap1(y + 1, ny) * nx;
+  const bool ina = x < nx && y < ny, inb = x + 1 < nx && y < ny;
+  const int yi = y < ny ? y : 0;
+  const size_t r0 = (size_t)yi * nx, rm = (size_t)wrap1(yi - 1, ny) * nx, rp = (size_t)wrap1(yi + 1, ny) * nx;
   float f0[Q], f1[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -762,7 +770,10 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
     const unsigned short* q = p + (size_t)i * N + row;
     const int s = x - cx(i);  // cell x pulls from column s, cell x + 1 from s + 1
     uint32_t bits;
-    if (cx(i) == 0) {
+    if (!whole) {
+      const unsigned lo = ina ? __ldg(q + wrap1(s, nx)) : 0u, hi = inb ? __ldg(q + wrap1(s + 1, nx)) : 0u;
+      bits = lo | (hi << 16);
+    } else if (cx(i) == 0) {
       bits = __ldg(reinterpret_cast<const uint32_t*>(q + x));
     } else if (s >= 0 && s + 1 < nx) {
       const uint32_t* w = reinterpret_cast<const uint32_t*>(q);
@@ -776,8 +787,13 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
   const float ra = ((f0[0] + f0[1]) + (f0[2] + f0[3])) + ((f0[4] + f0[5]) + (f0[6] + f0[7])) + f0[8];
   const float rb = ((f1[0] + f1[1]) + (f1[2] + f1[3])) + ((f1[4] + f1[5]) + (f1[6] + f1[7])) + f1[8];
   const size_t c = r0 + x;
-  *reinterpret_cast<float2*>(B.rho + c) = make_float2(ra, rb);
-  const bool ga = ra < B.threshold, gb = rb < B.threshold;
+  if (whole) {
+    *reinterpret_cast<float2*>(B.rho + c) = make_float2(ra, rb);
+  } else {
+    if (ina) B.rho[c] = ra;
+    if (inb) B.rho[c + 1] = rb;
+  }
+  const bool ga = ina && ra < B.threshold, gb = inb && rb < B.threshold;
   __shared__ int sp[kTX * kTY];  // tile-local union-find, as in kb_density_label
   const int la = threadIdx.y * kTX + 2 * threadIdx.x, lb = la + 1;
   sp[la] = ga ? la : -1;
@@ -800,12 +816,20 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
     if (gb) labb = tile_root_index(sp, lb, x0, y0, nx, &fail);
     if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
   }
-  if (ga || gb) {  // labels of the previous relabel, for the coalescence count
-    const int2 o = *reinterpret_cast<const int2*>(B.label + c);
-    if (ga) B.owner[c] = o.x >= 0 ? o.x : 0x7fffffff;
-    if (gb) B.owner[c + 1] = o.y >= 0 ? o.y : 0x7fffffff;
+  if (ga) {  // labels of the previous relabel, for the coalescence count
+    const int32_t o = B.label[c];
+    B.owner[c] = o >= 0 ? o : 0x7fffffff;
   }
-  *reinterpret_cast<int2*>(B.label + c) = make_int2(laba, labb);
+  if (gb) {
+    const int32_t o = B.label[c + 1];
+    B.owner[c + 1] = o >= 0 ? o : 0x7fffffff;
+  }
+  if (whole) {
+    *reinterpret_cast<int2*>(B.label + c) = make_int2(laba, labb);
+  } else {
+    if (ina) B.label[c] = laba;
+    if (inb) B.label[c + 1] = labb;
+  }
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     B.tile_gas[t] = (uint8_t)(any != 0);
     if (t == 0) {  // the tile lists are rebuilt by the next phase and the mask phase
@@ -824,7 +848,10 @@ __global__ void kb_active(const RelabelBox* __restrict__ boxes, const RelabelEnt
   const int t = (blockIdx.x - e[k].off_scan) * blockDim.x + threadIdx.x;
   const int ntx = B.ntx, nty = B.nty;
   if (t >= ntx * nty) return;
-  const int spx = (B.R + kTX - 1) / kTX, spy = (B.R + kTY - 1) / kTY;
+  // tiles within reach of R cells; across the periodic seam of a box with a
+  // ragged last tile one tile more
+  const int spx = (B.R + kTX - 1) / kTX + (B.nx % kTX ? 1 : 0);
+  const int spy = (B.R + kTY - 1) / kTY + (B.ny % kTY ? 1 : 0);
   const int ty = t / ntx, tx = t - ty * ntx;
   int a = 0;
   for (int dy = -spy; dy <= spy && !a; ++dy) {
@@ -864,9 +891,10 @@ __global__ void __launch_bounds__(kTX * kTY) kb_union(const RelabelBox* __restri
     if (!B.tile_gas[t]) continue;
     // edges inside the tile were joined by the density phase: only the
     // right and bottom borders (periodic wrap included) are left
-    const bool re = threadIdx.x == kTX - 1, be = threadIdx.y == kTY - 1;
-    if (!re && !be) continue;
     const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    if (x >= nx || y >= ny) continue;
+    const bool re = threadIdx.x == kTX - 1 || x == nx - 1, be = threadIdx.y == kTY - 1 || y == ny - 1;
+    if (!re && !be) continue;
     const int c = y * nx + x;
     if (L[c] < 0) continue;
     if (re) {
@@ -890,7 +918,9 @@ __global__ void __launch_bounds__(kTX * kTY) kb_flatten(const RelabelBox* __rest
   for (int w = lw.first; w < lw.n; w += lw.stride) {
     const int t = B.tile_list[w];
     if (!B.tile_gas[t]) continue;
-    const int c = ((t / B.ntx) * kTY + threadIdx.y) * B.nx + (t % B.ntx) * kTX + threadIdx.x;
+    const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    if (x >= B.nx || y >= B.ny) continue;
+    const int c = y * B.nx + x;
     if (L[c] >= 0) L[c] = find_root(L, c, &fail);
   }
   if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
@@ -907,7 +937,9 @@ __global__ void __launch_bounds__(kTX * kTY) kb_merge(const RelabelBox* __restri
   for (int w = lw.first; w < lw.n; w += lw.stride) {
     const int t = B.tile_list[w];
     if (!B.tile_gas[t]) continue;
-    const int c = ((t / B.ntx) * kTY + threadIdx.y) * B.nx + (t % B.ntx) * kTX + threadIdx.x;
+    const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    if (x >= B.nx || y >= B.ny) continue;
+    const int c = y * B.nx + x;
     const int r = B.label[c];
     if (r >= 0 && r != c) n += merge_vote(B.owner, r, B.owner[c]);
   }
@@ -957,9 +989,10 @@ __global__ void __launch_bounds__(kTX * kTY) kb_owner(const RelabelBox* __restri
     const int t = B.tile_list[w];
     const int tx = t % B.ntx, ty = t / B.ntx;
     const int x = tx * kTX + threadIdx.x, y = ty * kTY + threadIdx.y;
+    const bool in = x < nx && y < ny;
     const size_t c = (size_t)y * nx + x;
     if (!B.tile_active[t]) {  // went quiet since the previous relabel
-      B.owner[c] = -1;
+      if (in) B.owner[c] = -1;
       continue;
     }
     const int W = kTX + 2 * R, H = kTY + 2 * R;
@@ -977,7 +1010,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_owner(const RelabelBox* __restri
     } else if (result < 0) {
       result = window_owner(row0, W, R);
     }
-    B.owner[c] = result;
+    if (in) B.owner[c] = result;
   }
 }
 
@@ -992,8 +1025,9 @@ __global__ void __launch_bounds__(kTX * kTY) kb_rupture(const RelabelBox* __rest
     const int t = B.tile_list[w];
     const int act = B.tile_active[t];
     const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    const bool in = x < nx && y < ny;
     const size_t c = (size_t)y * nx + x;
-    const int o = act ? own[c] : -1;
+    const int o = act && in ? own[c] : -1;
     int dir = 0;
     if (o != -1) {
 #pragma unroll
@@ -1004,7 +1038,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_rupture(const RelabelBox* __rest
     }
     int opened = 0;
     if (dir == 0) {
-      B.sgn[c] = 0;
+      if (in) B.sgn[c] = 0;
     } else {
       int ex = 0, ey = 0;
 #pragma unroll
@@ -1043,9 +1077,10 @@ __global__ void __launch_bounds__(kTX * kTY) kb_mask(const RelabelBox* __restric
     const int t = B.tile_list[w];
     const int act = B.tile_active[t];
     const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    const bool in = x < nx && y < ny;
     const size_t c = (size_t)y * nx + x;
     unsigned msk = 0;
-    const int o = act ? B.owner[c] : -1;
+    const int o = act && in ? B.owner[c] : -1;
     if (o != -1 && !B.open[c]) {
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
@@ -1054,7 +1089,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_mask(const RelabelBox* __restric
         if (on != -1 && on != o && !B.open[nb]) msk |= 1u << (i - 1);
       }
     }
-    B.mask[c] = (uint8_t)msk;
+    if (in) B.mask[c] = (uint8_t)msk;
     // tiles holding a blocked edge go to the bounce-back's list
     const int film = __syncthreads_or((msk & kCanonBits) != 0);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -1125,6 +1160,7 @@ __global__ void __launch_bounds__(kTX * kTY) kb_bounce(const RelabelBox* __restr
   for (int w = lw.first; w < nfilm; w += lw.stride) {
     const int t = B.film_list[w];
     const int x = (t % B.ntx) * kTX + threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+    if (x >= B.nx || y >= B.ny) continue;
     const unsigned msk = B.mask[(size_t)y * B.nx + x];
     if (msk & kCanonBits) bounce_cell<T, TWO>(pops, N, x, y, B.nx, B.ny, msk);
   }
@@ -1299,7 +1335,7 @@ cudaError_t launch_bubble_list(int nx, int ny, const int32_t* label, int32_t* ar
   return cudaGetLastError();
 }
 
-bool relabel_tiled_ok(int nx, int ny, int R) { return nx % kTX == 0 && ny % kTY == 0 && R <= kOMaxR; }
+bool relabel_tiled_ok(int nx, int ny, int R) { return nx > 2 * R && ny > 2 * R && R <= kOMaxR; }
 
 int relabel_tile_count(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY); }
 

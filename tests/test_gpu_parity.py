@@ -89,7 +89,8 @@ def _bits_equal_except_near(a, b, ok_mask):
 def test_barrier_parity_two_bubbles_fp32(nx, ny, gap, R, eps):
     """Barrier on (K = 1): populations within 1e-5 and the owner map and
     blocked-edge mask bit-exact at steps 1, 10, 100 (160 x 80 runs the tiled
-    relabel pipeline, 164 x 84 the untiled one). Both films have wall cells
+    relabel pipeline on whole 32 x 8 tiles, 164 x 84 with a ragged last tile
+    column and row). Both films have wall cells
     (owner -2) on their symmetry plane (the 9-cell liquid gap of the 6-cell
     film is bridged by zones of radius 5; there the rupture test is off,
     since with it every wall cell opens within 10 steps as the initial
