@@ -64,8 +64,7 @@ def test_config_rules_of_the_variants():
         dict(components=2, tau_g=0.5),                      # tau_g > 0.5
         dict(components=2, G_mg=float("nan")),
         dict(components=3),
-        dict(components=2, barrier=True, nx=100),           # two-lattice barrier: tiled sizes only
-        dict(components=2, barrier=True, ny=60),
+        dict(components=2, barrier=True, zone_radius=17),   # two-lattice barrier: tiled pipeline, R_z <= 16
         dict(nx=65536, ny=65536),                           # nx * ny beyond int32
         dict(G=float("inf")),
         dict(rupture_eps=float("nan")),

@@ -49,10 +49,11 @@ def test_mixture_parity(nx, ny, taus):
         assert err < 1e-5
 
 
-@pytest.mark.parametrize("nx", [160, 352])
-def test_two_bubbles_with_barrier_parity(nx):
-    """Plain (160 columns) and staged (352) kernels with the barrier mask."""
-    ny, R, gap = 80, 12, 3.0
+@pytest.mark.parametrize("nx,ny", [(160, 80), (352, 80), (170, 77)])
+def test_two_bubbles_with_barrier_parity(nx, ny):
+    """Plain (160 columns) and staged (352) kernels with the barrier mask; a
+    box with ragged relabel tiles (170 x 77)."""
+    R, gap = 12, 3.0
     b = [[nx / 2 - R - gap / 2, ny / 2, R], [nx / 2 + R + gap / 2, ny / 2, R]]
     rm = O.init_bubbles(O.make_params(nx, ny), b, RL, RG, 4.0)
     rg = 0.005 + 0.3 * (RL - rm) / (RL - RG)
@@ -104,7 +105,7 @@ def test_mass_conservation_and_rules():
     with pytest.raises(LbmError):
         Simulation(make_config(n, n, components=2, storage="f16"))
     with pytest.raises(LbmError):
-        Simulation(make_config(100, 64, components=2, barrier=True))  # tiled relabel sizes only
+        Simulation(make_config(100, 64, components=2, barrier=True, zone_radius=17))  # tiled relabel: R_z <= 16
     with pytest.raises(LbmError) as e:
         sim.init_bubbles([[10.0, 10.0, 5.0]], RL, RG, 4.0)
     assert e.value.code == 6
