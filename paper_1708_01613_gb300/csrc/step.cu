@@ -1098,7 +1098,12 @@ template <int S, bool MASKED, bool TAU_ONE>
 cudaError_t launch_variant(const StepParams& p, cudaStream_t s) {
   const int v = p.force_generic;
   if ((v == 4 || v == 0) && tma2_ok<S>(p.nx)) return launch_dyn<S, MASKED, TAU_ONE>(p, s);
-  if ((v == 4 || v == 0) && tma2_unal_ok(p.nx)) return launch_dyn<S, MASKED, TAU_ONE, true>(p, s);
+  // automatic choice for other widths (measured at 2040-2056 columns): the
+  // unaligned staging where nx is even (FP16 2040^2: 0.086 ms against 0.103
+  // plain), the plain loads where it is odd (2047^2: 0.104 against 0.110;
+  // the helper warp's plain loads of each row's unaligned ends hold up
+  // every row)
+  if ((v == 4 || (v == 0 && p.nx % 2 == 0)) && tma2_unal_ok(p.nx)) return launch_dyn<S, MASKED, TAU_ONE, true>(p, s);
   if (v == 3) {
     if (tma2_ok<S>(p.nx)) return launch_tma2<S, MASKED, TAU_ONE>(p, s);
     if (tma2_unal_ok(p.nx)) return launch_tma2<S, MASKED, TAU_ONE, true>(p, s);
