@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--serve-policy", default="tiered", choices=["work", "time", "lockstep", "tiered"])
     ap.add_argument("--serve-big-s", type=float, default=0.02,
                     help="tiered policy: requests with more GPU time left than this are served first come, first served")
+    ap.add_argument("--serve-big-slowdown", type=float, default=1.25,
+                    help="tiered policy: the oldest big request takes the whole quantum past this slowdown")
     ap.add_argument("--serve-small-share", type=float, default=0.5,
                     help="tiered policy: most of each quantum that small requests take while a big one runs")
     ap.add_argument("--serve-load", type=float, default=0.9,
@@ -431,16 +433,21 @@ def run_served(args, dev, world, rank, capacity_ups):
                             inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55, True, 10))
     torch.cuda.synchronize(dev)
     server = FoamServer(memory_budget_bytes=int(args.serve_budget_gb * 2**30), max_boxes=32, device=str(dev),
-                        policy=args.serve_policy, big_s=args.serve_big_s, small_share=args.serve_small_share)
+                        policy=args.serve_policy, big_s=args.serve_big_s, small_share=args.serve_small_share,
+                        big_slowdown=args.serve_big_slowdown)
     served = summarize(server.run(reqs), server.stats["makespan_s"])
     alone_res, alone_span = run_one_at_a_time(reqs, device=str(dev))
     alone = summarize(alone_res, alone_span)
-    return {"workload": f"{n} requests, Poisson arrivals at offered load {args.serve_load} of the one-at-a-time "
-                        "throughput, sides "
-                        "128-4096 log-uniform, 2-300 bubbles, 1k-20k steps x step_scale, FP32/FP16 50/50, "
-                        "barrier on (K=10)",
+    reduced = n < 2000 or scale < 1.0
+    return {"workload": ("reduced stream: " if reduced else "") +
+                        f"{n} requests (the configuration: 2000), Poisson arrivals at offered load "
+                        f"{args.serve_load} of the one-at-a-time throughput, sides "
+                        "128-4096 log-uniform (any integer), 2-300 bubbles, 1k-20k steps x step_scale "
+                        f"({scale}), FP32/FP16 50/50, barrier on (K=10)",
+            "reduced": reduced,
             "step_scale": scale, "rate_per_s": round(rate, 3), "memory_budget_gb": args.serve_budget_gb,
             "policy": server.policy, "big_s": server.big_s, "small_share": server.small_share,
+            "big_slowdown": server.big_slowdown,
             "quantum_s": server.quantum_s,
             "p50_s": served["p50_s"], "p99_s": served["p99_s"], "mean_s": served["mean_s"],
             "p50_by_size_s": served["p50_by_size_s"], "mlups": served["mlups"],

@@ -197,7 +197,9 @@ class FoamServer:
     `quantum_updates` fixes the budget), "time" shares GPU time counting a
     launch cost per step (`fair_time_steps`), "lockstep" steps every box in
     every launch (`lockstep_steps`), "tiered" serves big jobs first come,
-    first served beside equally shared small ones (`tiered_steps`). Every batch runs its plan as multi-rate
+    first served beside equally shared small ones (`tiered_steps`), and
+    gives the oldest big job the whole quantum while its projected latency
+    exceeds `big_slowdown` times its work alone. Every batch runs its plan as multi-rate
     steps (lbm_batch_step_each), so small boxes can take many cheap steps
     while large ones take few."""
     memory_budget_bytes: int
@@ -207,6 +209,8 @@ class FoamServer:
     policy: str = "work"            # "work" | "time" | "lockstep" | "tiered"
     big_s: float = 0.05             # "tiered": a job with more work left than this much GPU time is big
     small_share: float = 0.5        # "tiered": most of a quantum the small jobs take while a big one runs
+    big_slowdown: float = 1.25      # "tiered": once the oldest big job's projected latency exceeds this
+                                    # many times its work alone, it takes the whole quantum
     device: str = "cuda"
     keep_pops: bool = False
     stats: dict = field(default_factory=dict)
@@ -280,7 +284,19 @@ class FoamServer:
                 share = lockstep_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
             elif self.policy == "tiered":
                 budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
-                share = tiered_steps(jobs_now, budget, self.big_s / model.s_per_update, self.small_share)
+                big_updates = self.big_s / model.s_per_update
+                small_share = self.small_share
+                bigs = [j for j in jobs_now if j.remaining * j.cells >= big_updates]
+                if bigs:
+                    # projected latency of the oldest big job at the full rate
+                    # from now on, against its work alone: past the bound it
+                    # takes the whole quantum (small jobs still move a step)
+                    j0 = min(bigs, key=lambda j: (j.req.arrival_s, j.req.rid))
+                    alone = j0.req.steps * j0.cells * model.s_per_update
+                    projected = (now - j0.req.arrival_s) + j0.remaining * j0.cells * model.s_per_update
+                    if projected > self.big_slowdown * alone:
+                        small_share = 0.0
+                share = tiered_steps(jobs_now, budget, big_updates, small_share)
             else:
                 raise ValueError(f"unknown policy {self.policy!r}")
             ts = time.perf_counter()

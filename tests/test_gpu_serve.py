@@ -93,6 +93,11 @@ def test_tiered_plan():
     assert s[2] == int((4e6 - 1e3 - s[3] * 1000) // 10**6) and s[1] == 0
     only_small = tiered_steps(jobs[:1] + jobs[3:], 4e6, big_updates=1e8)
     assert only_small == {0: 10, 3: int((4e6 - 1e3) // 1000)}
+    # a big job past its slowdown bound: the small ones move one step, the
+    # big one takes the rest of the quantum
+    late = tiered_steps(jobs, 4e6, big_updates=1e8, small_share=0.0)
+    assert late[0] == 1 and late[3] == 1 and late[1] == 0
+    assert late[2] == int((4e6 - 100 - 1000) // 10**6)
 
 
 @pytest.mark.gpu
