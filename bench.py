@@ -610,6 +610,23 @@ def cpu_sample(steps: int, warmup: int, budget_s: float | None):
     return n * n * steps / dt / 1e6, steps, dt, O.max_threads()
 
 
+def cpu_spinodal_config():
+    """The FP64 oracle on the spinodal configuration as stated: 128^2,
+    rho = 0.7 (1 + 0.01 U[-1, 1)), G = -5.5, 2000 steps (seed 1)."""
+    import inputs
+    import oracle as O
+
+    n, steps = 128, 2000
+    s = O.OracleSim(O.make_params(n, n, G=-5.5))
+    s.init_density(inputs.noise_density(n, n, seed=1))
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(n * n * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": O.max_threads(),
+            "kind": "oracle", "seconds": round(dt, 3),
+            "sample": "the whole spinodal run: 128^2, 2000 steps, rho = 0.7 (1 + 0.01 U[-1,1)), G = -5.5"}
+
+
 def cpu_sample_two_component(budget_s: float = 4.0):
     """The FP64 two-component oracle on a 256^2 box of the two-component
     leg's kind (one melt bubble filled with gas, G_mm = -5.5, G_mg = 1.0,
@@ -667,6 +684,7 @@ def main():
         O.set_threads(cores)
         out["cpu_baseline"]["single_thread"] = {"value": round(m1, 3), "unit": "MLUPS", "cores": 1,
                                                 "sample": f"{s1} steps of the same box ({d1:.1f} s, one thread)"}
+        out["cpu_baseline"]["spinodal_128"] = cpu_spinodal_config()
     if world > 1:
         import torch.distributed as dist
 
