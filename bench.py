@@ -69,8 +69,10 @@ def parse():
     ap.add_argument("--serve-policy", default="tiered", choices=["work", "time", "lockstep", "tiered"])
     ap.add_argument("--serve-big-s", type=float, default=0.02,
                     help="tiered policy: requests with more GPU time left than this are served first come, first served")
-    ap.add_argument("--serve-big-slowdown", type=float, default=1.25,
-                    help="tiered policy: the oldest big request takes the whole quantum past this slowdown")
+    ap.add_argument("--serve-big-slowdown", type=float, default=float("inf"),
+                    help="tiered policy: past this slowdown of the oldest big request the small ones' share "
+                         "is cut to --serve-late-share")
+    ap.add_argument("--serve-late-share", type=float, default=0.0)
     ap.add_argument("--serve-small-share", type=float, default=0.5,
                     help="tiered policy: most of each quantum that small requests take while a big one runs")
     ap.add_argument("--serve-load", type=float, default=0.9,
@@ -434,7 +436,7 @@ def run_served(args, dev, world, rank, capacity_ups):
     torch.cuda.synchronize(dev)
     server = FoamServer(memory_budget_bytes=int(args.serve_budget_gb * 2**30), max_boxes=32, device=str(dev),
                         policy=args.serve_policy, big_s=args.serve_big_s, small_share=args.serve_small_share,
-                        big_slowdown=args.serve_big_slowdown)
+                        big_slowdown=args.serve_big_slowdown, late_share=args.serve_late_share)
     served = summarize(server.run(reqs), server.stats["makespan_s"])
     alone_res, alone_span = run_one_at_a_time(reqs, device=str(dev))
     alone = summarize(alone_res, alone_span)
@@ -447,7 +449,7 @@ def run_served(args, dev, world, rank, capacity_ups):
             "reduced": reduced,
             "step_scale": scale, "rate_per_s": round(rate, 3), "memory_budget_gb": args.serve_budget_gb,
             "policy": server.policy, "big_s": server.big_s, "small_share": server.small_share,
-            "big_slowdown": server.big_slowdown,
+            "big_slowdown": server.big_slowdown, "late_share": server.late_share,
             "quantum_s": server.quantum_s,
             "p50_s": served["p50_s"], "p99_s": served["p99_s"], "mean_s": served["mean_s"],
             "p50_by_size_s": served["p50_by_size_s"], "mlups": served["mlups"],

@@ -198,8 +198,8 @@ class FoamServer:
     launch cost per step (`fair_time_steps`), "lockstep" steps every box in
     every launch (`lockstep_steps`), "tiered" serves big jobs first come,
     first served beside equally shared small ones (`tiered_steps`), and
-    gives the oldest big job the whole quantum while its projected latency
-    exceeds `big_slowdown` times its work alone. Every batch runs its plan as multi-rate
+    cuts the small ones' share to `late_share` while the oldest big job's
+    projected latency exceeds `big_slowdown` times its work alone. Every batch runs its plan as multi-rate
     steps (lbm_batch_step_each), so small boxes can take many cheap steps
     while large ones take few."""
     memory_budget_bytes: int
@@ -209,8 +209,9 @@ class FoamServer:
     policy: str = "work"            # "work" | "time" | "lockstep" | "tiered"
     big_s: float = 0.05             # "tiered": a job with more work left than this much GPU time is big
     small_share: float = 0.5        # "tiered": most of a quantum the small jobs take while a big one runs
-    big_slowdown: float = 1.25      # "tiered": once the oldest big job's projected latency exceeds this
-                                    # many times its work alone, it takes the whole quantum
+    big_slowdown: float = float("inf")  # "tiered": once the oldest big job's projected latency exceeds
+                                        # this many times its work alone, the small jobs' share is
+    late_share: float = 0.0             # cut to late_share (they still move a step per quantum)
     device: str = "cuda"
     keep_pops: bool = False
     stats: dict = field(default_factory=dict)
@@ -295,7 +296,7 @@ class FoamServer:
                     alone = j0.req.steps * j0.cells * model.s_per_update
                     projected = (now - j0.req.arrival_s) + j0.remaining * j0.cells * model.s_per_update
                     if projected > self.big_slowdown * alone:
-                        small_share = 0.0
+                        small_share = min(small_share, self.late_share)
                 share = tiered_steps(jobs_now, budget, big_updates, small_share)
             else:
                 raise ValueError(f"unknown policy {self.policy!r}")
