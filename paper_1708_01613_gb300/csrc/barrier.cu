@@ -764,25 +764,34 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
   const int yi = y < ny ? y : 0;
   const size_t r0 = (size_t)yi * nx, rm = (size_t)wrap1(yi - 1, ny) * nx, rp = (size_t)wrap1(yi + 1, ny) * nx;
   float f0[Q], f1[Q];
+  if (whole) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
-    const unsigned short* q = p + (size_t)i * N + row;
-    const int s = x - cx(i);  // cell x pulls from column s, cell x + 1 from s + 1
-    uint32_t bits;
-    if (!whole) {
-      const unsigned lo = ina ? __ldg(q + wrap1(s, nx)) : 0u, hi = inb ? __ldg(q + wrap1(s + 1, nx)) : 0u;
-      bits = lo | (hi << 16);
-    } else if (cx(i) == 0) {
-      bits = __ldg(reinterpret_cast<const uint32_t*>(q + x));
-    } else if (s >= 0 && s + 1 < nx) {
-      const uint32_t* w = reinterpret_cast<const uint32_t*>(q);
-      bits = __byte_perm(__ldg(w + ((s - 1) >> 1)), __ldg(w + ((s + 1) >> 1)), 0x5432);
-    } else {
-      bits = (uint32_t)__ldg(q + wrap1(s, nx)) | ((uint32_t)__ldg(q + wrap1(s + 1, nx)) << 16);
+    for (int i = 0; i < Q; ++i) {
+      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+      const unsigned short* q = p + (size_t)i * N + row;
+      const int s = x - cx(i);  // cell x pulls from column s, cell x + 1 from s + 1
+      uint32_t bits;
+      if (cx(i) == 0) {
+        bits = __ldg(reinterpret_cast<const uint32_t*>(q + x));
+      } else if (s >= 0 && s + 1 < nx) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(q);
+        bits = __byte_perm(__ldg(w + ((s - 1) >> 1)), __ldg(w + ((s + 1) >> 1)), 0x5432);
+      } else {
+        bits = (uint32_t)__ldg(q + wrap1(s, nx)) | ((uint32_t)__ldg(q + wrap1(s + 1, nx)) << 16);
+      }
+      f0[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)(bits & 0xffffu)));
+      f1[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)(bits >> 16)));
     }
-    f0[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)(bits & 0xffffu)));
-    f1[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)(bits >> 16)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+      const unsigned short* q = p + (size_t)i * N + row;
+      const int s = x - cx(i);
+      const unsigned lo = ina ? __ldg(q + wrap1(s, nx)) : 0u, hi = inb ? __ldg(q + wrap1(s + 1, nx)) : 0u;
+      f0[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)lo));
+      f1[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)hi));
+    }
   }
   const float ra = ((f0[0] + f0[1]) + (f0[2] + f0[3])) + ((f0[4] + f0[5]) + (f0[6] + f0[7])) + f0[8];
   const float rb = ((f1[0] + f1[1]) + (f1[2] + f1[3])) + ((f1[4] + f1[5]) + (f1[6] + f1[7])) + f1[8];
