@@ -505,11 +505,14 @@ __device__ __forceinline__ void copy_row_wrapped3(T* dst, const T* row, int star
 // Rows that do not start on 16-byte boundaries (nx % 16 != 0, variant UNAL
 // of the two-cell march): a staged row keeps window element e at slot
 // position e + off, where off = (index of window element 0 in the buffer,
-// plane offset i N included) mod M (M = elements per 16 bytes), so the row's
-// 16-byte-aligned interior can be
-// bulk-copied to an aligned slot position; its head and tail (fewer than M
-// elements each) and any halo that wraps around the periodic row are loaded
-// by the helper lanes with plain loads. A row slot holds M more elements.
+// plane offset i N included) mod M (M = elements per 16 bytes). A window
+// that does not wrap around the periodic row arrives in one bulk copy of the
+// 16-byte-aligned span that covers it (up to M - 1 elements on either side
+// land in the slot's slack and are never read); the mask row likewise. A
+// window that wraps (the box's first and last strips) takes its aligned
+// interior by bulk copy and the rest of what the march reads (its head and
+// tail, and the two halo elements on a wrapped side) by plain loads of the
+// helper lanes. A row slot holds 2 M more elements.
 template <typename T>
 struct URow {
   int off;  // slot position of window element 0
@@ -531,13 +534,15 @@ __device__ __forceinline__ URow<T> urow(long long gbase, int c0, int len, int nx
   return u;
 }
 
-// Plain loads of the elements kk = j, j + step, ... of a row's plain part.
+// Plain loads of the elements kk = j, j + step, ... of a row's plain part,
+// limited to the window elements [lo, hi) the march reads.
 template <typename T>
-__device__ __forceinline__ void urow_plain(T* dst, const T* row, const URow<T>& u, int c0, int len, int nx, int j,
-                                           int step) {
-  const int np = u.hA + (len - u.hB);
+__device__ __forceinline__ void urow_plain(T* dst, const T* row, const URow<T>& u, int c0, int lo, int hi, int nx,
+                                           int j, int step) {
+  const int n1 = u.hA > lo ? u.hA - lo : 0;
+  const int np = n1 + (hi > u.hB ? hi - u.hB : 0);
   for (int kk = j; kk < np; kk += step) {
-    const int e = kk < u.hA ? kk : u.hB + (kk - u.hA);
+    const int e = kk < n1 ? lo + kk : u.hB + (kk - n1);
     int c = (c0 + e) % nx;
     c = c < 0 ? c + nx : c;
     dst[e + u.off] = row[c];
@@ -553,8 +558,8 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
                                              int x0, int width, int lane) {
   using G = TmaGeom2<S>;
   using T = typename G::T;
-  constexpr int RB = G::ROW_BYTES + (UNAL ? 16 : 0);  // plane row stride in a slot
-  constexpr uint32_t SLOT_BYTES = Q * RB + (MASKED ? kBX2 + (UNAL ? 16 : 0) : 0);
+  constexpr int RB = G::ROW_BYTES + (UNAL ? 32 : 0);  // plane row stride in a slot
+  constexpr uint32_t SLOT_BYTES = Q * RB + (MASKED ? kBX2 + (UNAL ? 32 : 0) : 0);
   const int len = width + 2 * G::PAD;
   const int slot = (int)(gk % NSTAGE);
   unsigned char* st = stages + (size_t)slot * SLOT_BYTES;
@@ -586,6 +591,7 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
   const void* bsrc = nullptr;
   void* bdst = nullptr;
   if (q < Q) {
+    constexpr int M = 16 / G::E;
     const int ciy = (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
     int g = r - ciy;
     g = g < 0 ? g + ny : (g >= ny ? g - ny : g);
@@ -593,24 +599,31 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
     const T* row = src + (size_t)q * p.N + (size_t)g * nx;
     T* dst = reinterpret_cast<T*>(st + q * RB);
     const int c0 = x0 - G::PAD;
-    const URow<T> u = urow<T>((long long)q * p.N + (long long)g * nx, c0, len, nx);
-    urow_plain<T>(dst, row, u, c0, len, nx, j, 3);
-    if (j == 0 && u.hB > u.hA) {
-      bytes = (uint32_t)((u.hB - u.hA) * G::E);
-      bsrc = row + (c0 + u.hA);
-      bdst = dst + u.hA + u.off;
+    const long long gbase = (long long)q * p.N + (long long)g * nx;
+    if (c0 >= 0 && c0 + len <= nx) {  // no wrap: one covering bulk copy to slot position 0
+      const int off = (int)((gbase + c0) & (M - 1));
+      if (j == 0) {
+        bytes = (uint32_t)(((off + len + M - 1) / M) * 16);
+        bsrc = row + c0 - off;
+        bdst = dst;
+      }
+    } else {
+      const URow<T> u = urow<T>(gbase, c0, len, nx);
+      urow_plain<T>(dst, row, u, c0, G::PAD - 2, len - G::PAD + 2, nx, j, 3);
+      if (j == 0 && u.hB > u.hA) {
+        bytes = (uint32_t)((u.hB - u.hA) * G::E);
+        bsrc = row + (c0 + u.hA);
+        bdst = dst + u.hA + u.off;
+      }
     }
-  } else if (MASKED && q == Q) {
+  } else if (MASKED && q == Q && j == 0) {
+    // the mask window never wraps: one covering bulk copy to slot position 0
     const int g = r < 0 ? r + ny : (r >= ny ? r - ny : r);
-    const uint8_t* row = p.mask + (size_t)g * nx;
-    uint8_t* dst = st + Q * RB;
-    const URow<uint8_t> u = urow<uint8_t>((long long)g * nx, x0, width, nx);
-    urow_plain<uint8_t>(dst, row, u, x0, width, nx, j, 3);
-    if (j == 0 && u.hB > u.hA) {
-      bytes = (uint32_t)(u.hB - u.hA);
-      bsrc = row + (x0 + u.hA);
-      bdst = dst + u.hA + u.off;
-    }
+    const long long gm = (long long)g * nx + x0;
+    const int off = (int)(gm & 15);
+    bytes = (uint32_t)(((off + width + 15) / 16) * 16);
+    bsrc = p.mask + (gm - off);
+    bdst = st + Q * RB;
   }
   const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
   __syncwarp();  // the plain stores above are ordered before the arrive (release)
@@ -621,14 +634,14 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
 
 template <int S, bool MASKED, int NSTAGE, bool UNAL = false>
 constexpr size_t tma2_smem_bytes_c() {
-  return (size_t)NSTAGE * (Q * (TmaGeom2<S>::ROW_BYTES + (UNAL ? 16 : 0)) + (MASKED ? kBX2 + (UNAL ? 16 : 0) : 0)) +
+  return (size_t)NSTAGE * (Q * (TmaGeom2<S>::ROW_BYTES + (UNAL ? 32 : 0)) + (MASKED ? kBX2 + (UNAL ? 32 : 0) : 0)) +
          4 * (kBX2 + 4) * 4 + NSTAGE * 8 + 16;
 }
 
 template <int S, bool MASKED, int NSTAGE, bool UNAL = false>
 struct Tma2Smem {
-  static constexpr int RB = TmaGeom2<S>::ROW_BYTES + (UNAL ? 16 : 0);  // plane row stride
-  static constexpr int SLOT_BYTES = Q * RB + (MASKED ? kBX2 + (UNAL ? 16 : 0) : 0);
+  static constexpr int RB = TmaGeom2<S>::ROW_BYTES + (UNAL ? 32 : 0);  // plane row stride
+  static constexpr int SLOT_BYTES = Q * RB + (MASKED ? kBX2 + (UNAL ? 32 : 0) : 0);
   static constexpr int RW = kBX2 + 4;  // ring row: cell column c at index c + 2, halos at 1 and width + 2
   unsigned char* stages;
   float (*ring)[RW];
