@@ -1111,12 +1111,13 @@ template <int S, bool MASKED, bool TAU_ONE>
 cudaError_t launch_variant(const StepParams& p, cudaStream_t s) {
   const int v = p.force_generic;
   if ((v == 4 || v == 0) && tma2_ok<S>(p.nx)) return launch_dyn<S, MASKED, TAU_ONE>(p, s);
-  // automatic choice for other widths (measured at 2040-2056 columns): the
-  // unaligned staging where nx is even (FP16 2040^2: 0.086 ms against 0.103
-  // plain), the plain loads where it is odd (2047^2: 0.104 against 0.110;
-  // the helper warp's plain loads of each row's unaligned ends hold up
-  // every row)
-  if ((v == 4 || (v == 0 && p.nx % 2 == 0)) && tma2_unal_ok(p.nx)) return launch_dyn<S, MASKED, TAU_ONE, true>(p, s);
+  // automatic choice for other widths: the unaligned staging where the box
+  // has interior strips, whose windows arrive in one covering bulk copy
+  // (FP16 2047^2: 0.083 ms against 0.101 plain; 2040^2: 0.074 against 0.101),
+  // plain loads for boxes of at most two strips, whose every strip wraps and
+  // plain-loads its ends in the helper warp (1001^2: 0.035 plain against
+  // 0.039; 511^2: 0.020 against 0.026)
+  if ((v == 4 || (v == 0 && p.nx > 2 * kBX2)) && tma2_unal_ok(p.nx)) return launch_dyn<S, MASKED, TAU_ONE, true>(p, s);
   if (v == 3) {
     if (tma2_ok<S>(p.nx)) return launch_tma2<S, MASKED, TAU_ONE>(p, s);
     if (tma2_unal_ok(p.nx)) return launch_tma2<S, MASKED, TAU_ONE, true>(p, s);
