@@ -61,15 +61,16 @@ struct VOps<float> {
   static __device__ __forceinline__ int bad(float rho) { return !(rho > 0.f && rho < 1e30f); }
 };
 
+// The pair type uses the packed two-wide FP32 instructions of sm_100 and
+// later, whose rounding per component is that of the scalar intrinsics; a
+// difference is the fused b * (-1) + a, which rounds once, exactly as a - b.
 template <>
 struct VOps<float2> {
   static __device__ __forceinline__ float2 set(float a) { return make_float2(a, a); }
-  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
-  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
-  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
-  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
-    return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
-  }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
   static __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
   static __device__ __forceinline__ float2 ex(float2 a) { return make_float2(__expf(a.x), __expf(a.y)); }
   static __device__ __forceinline__ int bad(float2 rho) { return VOps<float>::bad(rho.x) | VOps<float>::bad(rho.y); }
