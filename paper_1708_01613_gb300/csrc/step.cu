@@ -882,20 +882,11 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_step_dyn(const StepParams
     __syncthreads();
     const int w = item_sh;
     if (w >= nitems) break;
-    // chunk order (measured): row-major for FP32; for 16-bit storage strip
-    // by strip, with the shorter last chunk row at the end (1.6 % faster)
-    int sx, cyk;
-    const int nch = (p.ny + rows - 1) / rows, full = gx * (nch - 1);
-    if (S == LBM_F32) {
-      sx = w % gx;
-      cyk = w / gx;
-    } else if (w < full) {
-      sx = w / (nch - 1);
-      cyk = w % (nch - 1);
-    } else {
-      sx = w - full;
-      cyk = nch - 1;
-    }
+    // row-major chunk order: the strips of a chunk row run together, so
+    // the halo columns a strip shares with its neighbours are read while
+    // still in L2 (measured for 16-bit storage at 8192^2 after the packed
+    // arithmetic: 0.459 ms strip by strip, 0.450 row-major)
+    const int sx = w % gx, cyk = w / gx;
     const int x0 = sx * kBX2, y0 = cyk * rows;
     const int y1 = min(y0 + rows, p.ny), width = min(kBX2, p.nx - x0);
     // full strips take the compile-time-width march (with tau != 1 the two
