@@ -623,14 +623,14 @@ __device__ __forceinline__ int find_entry(const RelabelEntry* __restrict__ e, in
   return lo;
 }
 
-// TWO: two-component boxes (FP32), which also get the mixture pressure; a
-// separate instantiation so that one-component relabels keep their register
-// budget.
+// One cell per thread. Used for two-component boxes (TWO, FP32), which also
+// get the mixture pressure; one-component boxes take the four-cell kernels
+// below, whose per-cell arithmetic is this kernel's.
 // Union-find inside one 32 x 8 tile in shared memory (local indices
 // ly * kTX + lx, -1 for liquid), hooking the larger root under the smaller,
 // so a root is the smallest local index of its piece. Bounded like the
 // global version.
-__device__ int tile_find(const int* sp, int a, int* fail) {
+__device__ __forceinline__ int tile_find(const int* sp, int a, int* fail) {
   for (int it = 0; it < kTX * kTY; ++it) {
     const int p = sp[a];
     if (p == a) return a;
@@ -640,7 +640,7 @@ __device__ int tile_find(const int* sp, int a, int* fail) {
   return a;
 }
 
-__device__ void tile_unite(int* sp, int a, int b, int* fail) {
+__device__ __forceinline__ void tile_unite(int* sp, int a, int b, int* fail) {
   for (int it = 0; it < kTX * kTY; ++it) {
     a = tile_find(sp, a, fail);
     b = tile_find(sp, b, fail);
@@ -739,105 +739,63 @@ __device__ __forceinline__ float dec16(unsigned short v) {
   else return __bfloat162float(__ushort_as_bfloat16(v));
 }
 
-// 16-bit storage: 16 x 8 threads per 32 x 8 tile, two cells (x, x + 1) per
-// thread from 32-bit loads, so a warp instruction moves 128 bytes as for
-// FP32. A plane the pull shifts by one column takes its pair (source columns
-// s, s + 1 with s odd) from the high half of one word and the low half of the
-// next; where the pull wraps around the box, from two 16-bit loads. Each
-// cell's arithmetic is kb_density_label's, so densities, labels and tile
-// flags are bitwise the same.
-template <int S>
-__global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const RelabelBox* __restrict__ boxes,
-                                                                    const RelabelEntry* __restrict__ e, int m,
-                                                                    int parity) {
-  const int k = find_entry<kOffTiles>(e, m, blockIdx.x);
-  const RelabelBox& B = boxes[e[k].box];
-  const int t = blockIdx.x - e[k].off_tiles;
-  const unsigned short* p = static_cast<const unsigned short*>(B.pops[B.cur ^ parity]);
-  const int nx = B.nx, ny = B.ny;
-  const size_t N = (size_t)nx * ny;
-  // whole tiles: nx % 32 == 0, so x is even and rows start on 4-byte
-  // boundaries (paired 32-bit loads); a box with ragged tiles loads cell by cell
-  const bool whole = nx % kTX == 0 && ny % kTY == 0;
-  const int x = (t % B.ntx) * kTX + 2 * threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
-  const bool ina = x < nx && y < ny, inb = x + 1 < nx && y < ny;
-  const int yi = y < ny ? y : 0;
-  const size_t r0 = (size_t)yi * nx, rm = (size_t)wrap1(yi - 1, ny) * nx, rp = (size_t)wrap1(yi + 1, ny) * nx;
-  float f0[Q], f1[Q];
-  if (whole) {
+// Four cells (x .. x + 3) of one tile row per thread, 8 x 8 threads per
+// 32 x 8 tile: the part after the densities r, shared by the vector density
+// kernels. Densities out, gas decision (rho < threshold), tile-local
+// union-find, the previous labels of gas cells kept for the coalescence
+// count, labels out, tile flags; the same results as kb_density_label's
+// one-cell threads. vec: the four cells lie inside the row and the row's
+// start is 16-byte aligned (one vector store each for densities and labels).
+__device__ __forceinline__ void density_label_tail4(const RelabelBox& B, int t, int x, int y, size_t c,
+                                                    const float (&r)[4], bool rowin, bool vec) {
+  float* const rho = B.rho;
+  int32_t* const label = B.label;
+  bool in[4], gas[4];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
-      const unsigned short* q = p + (size_t)i * N + row;
-      const int s = x - cx(i);  // cell x pulls from column s, cell x + 1 from s + 1
-      uint32_t bits;
-      if (cx(i) == 0) {
-        bits = __ldg(reinterpret_cast<const uint32_t*>(q + x));
-      } else if (s >= 0 && s + 1 < nx) {
-        const uint32_t* w = reinterpret_cast<const uint32_t*>(q);
-        bits = __byte_perm(__ldg(w + ((s - 1) >> 1)), __ldg(w + ((s + 1) >> 1)), 0x5432);
-      } else {
-        bits = (uint32_t)__ldg(q + wrap1(s, nx)) | ((uint32_t)__ldg(q + wrap1(s + 1, nx)) << 16);
-      }
-      f0[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)(bits & 0xffffu)));
-      f1[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)(bits >> 16)));
-    }
+  for (int j = 0; j < 4; ++j) {
+    in[j] = rowin && x + j < B.nx;
+    gas[j] = in[j] && r[j] < B.threshold;
+  }
+  if (vec) {
+    *reinterpret_cast<float4*>(rho + c) = make_float4(r[0], r[1], r[2], r[3]);
   } else {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
-      const unsigned short* q = p + (size_t)i * N + row;
-      const int s = x - cx(i);
-      const unsigned lo = ina ? __ldg(q + wrap1(s, nx)) : 0u, hi = inb ? __ldg(q + wrap1(s + 1, nx)) : 0u;
-      f0[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)lo));
-      f1[i] = __fadd_rn(B.wref[i], dec16<S>((unsigned short)hi));
-    }
+    for (int j = 0; j < 4; ++j)
+      if (in[j]) rho[c + j] = r[j];
   }
-  const float ra = ((f0[0] + f0[1]) + (f0[2] + f0[3])) + ((f0[4] + f0[5]) + (f0[6] + f0[7])) + f0[8];
-  const float rb = ((f1[0] + f1[1]) + (f1[2] + f1[3])) + ((f1[4] + f1[5]) + (f1[6] + f1[7])) + f1[8];
-  const size_t c = r0 + x;
-  if (whole) {
-    *reinterpret_cast<float2*>(B.rho + c) = make_float2(ra, rb);
-  } else {
-    if (ina) B.rho[c] = ra;
-    if (inb) B.rho[c + 1] = rb;
-  }
-  const bool ga = ina && ra < B.threshold, gb = inb && rb < B.threshold;
   __shared__ int sp[kTX * kTY];  // tile-local union-find, as in kb_density_label
-  const int la = threadIdx.y * kTX + 2 * threadIdx.x, lb = la + 1;
-  sp[la] = ga ? la : -1;
-  sp[lb] = gb ? lb : -1;
-  const int any = __syncthreads_or(ga || gb);
-  int32_t laba = -1, labb = -1;
+  const int la = threadIdx.y * kTX + 4 * threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sp[la + j] = gas[j] ? la + j : -1;
+  const int any = __syncthreads_or(gas[0] || gas[1] || gas[2] || gas[3]);
+  int32_t lab[4] = {-1, -1, -1, -1};
   if (any) {
     int fail = 0;
-    if (ga) {
-      if (gb) tile_unite(sp, la, lb, &fail);
-      if (threadIdx.y + 1 < kTY && sp[la + kTX] >= 0) tile_unite(sp, la, la + kTX, &fail);
-    }
-    if (gb) {
-      if (2 * threadIdx.x + 2 < kTX && sp[lb + 1] >= 0) tile_unite(sp, lb, lb + 1, &fail);
-      if (threadIdx.y + 1 < kTY && sp[lb + kTX] >= 0) tile_unite(sp, lb, lb + kTX, &fail);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!gas[j]) continue;
+      if (j < 3 ? gas[j + 1] : (4 * threadIdx.x + 4 < kTX && sp[la + 4] >= 0)) tile_unite(sp, la + j, la + j + 1, &fail);
+      if (threadIdx.y + 1 < kTY && sp[la + j + kTX] >= 0) tile_unite(sp, la + j, la + j + kTX, &fail);
     }
     __syncthreads();
-    const int x0 = x - 2 * threadIdx.x, y0 = y - threadIdx.y;
-    if (ga) laba = tile_root_index(sp, la, x0, y0, nx, &fail);
-    if (gb) labb = tile_root_index(sp, lb, x0, y0, nx, &fail);
+    const int x0 = x - 4 * threadIdx.x, y0 = y - threadIdx.y;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (gas[j]) lab[j] = tile_root_index(sp, la + j, x0, y0, B.nx, &fail);
     if (fail) atomicOr(B.flags + FLAG_TIMEOUT, 1);
   }
-  if (ga) {  // labels of the previous relabel, for the coalescence count
-    const int32_t o = B.label[c];
-    B.owner[c] = o >= 0 ? o : 0x7fffffff;
-  }
-  if (gb) {
-    const int32_t o = B.label[c + 1];
-    B.owner[c + 1] = o >= 0 ? o : 0x7fffffff;
-  }
-  if (whole) {
-    *reinterpret_cast<int2*>(B.label + c) = make_int2(laba, labb);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (gas[j]) {  // the label of the previous relabel, for the coalescence count
+      const int32_t o = label[c + j];
+      B.owner[c + j] = o >= 0 ? o : 0x7fffffff;
+    }
+  if (vec) {
+    *reinterpret_cast<int4*>(label + c) = make_int4(lab[0], lab[1], lab[2], lab[3]);
   } else {
-    if (ina) B.label[c] = laba;
-    if (inb) B.label[c + 1] = labb;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (in[j]) label[c + j] = lab[j];
   }
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     B.tile_gas[t] = (uint8_t)(any != 0);
@@ -846,6 +804,140 @@ __global__ void __launch_bounds__(kTX / 2 * kTY) kb_density_label16(const Relabe
       B.flags[FLAG_FILM] = 0;
     }
   }
+}
+
+// Sum of the nine pulled values in kb_density_label's order, for two cells
+// at once (the packed adds round per component like the scalar ones).
+__device__ __forceinline__ float2 rho_pair(const float2 (&f)[Q]) {
+  return __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(f[0], f[1]), __fadd2_rn(f[2], f[3])),
+                               __fadd2_rn(__fadd2_rn(f[4], f[5]), __fadd2_rn(f[6], f[7]))),
+                    f[8]);
+}
+
+// One-component FP32 storage, four cells per thread. Where the box's rows
+// start on 16-byte boundaries (nx % 4 == 0) and the cells and the columns
+// they pull from lie inside the row, a plane arrives in one 16-byte load, a
+// plane the pull shifts by one column adds the value beside it; other cells
+// (the box's first and last columns, ragged tiles, other widths) load one by
+// one with the periodic wrap.
+__global__ void __launch_bounds__(kTX / 4 * kTY, 16) kb_density_label32(const RelabelBox* __restrict__ boxes,
+                                                                        const RelabelEntry* __restrict__ e, int m,
+                                                                        int parity) {
+  const int k = find_entry<kOffTiles>(e, m, blockIdx.x);
+  const RelabelBox& B = boxes[e[k].box];
+  const int t = blockIdx.x - e[k].off_tiles;
+  const float* p = static_cast<const float*>(B.pops[B.cur ^ parity]);
+  const int nx = B.nx, ny = B.ny;
+  const size_t N = (size_t)nx * ny;
+  const int x = (t % B.ntx) * kTX + 4 * threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+  const bool rowin = y < ny;
+  const int yi = rowin ? y : 0;
+  const size_t r0 = (size_t)yi * nx, rm = (size_t)wrap1(yi - 1, ny) * nx, rp = (size_t)wrap1(yi + 1, ny) * nx;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(B.rho) |
+                         reinterpret_cast<uintptr_t>(B.label)) & 15u) == 0;
+  const bool vec = rowin && aligned && (nx & 3) == 0 && x >= 1 && x + 5 <= nx;  // columns x - 1 .. x + 4
+  float2 fa[Q], fb[Q];  // cells (x, x + 1) and (x + 2, x + 3)
+  if (vec) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+      const float* q = p + (size_t)i * N + row + x;
+      const float4 w = __ldg(reinterpret_cast<const float4*>(q));  // columns x .. x + 3
+      if (cx(i) > 0) {  // columns x - 1 .. x + 2
+        fa[i] = make_float2(__ldg(q - 1), w.x);
+        fb[i] = make_float2(w.y, w.z);
+      } else if (cx(i) < 0) {  // columns x + 1 .. x + 4
+        fa[i] = make_float2(w.y, w.z);
+        fb[i] = make_float2(w.w, __ldg(q + 4));
+      } else {
+        fa[i] = make_float2(w.x, w.y);
+        fb[i] = make_float2(w.z, w.w);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+      const float* q = p + (size_t)i * N + row;
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = rowin && x + j < nx ? __ldg(q + wrap1(x + j - cx(i), nx)) : 0.f;
+      fa[i] = make_float2(v[0], v[1]);
+      fb[i] = make_float2(v[2], v[3]);
+    }
+  }
+  const float2 ra = rho_pair(fa), rb = rho_pair(fb);
+  const float r[4] = {ra.x, ra.y, rb.x, rb.y};
+  density_label_tail4(B, t, x, y, r0 + x, r, rowin, vec);
+}
+
+// 16-bit storage, four cells per thread. Where the box's rows start on
+// 8-byte boundaries (nx % 4 == 0) and the four cells and the columns they
+// pull from lie inside the row, a plane arrives in one 8-byte load; a plane
+// the pull shifts by one column adds the 4-byte word beside it, and its
+// pairs (source columns s, s + 1 with s odd) are the high half of one word
+// and the low half of the next. Other cells load element by element with
+// the periodic wrap. Each cell's arithmetic is kb_density_label's, so
+// densities, labels and tile flags are bitwise the same.
+template <int S>
+__device__ __forceinline__ float2 dec16x2(uint32_t bits) {
+  return make_float2(dec16<S>((unsigned short)(bits & 0xffffu)), dec16<S>((unsigned short)(bits >> 16)));
+}
+
+template <int S>
+__global__ void __launch_bounds__(kTX / 4 * kTY, 16) kb_density_label16(const RelabelBox* __restrict__ boxes,
+                                                                        const RelabelEntry* __restrict__ e, int m,
+                                                                        int parity) {
+  const int k = find_entry<kOffTiles>(e, m, blockIdx.x);
+  const RelabelBox& B = boxes[e[k].box];
+  const int t = blockIdx.x - e[k].off_tiles;
+  const unsigned short* p = static_cast<const unsigned short*>(B.pops[B.cur ^ parity]);
+  const int nx = B.nx, ny = B.ny;
+  const size_t N = (size_t)nx * ny;
+  const int x = (t % B.ntx) * kTX + 4 * threadIdx.x, y = (t / B.ntx) * kTY + threadIdx.y;
+  const bool rowin = y < ny;
+  const int yi = rowin ? y : 0;
+  const size_t r0 = (size_t)yi * nx, rm = (size_t)wrap1(yi - 1, ny) * nx, rp = (size_t)wrap1(yi + 1, ny) * nx;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(B.rho) |
+                         reinterpret_cast<uintptr_t>(B.label)) & 15u) == 0;
+  const bool vec = rowin && aligned && (nx & 3) == 0 && x >= 2 && x + 6 <= nx;  // columns x - 2 .. x + 5
+  float2 fa[Q], fb[Q];  // cells (x, x + 1) and (x + 2, x + 3)
+  if (vec) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+      const unsigned short* q = p + (size_t)i * N + row + x;
+      const uint2 w = __ldg(reinterpret_cast<const uint2*>(q));  // columns x .. x + 3
+      uint32_t lo = w.x, hi = w.y;
+      if (cx(i) > 0) {  // columns x - 1 .. x + 2
+        const uint32_t wm = __ldg(reinterpret_cast<const uint32_t*>(q - 2));
+        lo = __byte_perm(wm, w.x, 0x5432);
+        hi = __byte_perm(w.x, w.y, 0x5432);
+      } else if (cx(i) < 0) {  // columns x + 1 .. x + 4
+        const uint32_t wp = __ldg(reinterpret_cast<const uint32_t*>(q + 4));
+        lo = __byte_perm(w.x, w.y, 0x5432);
+        hi = __byte_perm(w.y, wp, 0x5432);
+      }
+      const float2 wr = make_float2(B.wref[i], B.wref[i]);
+      fa[i] = __fadd2_rn(wr, dec16x2<S>(lo));
+      fb[i] = __fadd2_rn(wr, dec16x2<S>(hi));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const size_t row = cy(i) > 0 ? rm : (cy(i) < 0 ? rp : r0);
+      const unsigned short* q = p + (size_t)i * N + row;
+      unsigned v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = rowin && x + j < nx ? __ldg(q + wrap1(x + j - cx(i), nx)) : 0u;
+      const float2 wr = make_float2(B.wref[i], B.wref[i]);
+      fa[i] = __fadd2_rn(wr, dec16x2<S>(v[0] | (v[1] << 16)));
+      fb[i] = __fadd2_rn(wr, dec16x2<S>(v[2] | (v[3] << 16)));
+    }
+  }
+  const float2 ra = rho_pair(fa), rb = rho_pair(fb);
+  const float r[4] = {ra.x, ra.y, rb.x, rb.y};
+  density_label_tail4(B, t, x, y, r0 + x, r, rowin, vec);
 }
 
 // Also appends every tile that needs a visit (active now or at the previous
@@ -1365,12 +1457,12 @@ cudaError_t launch_relabel_boxes(int storage, const RelabelBox* boxes, const Rel
     kb_density_label<LBM_F32, true><<<totals[0], block, 0, s>>>(boxes, entries, m, parity);
   } else {
     switch (storage) {
-      case LBM_F32: kb_density_label<LBM_F32, false><<<totals[0], block, 0, s>>>(boxes, entries, m, parity); break;
+      case LBM_F32: kb_density_label32<<<totals[0], dim3(kTX / 4, kTY), 0, s>>>(boxes, entries, m, parity); break;
       case LBM_F16_DEV:
-        kb_density_label16<LBM_F16_DEV><<<totals[0], dim3(kTX / 2, kTY), 0, s>>>(boxes, entries, m, parity);
+        kb_density_label16<LBM_F16_DEV><<<totals[0], dim3(kTX / 4, kTY), 0, s>>>(boxes, entries, m, parity);
         break;
       case LBM_BF16_DEV:
-        kb_density_label16<LBM_BF16_DEV><<<totals[0], dim3(kTX / 2, kTY), 0, s>>>(boxes, entries, m, parity);
+        kb_density_label16<LBM_BF16_DEV><<<totals[0], dim3(kTX / 4, kTY), 0, s>>>(boxes, entries, m, parity);
         break;
       default: return cudaErrorInvalidValue;
     }
