@@ -63,10 +63,12 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-growth", action="store_true", help="skip the nucleation/growth leg")
     ap.add_argument("--no-2c", action="store_true", help="skip the two-component leg")
-    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-requests", type=int, default=192)
     ap.add_argument("--serve-step-scale", type=float, default=0.1)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
-    ap.add_argument("--serve-policy", default="tiered", choices=["work", "time", "lockstep", "tiered"])
+    ap.add_argument("--serve-policy", default="srpt", choices=["work", "time", "lockstep", "tiered", "fifo", "srpt"])
+    ap.add_argument("--serve-age-weight", type=float, default=0.5,
+                    help="srpt policy: requests are ordered by remaining GPU time minus this times the time waited")
     ap.add_argument("--serve-big-s", type=float, default=0.02,
                     help="tiered policy: requests with more GPU time left than this are served first come, first served")
     ap.add_argument("--serve-big-slowdown", type=float, default=float("inf"),
@@ -436,7 +438,8 @@ def run_served(args, dev, world, rank, capacity_ups):
     torch.cuda.synchronize(dev)
     server = FoamServer(memory_budget_bytes=int(args.serve_budget_gb * 2**30), max_boxes=32, device=str(dev),
                         policy=args.serve_policy, big_s=args.serve_big_s, small_share=args.serve_small_share,
-                        big_slowdown=args.serve_big_slowdown, late_share=args.serve_late_share)
+                        big_slowdown=args.serve_big_slowdown, late_share=args.serve_late_share,
+                        age_weight=args.serve_age_weight)
     served = summarize(server.run(reqs), server.stats["makespan_s"])
     alone_res, alone_span = run_one_at_a_time(reqs, device=str(dev))
     alone = summarize(alone_res, alone_span)
@@ -450,7 +453,7 @@ def run_served(args, dev, world, rank, capacity_ups):
             "step_scale": scale, "rate_per_s": round(rate, 3), "memory_budget_gb": args.serve_budget_gb,
             "policy": server.policy, "big_s": server.big_s, "small_share": server.small_share,
             "big_slowdown": server.big_slowdown, "late_share": server.late_share,
-            "quantum_s": server.quantum_s,
+            "age_weight": server.age_weight, "quantum_s": server.quantum_s,
             "p50_s": served["p50_s"], "p99_s": served["p99_s"], "mean_s": served["mean_s"],
             "p50_by_size_s": served["p50_by_size_s"], "mlups": served["mlups"],
             "makespan_s": served["makespan_s"], "batch_rebuilds": server.stats["batch_rebuilds"],

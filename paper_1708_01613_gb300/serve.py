@@ -156,6 +156,24 @@ def tiered_steps(jobs: list[_Job], budget_updates: float, big_updates: float, sm
     return out
 
 
+def ordered_steps(jobs: list[_Job], budget_updates: float, key) -> dict[int, int]:
+    """Greedy fill in the order `key`: each job in turn takes all its
+    remaining steps, or as many as the cell-update budget still allows (at
+    least one step for the first job of the order); the jobs after the
+    budget runs out wait (0 steps). With `key` the arrival this is first
+    come, first served with batching; with the remaining work it is shortest
+    remaining processing time first."""
+    out = {j.req.rid: 0 for j in jobs}
+    left = float(budget_updates)
+    for k, j in enumerate(sorted(jobs, key=key)):
+        if left <= 0.0 and k > 0:
+            break
+        s = min(j.remaining, max(1, int(left // j.cells)))
+        out[j.req.rid] = s
+        left -= s * j.cells
+    return out
+
+
 def _water_fill(jobs: list[_Job], budget: float, cost) -> dict[int, int]:
     out: dict[int, int] = {}
     left = float(budget)
@@ -197,7 +215,10 @@ class FoamServer:
     `quantum_updates` fixes the budget), "time" shares GPU time counting a
     launch cost per step (`fair_time_steps`), "lockstep" steps every box in
     every launch (`lockstep_steps`), "tiered" serves big jobs first come,
-    first served beside equally shared small ones (`tiered_steps`), and
+    first served beside equally shared small ones (`tiered_steps`), "fifo"
+    and "srpt" fill each quantum in arrival or shortest-remaining-work order
+    (`ordered_steps`; "srpt" credits each job `age_weight` times the time
+    it has waited, so the largest jobs are not starved), and "tiered"
     cuts the small ones' share to `late_share` while the oldest big job's
     projected latency exceeds `big_slowdown` times its work alone. Every batch runs its plan as multi-rate
     steps (lbm_batch_step_each), so small boxes can take many cheap steps
@@ -206,12 +227,13 @@ class FoamServer:
     max_boxes: int = 64
     quantum_s: float = 0.01
     quantum_updates: float | None = None
-    policy: str = "work"            # "work" | "time" | "lockstep" | "tiered"
+    policy: str = "work"            # "work" | "time" | "lockstep" | "tiered" | "fifo" | "srpt"
     big_s: float = 0.05             # "tiered": a job with more work left than this much GPU time is big
     small_share: float = 0.5        # "tiered": most of a quantum the small jobs take while a big one runs
     big_slowdown: float = float("inf")  # "tiered": once the oldest big job's projected latency exceeds
                                         # this many times its work alone, the small jobs' share is
     late_share: float = 0.0             # cut to late_share (they still move a step per quantum)
+    age_weight: float = 0.0         # "srpt": order by remaining GPU time minus this times the time waited
     device: str = "cuda"
     keep_pops: bool = False
     stats: dict = field(default_factory=dict)
@@ -283,6 +305,14 @@ class FoamServer:
                 share = fair_time_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
             elif self.policy == "lockstep":
                 share = lockstep_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
+            elif self.policy in ("fifo", "srpt"):
+                budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
+                if self.policy == "fifo":
+                    key = lambda j: (j.req.arrival_s, j.req.rid)
+                else:  # remaining GPU time, less `age_weight` times the time waited so far
+                    spu, a = model.s_per_update, self.age_weight
+                    key = lambda j: (j.remaining * j.cells * spu - a * (now - j.req.arrival_s), j.req.arrival_s, j.req.rid)
+                share = ordered_steps(jobs_now, budget, key)
             elif self.policy == "tiered":
                 budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
                 big_updates = self.big_s / model.s_per_update

@@ -100,6 +100,28 @@ def test_tiered_plan():
     assert late[2] == int((4e6 - 100 - 1000) // 10**6)
 
 
+def test_ordered_fill_plans():
+    """Pure host logic of the "fifo" and "srpt" policies: jobs take all their
+    remaining steps in the given order until the update budget runs out; the
+    first job in the order always moves; the rest wait."""
+    from paper_1708_01613_gb300.serve import _Job, ordered_steps
+
+    def job(rid, t, cells, rem):
+        return _Job(Request(rid, t, cells, 1, np.zeros((0, 3)), rem), None, rem, 0.0, 0)
+
+    jobs = [job(0, 0.2, 100, 10), job(1, 0.1, 10**6, 1000), job(2, 0.0, 10**6, 3), job(3, 0.3, 1000, 10**4)]
+    fifo = ordered_steps(jobs, 4e6, key=lambda j: (j.req.arrival_s, j.req.rid))
+    # job 2 (first) takes its 3 steps (3e6 updates), job 1 the one step that
+    # fits the last 1e6; jobs 0 and 3 wait
+    assert fifo == {2: 3, 1: 1, 0: 0, 3: 0}
+    srpt = ordered_steps(jobs, 4e6, key=lambda j: j.remaining * j.cells)
+    # by remaining work: job 0 (1e3), job 2 (3e6), job 3 (1e7: 999 steps of
+    # the 999000 left), job 1 nothing
+    assert srpt == {0: 10, 2: 3, 3: 999, 1: 0}
+    assert ordered_steps(jobs, 0.0, key=lambda j: j.req.rid) == {0: 1, 1: 0, 2: 0, 3: 0}
+    assert sum(srpt[j.req.rid] * j.cells for j in jobs) <= 4e6
+
+
 @pytest.mark.gpu
 def test_request_larger_than_budget_is_refused():
     r = requests()[3]
