@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=192)
     ap.add_argument("--serve-step-scale", type=float, default=0.1)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
-    ap.add_argument("--serve-policy", default="srpt", choices=["work", "time", "lockstep", "tiered", "fifo", "srpt"])
+    ap.add_argument("--serve-policy", default="hrrn", choices=["work", "time", "lockstep", "tiered", "fifo", "srpt", "hrrn"])
     ap.add_argument("--serve-age-weight", type=float, default=0.5,
                     help="srpt policy: requests are ordered by remaining GPU time minus this times the time waited")
     ap.add_argument("--serve-big-s", type=float, default=0.02,

@@ -332,6 +332,15 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps);
  * counter advances by the largest nsteps[i]. */
 int lbm_batch_step_each(lbm_batch* b, const int64_t* nsteps, int32_t n);
 
+/* Advances box `index` alone by nsteps steps through the single-box path
+ * (lbm_step: its own kernels and relabels, no batch launches), ordered after
+ * the batch's earlier work, with the batch's later work ordered after it; the
+ * batch re-reads the box's time and buffer parity at its next step call, and
+ * drops its captured graphs. For a server step in which one box of the batch
+ * moves. Errors: LBM_EINVAL (index out of range, nsteps < 0), or the box's
+ * own step error. Asynchronous. */
+int lbm_batch_step_one(lbm_batch* b, int32_t index, int64_t nsteps);
+
 /* Synchronises the batch stream and reports device faults of any box. */
 int lbm_batch_sync(lbm_batch* b);
 

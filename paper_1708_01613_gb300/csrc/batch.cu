@@ -538,6 +538,26 @@ int lbm_batch_set_active(lbm_batch* b, int32_t index, int active) {
   return LBM_OK;
 }
 
+int lbm_batch_step_one(lbm_batch* b, int32_t index, int64_t nsteps) {
+  if (!b) return LBM_EINVAL;
+  if (index < 0 || index >= b->n) return bfail(b, LBM_EINVAL, "index out of range");
+  if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps < 0");
+  lbm_handle* h = b->h[index];
+  // after the batch's earlier work, on the box's own stream; the batch's
+  // later work after this (its next upload re-reads time and parity)
+  BCUDA(b, cudaEventRecord(b->ev_out, b->stream));
+  BCUDA(b, cudaStreamWaitEvent(h->stream, b->ev_out, 0));
+  h->in_batch = 0;
+  const int rc = lbm_step(h, nsteps);
+  h->in_batch = 1;
+  b->dirty = 1;
+  drop_graphs(b);
+  if (rc) return bfail(b, rc, "box %d: %s", index, h->err);
+  BCUDA(b, cudaEventRecord(b->ev_in, h->stream));
+  BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+  return LBM_OK;
+}
+
 int lbm_batch_use_graph(lbm_batch* b, int enable) {
   if (!b) return LBM_EINVAL;
   b->use_graph = enable ? 1 : 0;

@@ -507,48 +507,21 @@ __device__ __forceinline__ void copy_row_wrapped3(T* dst, const T* row, int star
 // of the two-cell march): a staged row keeps window element e at slot
 // position e + off, where off = (index of window element 0 in the buffer,
 // plane offset i N included) mod M (M = elements per 16 bytes). A window
-// that does not wrap around the periodic row arrives in one bulk copy of the
-// 16-byte-aligned span that covers it (up to M - 1 elements on either side
-// land in the slot's slack and are never read); the mask row likewise. A
-// window that wraps (the box's first and last strips) takes its aligned
-// interior by bulk copy and the rest of what the march reads (its head and
-// tail, and the two halo elements on a wrapped side) by plain loads of the
-// helper lanes. A row slot holds 2 M more elements.
-template <typename T>
-struct URow {
-  int off;  // slot position of window element 0
-  int hA;   // window elements [0, hA) and [hB, len) come by plain loads,
-  int hB;   // [hA, hB) by one bulk copy
+// arrives in one bulk copy of the 16-byte-aligned span that covers its part
+// inside the periodic row (up to M - 1 elements on either side land in the
+// slot's slack and are never read); the mask row likewise. Where the window
+// wraps (the box's first strip, and the strips that reach its last column),
+// the two elements on a wrapped side that the march reads come by plain
+// loads into a side area of the slot. A row slot holds 2 M more elements.
+// Layout of one stage slot of the two-cell march: nine plane rows of RB bytes,
+// the mask row, and (UNAL) a side area of four elements per plane for the
+// window elements of a wrapped window that the staged rows cannot hold.
+template <int S, bool MASKED, bool UNAL>
+struct Slot2 {
+  static constexpr int RB = TmaGeom2<S>::ROW_BYTES + (UNAL ? 32 : 0);  // plane row stride
+  static constexpr int SIDE_OFF = Q * RB + (MASKED ? kBX2 + (UNAL ? 32 : 0) : 0);
+  static constexpr int BYTES = SIDE_OFF + (UNAL ? (Q * 4 * TmaGeom2<S>::E + 15) / 16 * 16 : 0);
 };
-
-// gbase: buffer index of the row's column 0 (plane offset included).
-template <typename T>
-__device__ __forceinline__ URow<T> urow(long long gbase, int c0, int len, int nx) {
-  constexpr int M = 16 / (int)sizeof(T);
-  URow<T> u;
-  u.off = (int)((gbase + c0 + M) & (M - 1));  // gbase + c0 >= -M
-  const int a = c0 > 0 ? c0 : 0, b = c0 + len < nx ? c0 + len : nx;  // columns inside the row
-  long long iA = (gbase + a + M - 1) / M * M, iB = (gbase + b) / M * M;
-  if (iA >= iB) iA = iB = gbase + b;  // no aligned interior: all plain
-  u.hA = (int)(iA - gbase) - c0;
-  u.hB = (int)(iB - gbase) - c0;
-  return u;
-}
-
-// Plain loads of the elements kk = j, j + step, ... of a row's plain part,
-// limited to the window elements [lo, hi) the march reads.
-template <typename T>
-__device__ __forceinline__ void urow_plain(T* dst, const T* row, const URow<T>& u, int c0, int lo, int hi, int nx,
-                                           int j, int step) {
-  const int n1 = u.hA > lo ? u.hA - lo : 0;
-  const int np = n1 + (hi > u.hB ? hi - u.hB : 0);
-  for (int kk = j; kk < np; kk += step) {
-    const int e = kk < n1 ? lo + kk : u.hB + (kk - n1);
-    int c = (c0 + e) % nx;
-    c = c < 0 ? c + nx : c;
-    dst[e + u.off] = row[c];
-  }
-}
 
 // One stage of the two-cell march: for output row r = y0 - 1 + k, plane i's
 // source row r - c_iy, columns x0 - PAD .. x0 + width + PAD (wrapped), and the
@@ -559,8 +532,8 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
                                              int x0, int width, int lane) {
   using G = TmaGeom2<S>;
   using T = typename G::T;
-  constexpr int RB = G::ROW_BYTES + (UNAL ? 32 : 0);  // plane row stride in a slot
-  constexpr uint32_t SLOT_BYTES = Q * RB + (MASKED ? kBX2 + (UNAL ? 32 : 0) : 0);
+  constexpr int RB = Slot2<S, MASKED, UNAL>::RB;  // plane row stride in a slot
+  constexpr uint32_t SLOT_BYTES = Slot2<S, MASKED, UNAL>::BYTES;
   const int len = width + 2 * G::PAD;
   const int slot = (int)(gk % NSTAGE);
   unsigned char* st = stages + (size_t)slot * SLOT_BYTES;
@@ -609,12 +582,27 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
         bdst = dst;
       }
     } else {
-      const URow<T> u = urow<T>(gbase, c0, len, nx);
-      urow_plain<T>(dst, row, u, c0, G::PAD - 2, len - G::PAD + 2, nx, j, 3);
-      if (j == 0 && u.hB > u.hA) {
-        bytes = (uint32_t)((u.hB - u.hA) * G::E);
-        bsrc = row + (c0 + u.hA);
-        bdst = dst + u.hA + u.off;
+      // the window wraps around the periodic row: its part inside the row
+      // by one covering copy, whose slot start a + off - ra is a multiple of
+      // M (0, or M after a left wrap); the wrapped elements the march reads
+      // (two on a wrapped side) by plain loads into the side area, since
+      // the copy's slack may cover their slot positions
+      const int off = (int)((gbase + c0 + M) & (M - 1));  // gbase + c0 >= -M
+      const int a = c0 < 0 ? -c0 : 0, b = c0 + len > nx ? nx - c0 : len;
+      const long long ga = gbase + c0 + a;  // buffer index of the first element inside the row
+      const int ra = (int)(ga & (M - 1));
+      T* side = reinterpret_cast<T*>(st + Slot2<S, MASKED, UNAL>::SIDE_OFF) + 4 * q;
+      if (j == 0) {
+        const long long gend = gbase + c0 + b;  // one past the last element inside the row
+        bytes = (uint32_t)(((gend + M - 1) / M * M - (ga - ra)) * G::E);
+        bsrc = row + (c0 + a - ra);
+        bdst = dst + (a + off - ra);
+      } else if (j == 1 && a > 0) {  // window elements PAD - 2, PAD - 1: columns nx - 2, nx - 1
+        side[0] = row[nx - 2];
+        side[1] = row[nx - 1];
+      } else if (j == 2 && b < len) {  // window elements b, b + 1: columns 0, 1
+        side[2] = row[0];
+        side[3] = row[1];
       }
     }
   } else if (MASKED && q == Q && j == 0) {
@@ -635,14 +623,13 @@ __device__ __forceinline__ void issue_stage2(const StepParams& p, const typename
 
 template <int S, bool MASKED, int NSTAGE, bool UNAL = false>
 constexpr size_t tma2_smem_bytes_c() {
-  return (size_t)NSTAGE * (Q * (TmaGeom2<S>::ROW_BYTES + (UNAL ? 32 : 0)) + (MASKED ? kBX2 + (UNAL ? 32 : 0) : 0)) +
-         4 * (kBX2 + 4) * 4 + NSTAGE * 8 + 16;
+  return (size_t)NSTAGE * Slot2<S, MASKED, UNAL>::BYTES + 4 * (kBX2 + 4) * 4 + NSTAGE * 8 + 16;
 }
 
 template <int S, bool MASKED, int NSTAGE, bool UNAL = false>
 struct Tma2Smem {
-  static constexpr int RB = TmaGeom2<S>::ROW_BYTES + (UNAL ? 32 : 0);  // plane row stride
-  static constexpr int SLOT_BYTES = Q * RB + (MASKED ? kBX2 + (UNAL ? 32 : 0) : 0);
+  static constexpr int RB = Slot2<S, MASKED, UNAL>::RB;  // plane row stride
+  static constexpr int SLOT_BYTES = Slot2<S, MASKED, UNAL>::BYTES;
   static constexpr int RW = kBX2 + 4;  // ring row: cell column c at index c + 2, halos at 1 and width + 2
   unsigned char* stages;
   float (*ring)[RW];
@@ -692,6 +679,12 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
 
   const int jc = 2 * tid + 2;        // ring index of the first cell of the pair
   const int pos = G::PAD + 2 * tid;  // window position of the first cell
+  // UNAL: window elements [PAD - 2, ea) and [eb, eb + 2) of a wrapped window
+  // are read from the stage's side area (thread 0 after a left wrap, the
+  // last pair before a right wrap, and the halo lanes)
+  const int ea = UNAL && x0 < G::PAD ? G::PAD - x0 : 0;
+  const int eb = UNAL && x0 + width + G::PAD > nx ? nx - x0 + G::PAD : (1 << 30);
+  const bool fixw = UNAL && active && ((tid == 0 && ea > 0) || pos + 2 >= eb);
   float2 fprev[Q];
   float2 rho_prev = make_float2(1.f, 1.f), jx_prev = make_float2(0.f, 0.f), jy_prev = make_float2(0.f, 0.f);
   unsigned m_prev = 0;
@@ -723,6 +716,13 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
           const int off = ((cy(i) > 0 ? bm : (cy(i) < 0 ? bp : b0)) + (int)((i * p.N) & (M - 1))) & (M - 1);
           const int q = pos - cx(i) + off;
           f[i] = load_pair<S>(st + i * RB, q, q & 1);
+          if (fixw) {
+            const T* sd = reinterpret_cast<const T*>(st + Slot2<S, MASKED, UNAL>::SIDE_OFF) + 4 * i;
+            const int e0 = pos - cx(i);
+            if (e0 < ea) f[i].x = Store<S>::raw_smem(sd, e0 - (G::PAD - 2));
+            if (e0 >= eb) f[i].x = Store<S>::raw_smem(sd, 2 + e0 - eb);
+            if (e0 + 1 >= eb) f[i].y = Store<S>::raw_smem(sd, 3 + e0 - eb);
+          }
         } else {
           f[i] = load_pair<S>(st + i * RB, pos - cx(i), cx(i));
         }
@@ -740,8 +740,11 @@ __device__ __forceinline__ bool march2(const StepParams& p, const Tma2Smem<S, MA
     } else if (helper) {
       const int ho =
           UNAL ? ((hcy > 0 ? bm : (hcy < 0 ? bp : b0)) + (int)((hplane * p.N) & (M - 1))) & (M - 1) : 0;
-      const float v =
-          hlane ? Store<S>::raw_smem(reinterpret_cast<const T*>(st + hplane * RB), hpos + ho) : 0.f;
+      float v = hlane ? Store<S>::raw_smem(reinterpret_cast<const T*>(st + hplane * RB), hpos + ho) : 0.f;
+      if (UNAL && hlane && (hpos < ea || hpos >= eb)) {
+        const T* sd = reinterpret_cast<const T*>(st + Slot2<S, MASKED, UNAL>::SIDE_OFF) + 4 * hplane;
+        v = Store<S>::raw_smem(sd, hpos < ea ? hpos - (G::PAD - 2) : 2 + hpos - eb);
+      }
       const float t1 = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, 1));
       const float t2 = __fadd_rn(t1, __shfl_xor_sync(0xffffffffu, t1, 2));
       const float t3 = __fadd_rn(t2, __shfl_xor_sync(0xffffffffu, t2, 4));

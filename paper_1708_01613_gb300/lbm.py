@@ -93,6 +93,7 @@ SIGNATURES = {
     "lbm_batch_set_active": (C.c_int, [_vp, C.c_int32, C.c_int]),
     "lbm_batch_step": (C.c_int, [_vp, C.c_int64]),
     "lbm_batch_step_each": (C.c_int, [_vp, _vp, C.c_int32]),
+    "lbm_batch_step_one": (C.c_int, [_vp, C.c_int32, C.c_int64]),
     "lbm_batch_sync": (C.c_int, [_vp]),
     "lbm_batch_steps_done": (C.c_int64, [_vp]),
     "lbm_batch_kernel_launches": (C.c_int64, [_vp]),
@@ -428,6 +429,10 @@ class Batch:
         if a.shape != (len(self.sims),):
             raise LbmError(LBM_EINVAL, f"need {len(self.sims)} step counts")
         self._call("lbm_batch_step_each", C.c_void_p(a.ctypes.data), len(self.sims))
+
+    def step_one(self, index: int, n: int) -> None:
+        """Box `index` advances n steps alone (its own step path), asynchronously."""
+        self._call("lbm_batch_step_one", int(index), C.c_int64(int(n)))
 
     def sync(self) -> None:
         self._call("lbm_batch_sync")

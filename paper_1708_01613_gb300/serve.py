@@ -218,7 +218,8 @@ class FoamServer:
     first served beside equally shared small ones (`tiered_steps`), "fifo"
     and "srpt" fill each quantum in arrival or shortest-remaining-work order
     (`ordered_steps`; "srpt" credits each job `age_weight` times the time
-    it has waited, so the largest jobs are not starved), and "tiered"
+    it has waited, so the largest jobs are not starved), "hrrn" fills it in
+    order of the ratio of time since arrival to remaining work, and "tiered"
     cuts the small ones' share to `late_share` while the oldest big job's
     projected latency exceeds `big_slowdown` times its work alone. Every batch runs its plan as multi-rate
     steps (lbm_batch_step_each), so small boxes can take many cheap steps
@@ -227,7 +228,7 @@ class FoamServer:
     max_boxes: int = 64
     quantum_s: float = 0.01
     quantum_updates: float | None = None
-    policy: str = "work"            # "work" | "time" | "lockstep" | "tiered" | "fifo" | "srpt"
+    policy: str = "work"            # "work" | "time" | "lockstep" | "tiered" | "fifo" | "srpt" | "hrrn"
     big_s: float = 0.05             # "tiered": a job with more work left than this much GPU time is big
     small_share: float = 0.5        # "tiered": most of a quantum the small jobs take while a big one runs
     big_slowdown: float = float("inf")  # "tiered": once the oldest big job's projected latency exceeds
@@ -305,13 +306,17 @@ class FoamServer:
                 share = fair_time_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
             elif self.policy == "lockstep":
                 share = lockstep_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
-            elif self.policy in ("fifo", "srpt"):
+            elif self.policy in ("fifo", "srpt", "hrrn"):
                 budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
+                spu = model.s_per_update
                 if self.policy == "fifo":
                     key = lambda j: (j.req.arrival_s, j.req.rid)
-                else:  # remaining GPU time, less `age_weight` times the time waited so far
-                    spu, a = model.s_per_update, self.age_weight
+                elif self.policy == "srpt":  # remaining GPU time, less `age_weight` times the time waited
+                    a = self.age_weight
                     key = lambda j: (j.remaining * j.cells * spu - a * (now - j.req.arrival_s), j.req.arrival_s, j.req.rid)
+                else:  # highest response ratio (time since arrival over remaining GPU time) first
+                    key = lambda j: (-(now - j.req.arrival_s) / max(j.remaining * j.cells * spu, 1e-9),
+                                     j.req.arrival_s, j.req.rid)
                 share = ordered_steps(jobs_now, budget, key)
             elif self.policy == "tiered":
                 budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
@@ -334,7 +339,13 @@ class FoamServer:
             live = []
             for b, jobs in batches.values():
                 plan = [share.get(j.req.rid, 0) if j.remaining > 0 else 0 for j in jobs]
-                if any(plan):
+                movers = [i for i, n in enumerate(plan) if n > 0]
+                if len(movers) == 1:
+                    # a single box moves: its own step path, which a batch's per-step
+                    # launches only slow down
+                    b.step_one(movers[0], plan[movers[0]])
+                    live.append((b, jobs, plan))
+                elif movers:
                     b.step_each(plan)  # each batch on its own stream: the storage classes overlap
                     live.append((b, jobs, plan))
             for b, _, _ in live:

@@ -131,6 +131,35 @@ def test_step_each_multi_rate_bitwise(storage):
     b.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_step_one_between_batch_steps_bitwise(storage):
+    """A box advanced alone inside its batch (lbm_batch_step_one: the
+    single-box path) between multi-rate and graph-replayed batch steps ends
+    bitwise where its lone run ends, and so do the boxes around it."""
+    K = 3
+    boxes = [make_box(nx, ny, storage, True, K, 500 + i) for i, (nx, ny) in enumerate(SIZES)]
+    ref = [make_box(nx, ny, storage, True, K, 500 + i) for i, (nx, ny) in enumerate(SIZES)]
+    b = Batch(boxes)
+    plan = [[4, 0, 3, 7, 1, 5, 2], [2, 5, 5, 1, 3, 1, 6]]
+    extra = {2: 5, 5: 4, 6: 1}
+    b.step_each(plan[0])
+    for i, n in extra.items():
+        b.step_one(i, n)
+    b.step(4)
+    b.step_one(0, 2)
+    b.step_each(plan[1])
+    with pytest.raises(LbmError):
+        b.step_one(len(SIZES), 1)
+    b.sync()
+    for i, (s, r) in enumerate(zip(boxes, ref)):
+        n = plan[0][i] + extra.get(i, 0) + 4 + (2 if i == 0 else 0) + plan[1][i]
+        r.step(n)
+        assert s.steps_done == n
+        assert np.array_equal(s.read("pops")["pops"], r.read("pops")["pops"]), (s.nx, s.ny)
+        assert np.array_equal(s.read("mask")["mask"], r.read("mask")["mask"])
+    b.close()
+
+
 ORACLE_SIZES = [(160, 80), (256, 128), (192, 96), (96, 64), (150, 90)]
 
 
