@@ -66,11 +66,12 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=192)
     ap.add_argument("--serve-step-scale", type=float, default=0.1)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
-    ap.add_argument("--serve-policy", default="hrrn", choices=["work", "time", "lockstep", "tiered", "fifo", "srpt", "hrrn"])
+    ap.add_argument("--serve-policy", default="hrrn", choices=["work", "time", "lockstep", "tiered", "fifo", "express", "srpt", "hrrn"])
     ap.add_argument("--serve-age-weight", type=float, default=0.5,
                     help="srpt policy: requests are ordered by remaining GPU time minus this times the time waited")
     ap.add_argument("--serve-big-s", type=float, default=0.02,
-                    help="tiered policy: requests with more GPU time left than this are served first come, first served")
+                    help="tiered and express policies: requests with more GPU time left than this are served first come, "
+                         "first served")
     ap.add_argument("--serve-big-slowdown", type=float, default=float("inf"),
                     help="tiered policy: past this slowdown of the oldest big request the small ones' share "
                          "is cut to --serve-late-share")

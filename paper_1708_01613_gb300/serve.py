@@ -218,8 +218,10 @@ class FoamServer:
     first served beside equally shared small ones (`tiered_steps`), "fifo"
     and "srpt" fill each quantum in arrival or shortest-remaining-work order
     (`ordered_steps`; "srpt" credits each job `age_weight` times the time
-    it has waited, so the largest jobs are not starved), "hrrn" fills it in
-    order of the ratio of time since arrival to remaining work, and "tiered"
+    it has waited, so the largest jobs are not starved), "express" puts the
+    jobs with less than `big_s` of work left first and keeps arrival order
+    otherwise, "hrrn" fills it in order of the ratio of time since arrival to
+    remaining work, and "tiered"
     cuts the small ones' share to `late_share` while the oldest big job's
     projected latency exceeds `big_slowdown` times its work alone. Every batch runs its plan as multi-rate
     steps (lbm_batch_step_each), so small boxes can take many cheap steps
@@ -228,7 +230,7 @@ class FoamServer:
     max_boxes: int = 64
     quantum_s: float = 0.01
     quantum_updates: float | None = None
-    policy: str = "work"            # "work" | "time" | "lockstep" | "tiered" | "fifo" | "srpt" | "hrrn"
+    policy: str = "work"            # "work" | "time" | "lockstep" | "tiered" | "fifo" | "express" | "srpt" | "hrrn"
     big_s: float = 0.05             # "tiered": a job with more work left than this much GPU time is big
     small_share: float = 0.5        # "tiered": most of a quantum the small jobs take while a big one runs
     big_slowdown: float = float("inf")  # "tiered": once the oldest big job's projected latency exceeds
@@ -306,11 +308,14 @@ class FoamServer:
                 share = fair_time_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
             elif self.policy == "lockstep":
                 share = lockstep_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
-            elif self.policy in ("fifo", "srpt", "hrrn"):
+            elif self.policy in ("fifo", "express", "srpt", "hrrn"):
                 budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
                 spu = model.s_per_update
                 if self.policy == "fifo":
                     key = lambda j: (j.req.arrival_s, j.req.rid)
+                elif self.policy == "express":  # jobs with less than big_s of work left first, then arrival order
+                    bs = self.big_s
+                    key = lambda j: (j.remaining * j.cells * spu >= bs, j.req.arrival_s, j.req.rid)
                 elif self.policy == "srpt":  # remaining GPU time, less `age_weight` times the time waited
                     a = self.age_weight
                     key = lambda j: (j.remaining * j.cells * spu - a * (now - j.req.arrival_s), j.req.arrival_s, j.req.rid)

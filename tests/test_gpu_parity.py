@@ -361,16 +361,19 @@ def test_full_box_8192_crop_against_full_oracle():
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("nx,ny,barrier", [(528, 70, False), (272, 9, False), (320, 80, True), (544, 80, True),
-                                           (1043, 40, False), (250, 9, False), (337, 80, True), (19, 12, False)])
+                                           (1043, 40, False), (250, 9, False), (337, 80, True), (19, 12, False),
+                                           (1025, 9, False), (513, 11, False)])
 @pytest.mark.parametrize("tau", [1.0, 0.8])
 def test_tma_staged_kernel_matches_plain_kernel_bitwise(storage, nx, ny, barrier, tau):
     """The TMA-staged fused steps (one and two cells per thread; ragged last
     strips, periodic wrap, barrier mask staged alongside) give bitwise the
     plain-load kernel's populations, and the FP32 run stays close to the
     oracle. Widths that are not multiples of 16 (1043: a 19-column last strip;
-    250, 337, 19) take the two-cell kernel's variant that bulk-copies the
-    aligned interior of each row and plain-loads the rest, with odd widths and
-    rows that start at odd cell indices."""
+    250, 337, 19; 1025 and 513: a one-column last strip, so the strip before
+    it reaches the last column and its right halo wraps) take the two-cell
+    kernel's variant that bulk-copies the part of each window inside the row
+    and takes the wrapped elements from a side area, with odd widths and rows
+    that start at odd cell indices."""
     if barrier:
         b = two_bubbles(nx, ny, R=20, gap=3.0)
         rho = O.init_bubbles(O.make_params(nx, ny), b, RL, RG, 4.0)
