@@ -27,6 +27,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -66,7 +67,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=192)
     ap.add_argument("--serve-step-scale", type=float, default=0.1)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
-    ap.add_argument("--serve-policy", default="hrrn", choices=["work", "time", "lockstep", "tiered", "fifo", "express", "srpt", "hrrn"])
+    ap.add_argument("--serve-policy", default="hrrn",
+                    choices=["work", "time", "lockstep", "tiered", "fifo", "express", "srpt", "hrrn"])
     ap.add_argument("--serve-age-weight", type=float, default=0.5,
                     help="srpt policy: requests are ordered by remaining GPU time minus this times the time waited")
     ap.add_argument("--serve-big-s", type=float, default=0.02,
@@ -99,10 +101,14 @@ TRAFFIC_SOURCES = {"step": ("step.cu", "lbm_internal.cuh", "tma.cuh"),
 
 
 def sources_sha256(kind: str) -> str:
-    """Hash of the sources a step kernel is built from."""
+    """Hash of the code (comments and whitespace left out) of the sources a
+    step kernel is built from."""
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES[kind]:
-        h.update(open(os.path.join(ROOT, "paper_1708_01613_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1708_01613_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

@@ -276,8 +276,9 @@ void lbm_destroy(lbm_handle* h);
  * Batches: many boxes advanced together. Not in the paper; it serves runs
  * of many independent foam simulations on one GPU. Every step of a batch is
  * one persistent launch of the two-cell staged kernel over a list of work
- * items (box, column strip, row chunk) of all active boxes with nx % 16 == 0
- * (rows the bulk copies can stage), plus one plain-load step per other box,
+ * items (box, column strip, row chunk) of all active boxes with nx % 16 == 0,
+ * one of its unaligned-row variant over the other boxes of at least 16
+ * columns, and one plain-load step per narrower box,
  * preceded, when a relabel is due, by each box's barrier pipeline and
  * followed, with the barrier, by the bounce-back across blocked edges;
  * blocks of steps are captured as CUDA graphs and replayed. Each box evolves

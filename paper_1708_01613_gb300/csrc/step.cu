@@ -1019,7 +1019,8 @@ constexpr int kDynRows = 48;  // row chunk of the dynamically scheduled step
 
 // Rows whose starts are 16-byte aligned for every storage (and mask rows):
 // whole rows are bulk-copied. Other boxes of at least 16 columns take the
-// UNAL variant (aligned interiors bulk-copied, heads and tails plain-loaded).
+// UNAL variant (each window's part inside the row by a covering bulk copy,
+// the elements of a wrapped side from the slot's side area).
 template <int S>
 bool tma2_ok(int nx) {
   return nx % 16 == 0;
@@ -1107,11 +1108,10 @@ cudaError_t launch_variant(const StepParams& p, cudaStream_t s) {
   const int v = p.force_generic;
   if ((v == 4 || v == 0) && tma2_ok<S>(p.nx)) return launch_dyn<S, MASKED, TAU_ONE>(p, s);
   // automatic choice for other widths: the unaligned staging where the box
-  // has interior strips, whose windows arrive in one covering bulk copy
-  // (FP16 2047^2: 0.083 ms against 0.101 plain; 2040^2: 0.074 against 0.101),
-  // plain loads for boxes of at most two strips, whose every strip wraps and
-  // plain-loads its ends in the helper warp (1001^2: 0.035 plain against
-  // 0.039; 511^2: 0.020 against 0.026)
+  // has more than two strips (FP16 2047^2: 0.077 ms against 0.100 plain;
+  // 2040^2: 0.074 against 0.099), plain loads for boxes of at most two
+  // strips, every one of which wraps (1001^2: 0.035 plain against 0.038;
+  // 511^2: 0.020 against 0.026)
   if ((v == 4 || (v == 0 && p.nx > 2 * kBX2)) && tma2_unal_ok(p.nx)) return launch_dyn<S, MASKED, TAU_ONE, true>(p, s);
   if (v == 3) {
     if (tma2_ok<S>(p.nx)) return launch_tma2<S, MASKED, TAU_ONE>(p, s);
