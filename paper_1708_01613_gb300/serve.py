@@ -174,6 +174,27 @@ def ordered_steps(jobs: list[_Job], budget_updates: float, key) -> dict[int, int
     return out
 
 
+def order_key(policy: str, now: float, s_per_update: float, age_weight: float = 0.5, big_s: float = 0.02):
+    """Sort key of the ordered policies at time `now` (seconds since the
+    stream started); ties go to the earlier arrival, then the lower id.
+    "fifo": arrival order; "express": jobs with less than `big_s` of GPU
+    time left first, arrival order within each class; "srpt": remaining GPU
+    time less `age_weight` times the time waited; "hrrn": the highest
+    response ratio, time since arrival over remaining GPU time, first."""
+    def left(j):
+        return j.remaining * j.cells * s_per_update
+
+    if policy == "fifo":
+        return lambda j: (j.req.arrival_s, j.req.rid)
+    if policy == "express":
+        return lambda j: (left(j) >= big_s, j.req.arrival_s, j.req.rid)
+    if policy == "srpt":
+        return lambda j: (left(j) - age_weight * (now - j.req.arrival_s), j.req.arrival_s, j.req.rid)
+    if policy == "hrrn":
+        return lambda j: (-(now - j.req.arrival_s) / max(left(j), 1e-9), j.req.arrival_s, j.req.rid)
+    raise ValueError(f"no ordered policy {policy!r}")
+
+
 def _water_fill(jobs: list[_Job], budget: float, cost) -> dict[int, int]:
     out: dict[int, int] = {}
     left = float(budget)
@@ -310,18 +331,7 @@ class FoamServer:
                 share = lockstep_steps(jobs_now, self.quantum_s, model.launch_s, model.s_per_update)
             elif self.policy in ("fifo", "express", "srpt", "hrrn"):
                 budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update
-                spu = model.s_per_update
-                if self.policy == "fifo":
-                    key = lambda j: (j.req.arrival_s, j.req.rid)
-                elif self.policy == "express":  # jobs with less than big_s of work left first, then arrival order
-                    bs = self.big_s
-                    key = lambda j: (j.remaining * j.cells * spu >= bs, j.req.arrival_s, j.req.rid)
-                elif self.policy == "srpt":  # remaining GPU time, less `age_weight` times the time waited
-                    a = self.age_weight
-                    key = lambda j: (j.remaining * j.cells * spu - a * (now - j.req.arrival_s), j.req.arrival_s, j.req.rid)
-                else:  # highest response ratio (time since arrival over remaining GPU time) first
-                    key = lambda j: (-(now - j.req.arrival_s) / max(j.remaining * j.cells * spu, 1e-9),
-                                     j.req.arrival_s, j.req.rid)
+                key = order_key(self.policy, now, model.s_per_update, self.age_weight, self.big_s)
                 share = ordered_steps(jobs_now, budget, key)
             elif self.policy == "tiered":
                 budget = self.quantum_updates if self.quantum_updates else self.quantum_s / model.s_per_update

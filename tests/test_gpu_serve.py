@@ -122,6 +122,29 @@ def test_ordered_fill_plans():
     assert sum(srpt[j.req.rid] * j.cells for j in jobs) <= 4e6
 
 
+def test_order_keys_of_the_ordered_policies():
+    """Pure host logic: the orders "fifo", "express", "srpt" and "hrrn" put
+    the jobs where their definitions say, at one time of the stream."""
+    from paper_1708_01613_gb300.serve import _Job, order_key
+
+    def job(rid, t, cells, rem):
+        return _Job(Request(rid, t, cells, 1, np.zeros((0, 3)), rem), None, rem, 0.0, 0)
+
+    # at now = 10 s with 1e-9 s per update: remaining GPU time 1e-3, 5.0, 2.0, 0.01 s;
+    # waited 9, 8, 2, 1 s
+    jobs = [job(0, 1.0, 10**4, 100), job(1, 2.0, 10**6, 5000), job(2, 8.0, 10**6, 2000), job(3, 9.0, 10**5, 100)]
+    order = lambda pol, **kw: [j.req.rid for j in sorted(jobs, key=order_key(pol, 10.0, 1e-9, **kw))]
+    assert order("fifo") == [0, 1, 2, 3]
+    assert order("express", big_s=0.02) == [0, 3, 1, 2]
+    # srpt: remaining - w * waited: w = 0: 0.001, 5, 2, 0.01; w = 1: -8.999, -3, 0, -0.99
+    assert order("srpt", age_weight=0.0) == [0, 3, 2, 1]
+    assert order("srpt", age_weight=1.0) == [0, 1, 3, 2]
+    # hrrn: waited / remaining = 9000, 1.6, 1, 100
+    assert order("hrrn") == [0, 3, 1, 2]
+    with pytest.raises(ValueError):
+        order_key("tiered", 0.0, 1e-9)
+
+
 @pytest.mark.gpu
 def test_request_larger_than_budget_is_refused():
     r = requests()[3]
