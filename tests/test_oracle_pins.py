@@ -310,7 +310,7 @@ def test_laplace_law_droplets():
     small gas bubbles in a closed box at coexistence density dissolve. Radii
     10, 20, 30, 40 in boxes of 64-160 cells, relaxed for 12000 steps (the
     fit's intercept is 5 % of dp(10) after 4000 steps, 0.7 % after 8000 and
-    0.05 % after 12000); the GPU sweep takes the survey's 10-60."""
+    0.05 % after 12000); the GPU sweep takes radii 10-60."""
     rl, rg = inputs.RHO_LIQ_G55, inputs.RHO_GAS_G55
     pts = []
     for R, L in ((10, 64), (20, 96), (30, 128), (40, 160)):
@@ -650,7 +650,7 @@ def test_merge_events_brute_force(seed):
 
 
 def test_barrier_without_rupture_stops_coalescence():
-    """Survey pin 9(ii), the paper's statement that while the oxide-network
+    """The paper's statement that while the oxide-network
     wall stands the bubbles never cross it and do not coalesce (Sec. 2.1.5,
     text after the modified Shan-Chen flowchart). Barrier on with rupture
     disabled (eps < 0), K = 1: no coalescence event in 20000 steps for films
@@ -671,7 +671,7 @@ def test_barrier_without_rupture_stops_coalescence():
 
 
 def test_rupture_lets_the_bubbles_merge_later_than_without_barrier():
-    """Survey pin 9(iii): with the barrier and the rupture criterion of Eq. 41
+    """With the barrier and the rupture criterion of Eq. 41
     (default eps), a film cell opens, the wall is removed there and the two
     bubbles coalesce (a true merge event: one component covers both), later
     than without the barrier. T_m itself has no value in the paper to pin
